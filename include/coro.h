@@ -1,0 +1,233 @@
+/*
+ * coro.h -- C ABI of libcoro: coronagraph wavefront propagation on one GB300 (sm_103a).
+ *
+ * The operations follow Douglas & Perrin, "Accelerated Modeling of Near and Far-Field
+ * Diffraction for Coronagraphic Optical Systems" (SPIE 2018):
+ *   - a sampled complex wavefront built from pupil size, oversampling and wavelength
+ *     (Sec. 1.1 "general complex wavefront class"; App. A),
+ *   - optical elements multiplied onto it: A exp(2 pi i OPD / lambda) (Eq. 3), thin lenses
+ *     and quadratic phase factors exp(i pi r^2 / (lambda z)) (Eq. 2; Sec. 1.1),
+ *   - plane-to-plane Fresnel propagation by the angular-spectrum and direct methods
+ *     (Sec. 1.1, Sec. 2.2),
+ *   - the matrix Fourier transform of the semi-analytic coronagraph method (Sec. 1.1, Sec. 2.3),
+ *   - detector intensity and dark-hole reductions (Sec. 1, the 1e-10 contrast goal).
+ *
+ * Conventions (the paper states none of them):
+ *   - A field is [batch][n][n] interleaved complex (re, im), row-major [y][x], in DEVICE
+ *     memory owned by the caller. CORO_C64 = float2, CORO_C128 = double2.
+ *   - Pixel centres sit at x_j = (j - n/2) * pixelscale; the optical axis is pixel n/2.
+ *   - DFT sign: forward exp(-2 pi i jk/n); inverse carries 1/n per axis.
+ *   - SI units (metres, radians); focal-plane sampling in lambda/D per pixel.
+ *
+ * Every call returns a coro_status and never aborts the process. Arguments are checked on the
+ * host before any launch; on failure nothing is launched and coro_last_error() (thread-local)
+ * describes the problem. All launches are asynchronous on the context's stream; device
+ * pointers handed in are borrowed for the duration of that stream-ordered work. There is no
+ * CPU fallback: without a CUDA device every call that launches work returns CORO_ECUDA.
+ */
+#ifndef CORO_H
+#define CORO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CORO_VERSION 1
+
+typedef enum {
+    CORO_OK = 0,
+    CORO_EINVAL = -1,     /* bad argument (null pointer, unsupported size, bad enum)        */
+    CORO_ENOMEM = -2,     /* device or host allocation failed                               */
+    CORO_ECUDA = -3,      /* a CUDA runtime call failed (message in coro_last_error)        */
+    CORO_ETIMEOUT = -4,   /* a bounded device-side wait expired (status flag set by kernel) */
+    CORO_ENOTIMPL = -5,   /* combination not implemented                                    */
+    CORO_ESIZE = -6       /* size outside the supported range                               */
+} coro_status;
+
+typedef enum { CORO_C64 = 0, CORO_C128 = 1 } coro_dtype;
+
+/* ------------------------------------------------------------------------------------------
+ * Context: one device, one stream, cached twiddle tables.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct coro_ctx_s* coro_ctx;
+
+/* Create a context on `device` issuing work on `stream` (a cudaStream_t, borrowed; NULL =
+ * legacy default stream). Allocates small device tables lazily. *out owned by the caller,
+ * released by coro_ctx_destroy. Errors: CORO_EINVAL (out NULL), CORO_ECUDA (no device). */
+coro_status coro_ctx_create(int device, void* stream, coro_ctx* out);
+coro_status coro_ctx_destroy(coro_ctx ctx);
+/* Change the stream later launches go to (borrowed). */
+coro_status coro_ctx_set_stream(coro_ctx ctx, void* stream);
+/* Block the host until the context's stream has drained; reports asynchronous faults. */
+coro_status coro_ctx_synchronize(coro_ctx ctx);
+/* Thread-local description of the last failure ("" if none). Valid until the next call. */
+const char* coro_last_error(void);
+int coro_version(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Wavefront descriptor (Sec. 1.1 complex wavefront class; App. A FresnelWavefront).
+ * Plain struct; no memory is owned by the library.
+ *   data        device, [batch][n][n] complex (see dtype), row-major [y][x]
+ *   pixelscale  host, [batch], metres per pixel; the direct Fresnel hop rewrites it
+ *   wavelength  host, [batch], metres
+ * n is a power of two in [32, 8192] (C128: [32, 4096]); batch >= 1.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    void* data;
+    int dtype;
+    int batch;
+    int n;
+    double* pixelscale;
+    const double* wavelength;
+} coro_wavefront;
+
+/* a1: fill every sample with `amplitude` (App. A: a new wavefront has unit amplitude). */
+coro_status coro_wavefront_init(coro_ctx ctx, const coro_wavefront* wf, double amplitude);
+
+/* ------------------------------------------------------------------------------------------
+ * Optical elements (a2, a3). An element multiplies the field pointwise by a transmission.
+ * Geometry uses the wavefront's per-item pixelscale (metres) unless noted.
+ * ------------------------------------------------------------------------------------------ */
+typedef enum {
+    CORO_EL_APERTURE = 1, /* circular aperture r <= radius, central obscuration r < obscuration
+                             * radius, n_spiders (0 or 4) vanes |x|<w/2 or |y|<w/2 (App. A
+                             * CircularAperture; obscured/spidered pupils)                    */
+    CORO_EL_CIRCLE = 2,   /* circular stop r <= radius transmits; CORO_ELF_OPAQUE_INSIDE makes
+                             * it an occulting spot (field stops, Lyot stops, occulters)      */
+    CORO_EL_LENS = 3,     /* thin lens exp(-i pi r^2 / (lambda f)) (Sec. 1.1, Eq. 2 reading)  */
+    CORO_EL_OPD_MAP = 4,  /* A exp(2 pi i OPD / lambda) from a device float map (Eq. 3);
+                             * amplitude map optional                                         */
+    CORO_EL_ZERNIKE = 5,  /* OPD = sum_j c_j Z_j(r/radius) over Noll j = j_first.., zero
+                             * outside the disk (unit-RMS Noll normalisation)                 */
+    CORO_EL_SINE = 6,     /* OPD = sine_amplitude * sin(2 pi sine_freq x) along x (axis 0) or y
+                             * (axis 1) (App. A SineWaveWFE)                                   */
+    CORO_EL_SCALAR = 7    /* multiply by a real scalar (ScalarTransmission, App. B)            */
+} coro_element_kind;
+
+#define CORO_ELF_OPAQUE_INSIDE 1  /* CORO_EL_CIRCLE: block r <= radius instead of passing it */
+#define CORO_ELF_MAP_BATCHED   2  /* CORO_EL_OPD_MAP: map is [batch][n][n], else [n][n]       */
+
+typedef struct {
+    int kind;                 /* coro_element_kind                                           */
+    int flags;                /* CORO_ELF_*                                                  */
+    int plane;                /* plane index inside a Fresnel plan (ignored by apply_element) */
+    int n_spiders;            /* APERTURE: 0 or 4                                            */
+    double radius;            /* APERTURE/CIRCLE/ZERNIKE: metres                             */
+    double obscuration;       /* APERTURE: fraction of radius (0 = none)                     */
+    double spider_width;      /* APERTURE: vane width, metres                                */
+    double focal_length;      /* LENS: metres (positive = converging)                        */
+    const float* opd;         /* OPD_MAP: device, metres                                     */
+    const float* amplitude;   /* OPD_MAP: device amplitude (same shape as opd) or NULL       */
+    const double* coeffs;     /* ZERNIKE: host, metres, n_coeffs values                      */
+    int j_first;              /* ZERNIKE: Noll index of coeffs[0] (>= 1)                     */
+    int n_coeffs;             /* ZERNIKE: count, j_first + n_coeffs - 1 <= 36                */
+    double sine_freq;         /* SINE: cycles per metre                                      */
+    double sine_amplitude;    /* SINE: metres                                                */
+    int axis;                 /* SINE: 0 = varies along x, 1 = along y                       */
+    double scalar;            /* SCALAR                                                      */
+} coro_element;
+
+/* Apply one element in place (unfused elementwise kernel). */
+coro_status coro_apply_element(coro_ctx ctx, const coro_wavefront* wf, const coro_element* el);
+
+/* ------------------------------------------------------------------------------------------
+ * Fresnel propagation (a4-a6, a6').
+ * CORO_FRESNEL_AS: angular spectrum (Sec. 1.1, Lawrence Eqs. 82-89 cited):
+ *     E(z) = IDFT2[ exp(-i pi lambda z (fx^2 + fy^2)) DFT2[E] ], pixelscale unchanged.
+ * CORO_FRESNEL_DIRECT: single-FFT Fresnel (Sec. 1.1):
+ *     E'(u) = 1/(i lambda z) exp(i pi u^2/(lambda z)) dx^2 DFT2[E exp(i pi x^2/(lambda z))],
+ *     pixelscale[b] <- lambda_b z / (n dx_b).
+ * DFTs are centred (fftshift folded into the kernels). The global piston exp(2 pi i z/lambda)
+ * is dropped. z != 0. Three HBM passes (row FFT, column FFT*H*IFFT, row IFFT).
+ * ------------------------------------------------------------------------------------------ */
+typedef enum { CORO_FRESNEL_AS = 0, CORO_FRESNEL_DIRECT = 1 } coro_fresnel_method;
+
+coro_status coro_propagate_fresnel(coro_ctx ctx, coro_wavefront* wf, double z, int method);
+
+/* Centred 2-D DFT in place: direction -1 forward (no scaling), +1 inverse (1/n^2). Used for
+ * Fraunhofer propagation by large FFT (Sec. 1.1). */
+coro_status coro_fft2(coro_ctx ctx, const coro_wavefront* wf, int direction);
+
+/* ------------------------------------------------------------------------------------------
+ * Fused Fresnel system (D2: the ordered (optic, distance) list of App. B).
+ * Plane p receives every element whose .plane == p (applied in array order), then the field
+ * hops distance[p] by method[p] to plane p+1 (for p < n_planes-1). Consecutive hops are fused
+ * so that each angular-spectrum hop costs two HBM round trips: a row pass
+ * (IFFT_rows . elements . FFT_rows) and a column pass (FFT_cols . H . IFFT_cols).
+ * flags: CORO_PLAN_INIT_UNIFORM -- the input is a unit-amplitude field (a1) that is generated
+ * in the first pass instead of read.
+ * The plan copies everything it needs (tables are built on the device in FP64 and rounded to
+ * the field precision), except device maps referenced by elements, which must stay valid and
+ * unchanged while the plan is executed.
+ * ------------------------------------------------------------------------------------------ */
+#define CORO_PLAN_INIT_UNIFORM 1
+
+typedef struct coro_plan_s* coro_plan;
+
+typedef struct {
+    int dtype;
+    int batch;
+    int n;
+    const double* pixelscale;   /* host [batch], pixelscale at plane 0                       */
+    const double* wavelength;   /* host [batch]                                              */
+    int n_planes;
+    const double* distance;     /* host [n_planes-1], metres                                 */
+    const int* method;          /* host [n_planes-1], coro_fresnel_method; NULL = all AS     */
+    int n_elements;
+    const coro_element* elements;
+    int flags;
+} coro_fresnel_desc;
+
+coro_status coro_fresnel_plan_create(coro_ctx ctx, const coro_fresnel_desc* desc, coro_plan* out);
+/* Run the plan in place on `field` (device, [batch][n][n]). pixelscale_out (host [batch], may
+ * be NULL) receives the final pixel scale. */
+coro_status coro_fresnel_plan_execute(coro_plan plan, void* field, double* pixelscale_out);
+/* Number of kernels one execute launches (for launch accounting). */
+coro_status coro_plan_launch_count(coro_plan plan, int* out);
+/* Run passes [first, first + count) of the plan only (for per-launch timing); running every
+ * range in order is identical to coro_fresnel_plan_execute. */
+coro_status coro_fresnel_plan_execute_range(coro_plan plan, void* field, int first, int count);
+/* Describe pass i: *is_row (1 = row pass, 0 = column pass) and *bytes, the algorithmic HBM
+ * traffic of the launch (field read unless generated, field write, OPD/amplitude maps read). */
+coro_status coro_fresnel_plan_pass_info(coro_plan plan, int i, int* is_row, double* bytes);
+coro_status coro_plan_destroy(coro_plan plan);
+
+/* ------------------------------------------------------------------------------------------
+ * Matrix Fourier transform (a7; Sec. 1.1 "discrete matrix Fourier transforms", Soummer 2007;
+ * Sec. 2.3 "sines and cosines ... in the matrix DFT").
+ * direction -1 (pupil -> focal plane):
+ *     out[v,u] = s sum_{i,j} in[i,j] exp(-2 pi i (X_j U_u + Y_i V_v)),
+ *     X_j = (j - n/2)/npix (units of D), U_u = (u - m/2) du (units of lambda/D), s = du/npix.
+ * direction +1 (focal plane -> pupil): input pitch du (lambda/D), output pitch 1/npix (D),
+ *     exponent +2 pi i, same s.
+ * in: [batch][n_in][n_in]; out: [batch][m][m]; C64 only. du: host [batch] (lambda/D per pixel
+ * of the focal-plane side). npix: pupil pixels across D. precision: coro_mft_prec.
+ * Work buffers are taken from the context (allocated on first use, grown as needed).
+ * ------------------------------------------------------------------------------------------ */
+typedef enum {
+    CORO_MFT_FP32 = 0,    /* FP32 CUDA-core complex GEMM                                     */
+    CORO_MFT_3XTF32 = 1,  /* split TF32 tensor-core GEMM (hi*hi + hi*lo + lo*hi), FP32 acc   */
+    CORO_MFT_3XBF16 = 2   /* split BF16 tensor-core GEMM, FP32 accumulate                    */
+} coro_mft_prec;
+
+coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in, double npix, int direction,
+                               int m, const double* du, int precision, coro_wavefront* out);
+
+/* ------------------------------------------------------------------------------------------
+ * Detector reductions (a9).
+ * coro_intensity: out[b][y][x] = |E|^2 / norm[b] (norm NULL = 1); out device float.
+ * coro_darkhole_sum: host_out[b] = sum over rho in [r_in, r_out] of |E|^2 / norm[b], with
+ *     rho = |(x - n/2, y - n/2)| * du[b] in lambda/D; FP64 accumulation. Synchronises the
+ *     stream to return the host values.
+ * ------------------------------------------------------------------------------------------ */
+coro_status coro_intensity(coro_ctx ctx, const coro_wavefront* wf, const double* norm, float* out);
+coro_status coro_darkhole_sum(coro_ctx ctx, const coro_wavefront* wf, const double* du,
+                              double r_in, double r_out, const double* norm, double* host_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CORO_H */

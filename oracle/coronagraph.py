@@ -66,8 +66,7 @@ def peak_intensity(e_pupil: np.ndarray, p: LyotParams) -> float:
 
 
 def dark_hole_mask(m: int, du: float, r_in: float, r_out: float) -> np.ndarray:
-    x, y = optics.grid(m, du)
-    r2 = x * x + y * y
+    r2 = optics.radius_sq_exact(m, du)
     return ((r2 >= r_in * r_in) & (r2 <= r_out * r_out)).astype(np.float64)
 
 

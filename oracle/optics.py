@@ -23,10 +23,12 @@ def grid(n: int, dx: float) -> tuple[np.ndarray, np.ndarray]:
 
 
 def radius_sq_exact(n: int, dx: float) -> np.ndarray:
-    """r^2 = dx^2 (i'^2 + j'^2) with the integer part exact (Sec. 2.3: the quadratic phase
-    argument is large, so it is formed from exact integers)."""
+    """r^2 = (i'^2 + j'^2) * (dx * dx), with i' = i - n/2 and the integer sum exact (Sec. 2.3:
+    the quadratic phase argument is large, so it is formed from exact integers). Every binary
+    mask below is the FP64 predicate r^2 <= R * R on this array."""
     k = np.arange(n, dtype=np.int64) - n // 2
-    return (k[None, :] ** 2 + k[:, None] ** 2).astype(np.float64) * dx * dx
+    k2 = (k[None, :] ** 2 + k[:, None] ** 2).astype(np.float64)
+    return k2 * (dx * dx)
 
 
 def circular_aperture(n: int, dx: float, radius: float, obscuration: float = 0.0,
@@ -35,10 +37,11 @@ def circular_aperture(n: int, dx: float, radius: float, obscuration: float = 0.0
     (central obscuration), and blocks the vanes |x| < w/2 or |y| < w/2 when spiders are on
     (four vanes in a '+' through the centre)."""
     x, y = grid(n, dx)
-    r2 = x * x + y * y
+    r2 = radius_sq_exact(n, dx)
     a = (r2 <= radius * radius).astype(np.float64)
     if obscuration > 0.0:
-        a[r2 < (obscuration * radius) ** 2] = 0.0
+        ro = obscuration * radius
+        a[r2 < ro * ro] = 0.0
     if n_spiders:
         if n_spiders != 4:
             raise ValueError("only the four-vane '+' spider is defined")
@@ -51,8 +54,7 @@ def circle_stop(n: int, pitch: float, radius: float, opaque_inside: bool = False
     """Circular stop on a grid of the given pitch: transmits r <= radius (a field or Lyot stop),
     or, with ``opaque_inside``, blocks r <= radius (an occulting spot). A negative radius
     is an empty disk."""
-    x, y = grid(n, pitch)
-    inside = ((x * x + y * y) <= radius * radius) & (radius >= 0.0)
+    inside = (radius_sq_exact(n, pitch) <= radius * radius) & (radius >= 0.0)
     return (~inside if opaque_inside else inside).astype(np.float64)
 
 
@@ -141,7 +143,7 @@ def zernike_opd(n: int, dx: float, radius: float, coeffs_m: np.ndarray,
     opd = np.zeros((n, n))
     for i, c in enumerate(coeffs_m):
         opd += c * zernike_noll(j_first + i, rho, theta)
-    opd[rho > 1.0] = 0.0
+    opd[radius_sq_exact(n, dx) > radius * radius] = 0.0
     return opd
 
 

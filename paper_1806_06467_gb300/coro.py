@@ -1,0 +1,313 @@
+"""Thin Python binding of libcoro's C ABI (include/coro.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels. PyTorch supplies device memory and the stream. If ``libcoro.so`` has not been built
+the import of the library raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcoro.so")
+
+# status codes
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, ESIZE = 0, -1, -2, -3, -4, -5, -6
+C64, C128 = 0, 1
+EL_APERTURE, EL_CIRCLE, EL_LENS, EL_OPD_MAP, EL_ZERNIKE, EL_SINE, EL_SCALAR = 1, 2, 3, 4, 5, 6, 7
+ELF_OPAQUE_INSIDE, ELF_MAP_BATCHED = 1, 2
+FRESNEL_AS, FRESNEL_DIRECT = 0, 1
+PLAN_INIT_UNIFORM = 1
+MFT_FP32, MFT_3XTF32, MFT_3XBF16 = 0, 1, 2
+
+
+class CoroError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libcoro status {status}: {msg}")
+        self.status = status
+
+
+class Wavefront(ct.Structure):
+    _fields_ = [("data", ct.c_void_p), ("dtype", ct.c_int), ("batch", ct.c_int), ("n", ct.c_int),
+                ("pixelscale", ct.POINTER(ct.c_double)), ("wavelength", ct.POINTER(ct.c_double))]
+
+
+class Element(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("flags", ct.c_int), ("plane", ct.c_int), ("n_spiders", ct.c_int),
+                ("radius", ct.c_double), ("obscuration", ct.c_double), ("spider_width", ct.c_double),
+                ("focal_length", ct.c_double), ("opd", ct.c_void_p), ("amplitude", ct.c_void_p),
+                ("coeffs", ct.POINTER(ct.c_double)), ("j_first", ct.c_int), ("n_coeffs", ct.c_int),
+                ("sine_freq", ct.c_double), ("sine_amplitude", ct.c_double), ("axis", ct.c_int),
+                ("scalar", ct.c_double)]
+
+
+class FresnelDesc(ct.Structure):
+    _fields_ = [("dtype", ct.c_int), ("batch", ct.c_int), ("n", ct.c_int),
+                ("pixelscale", ct.POINTER(ct.c_double)), ("wavelength", ct.POINTER(ct.c_double)),
+                ("n_planes", ct.c_int), ("distance", ct.POINTER(ct.c_double)), ("method", ct.POINTER(ct.c_int)),
+                ("n_elements", ct.c_int), ("elements", ct.POINTER(Element)), ("flags", ct.c_int)]
+
+
+_P = ct.c_void_p
+_SIGS = {
+    "coro_version": (ct.c_int, []),
+    "coro_last_error": (ct.c_char_p, []),
+    "coro_ctx_create": (ct.c_int, [ct.c_int, _P, ct.POINTER(_P)]),
+    "coro_ctx_destroy": (ct.c_int, [_P]),
+    "coro_ctx_set_stream": (ct.c_int, [_P, _P]),
+    "coro_ctx_synchronize": (ct.c_int, [_P]),
+    "coro_wavefront_init": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_double]),
+    "coro_apply_element": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.POINTER(Element)]),
+    "coro_propagate_fresnel": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_double, ct.c_int]),
+    "coro_fft2": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_int]),
+    "coro_fresnel_plan_create": (ct.c_int, [_P, ct.POINTER(FresnelDesc), ct.POINTER(_P)]),
+    "coro_fresnel_plan_execute": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double)]),
+    "coro_plan_launch_count": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
+    "coro_fresnel_plan_execute_range": (ct.c_int, [_P, _P, ct.c_int, ct.c_int]),
+    "coro_fresnel_plan_pass_info": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]),
+    "coro_plan_destroy": (ct.c_int, [_P]),
+    "coro_propagate_mft": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_double, ct.c_int, ct.c_int,
+                                      ct.POINTER(ct.c_double), ct.c_int, ct.POINTER(Wavefront)]),
+    "coro_intensity": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.POINTER(ct.c_double), _P]),
+    "coro_darkhole_sum": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.POINTER(ct.c_double), ct.c_double,
+                                     ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
+}
+
+
+def declared_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+class Library:
+    """The loaded libcoro.so with typed entry points."""
+    _inst: "Library | None" = None
+
+    def __init__(self, path: str = LIB_PATH):
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcoro is not built ({path} missing): run __graft_entry__.build()")
+        self.path = path
+        self.dll = ct.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(self.dll, name)
+            fn.restype = res
+            fn.argtypes = args
+
+    @classmethod
+    def get(cls) -> "Library":
+        if cls._inst is None:
+            cls._inst = cls()
+        return cls._inst
+
+    def check(self, status: int):
+        if status != OK:
+            raise CoroError(status, self.dll.coro_last_error().decode())
+
+    def __getattr__(self, name):
+        return getattr(self.dll, name)
+
+
+def _dbl(values) -> ct.Array:
+    arr = np.ascontiguousarray(np.asarray(values, dtype=np.float64).ravel())
+    return (ct.c_double * len(arr))(*arr.tolist())
+
+
+class Context:
+    """coro_ctx bound to a CUDA device and stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.lib = Library.get()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ct.c_void_p()
+        self.lib.check(self.lib.coro_ctx_create(device, ct.c_void_p(stream.cuda_stream), ct.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.coro_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        self.lib.check(self.lib.coro_ctx_synchronize(self.handle))
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.complex64:
+        return C64
+    if t.dtype == torch.complex128:
+        return C128
+    raise TypeError(f"field must be complex64 or complex128, got {t.dtype}")
+
+
+class WF:
+    """Keeps a Wavefront struct and its host arrays alive. field: [batch][n][n] CUDA tensor."""
+
+    def __init__(self, field, pixelscale: Sequence[float] | float | None = None,
+                 wavelength: Sequence[float] | float | None = None):
+        if field.dim() == 2:
+            field = field.unsqueeze(0)
+        if not field.is_cuda or not field.is_contiguous():
+            raise ValueError("field must be a contiguous CUDA tensor")
+        self.field = field
+        b, n0, n1 = field.shape
+        if n0 != n1:
+            raise ValueError("field must be square")
+        ps = np.broadcast_to(np.asarray(1.0 if pixelscale is None else pixelscale, float), (b,))
+        lam = np.broadcast_to(np.asarray(1.0 if wavelength is None else wavelength, float), (b,))
+        self._ps = _dbl(ps)
+        self._lam = _dbl(lam)
+        self.s = Wavefront(field.data_ptr(), _dtype_code(field), b, n0, self._ps, self._lam)
+
+    @property
+    def pixelscale(self) -> np.ndarray:
+        return np.array(self._ps[:])
+
+
+def element(kind: int, plane: int = 0, **kw) -> Element:
+    """Build a coro_element; keyword names follow the C struct (coeffs as a sequence)."""
+    e = Element()
+    e.kind = kind
+    e.plane = plane
+    keep = []
+    for k, v in kw.items():
+        if k == "coeffs":
+            arr = _dbl(v)
+            keep.append(arr)
+            e.coeffs = arr
+            e.n_coeffs = len(arr)
+        elif k in ("opd", "amplitude"):
+            if v is not None:
+                keep.append(v)
+                setattr(e, k, v.data_ptr())
+        else:
+            setattr(e, k, v)
+    e._keep = keep
+    return e
+
+
+def wavefront_init(ctx: Context, field, amplitude: float = 1.0):
+    w = WF(field)
+    ctx.lib.check(ctx.lib.coro_wavefront_init(ctx.handle, ct.byref(w.s), amplitude))
+
+
+def apply_element(ctx: Context, field, pixelscale, wavelength, el: Element):
+    w = WF(field, pixelscale, wavelength)
+    ctx.lib.check(ctx.lib.coro_apply_element(ctx.handle, ct.byref(w.s), ct.byref(el)))
+
+
+def propagate_fresnel(ctx: Context, field, pixelscale, wavelength, z: float, method: int = FRESNEL_AS) -> np.ndarray:
+    """In-place hop; returns the new per-item pixel scale."""
+    w = WF(field, pixelscale, wavelength)
+    ctx.lib.check(ctx.lib.coro_propagate_fresnel(ctx.handle, ct.byref(w.s), z, method))
+    return w.pixelscale
+
+
+def fft2(ctx: Context, field, direction: int = -1):
+    w = WF(field)
+    ctx.lib.check(ctx.lib.coro_fft2(ctx.handle, ct.byref(w.s), direction))
+
+
+def propagate_mft(ctx: Context, field, npix: float, direction: int, m: int, du, precision: int = MFT_FP32, out=None):
+    import torch
+    w = WF(field)
+    b = w.s.batch
+    if out is None:
+        out = torch.empty((b, m, m), dtype=field.dtype, device=field.device)
+    wo = WF(out)
+    du_arr = _dbl(np.broadcast_to(np.asarray(du, float), (b,)))
+    ctx.lib.check(ctx.lib.coro_propagate_mft(ctx.handle, ct.byref(w.s), npix, direction, m, du_arr,
+                                             precision, ct.byref(wo.s)))
+    return out
+
+
+def intensity(ctx: Context, field, norm=None, out=None):
+    import torch
+    w = WF(field)
+    if out is None:
+        out = torch.empty(w.field.shape, dtype=torch.float32, device=field.device)
+    nrm = None if norm is None else _dbl(np.broadcast_to(np.asarray(norm, float), (w.s.batch,)))
+    ctx.lib.check(ctx.lib.coro_intensity(ctx.handle, ct.byref(w.s), nrm, ct.c_void_p(out.data_ptr())))
+    return out
+
+
+def darkhole_sum(ctx: Context, field, du, r_in: float, r_out: float, norm=None) -> np.ndarray:
+    w = WF(field)
+    b = w.s.batch
+    du_arr = _dbl(np.broadcast_to(np.asarray(du, float), (b,)))
+    nrm = None if norm is None else _dbl(np.broadcast_to(np.asarray(norm, float), (b,)))
+    out = (ct.c_double * b)()
+    ctx.lib.check(ctx.lib.coro_darkhole_sum(ctx.handle, ct.byref(w.s), du_arr, r_in, r_out, nrm, out))
+    return np.array(out[:])
+
+
+class FresnelPlan:
+    """Fused plane-by-plane Fresnel system (coro_fresnel_plan_*)."""
+
+    def __init__(self, ctx: Context, *, n: int, batch: int, pixelscale, wavelength, distances,
+                 elements: Sequence[Element], methods=None, dtype: int = C64, init_uniform: bool = False):
+        self.ctx = ctx
+        self.batch = batch
+        d = FresnelDesc()
+        d.dtype, d.batch, d.n = dtype, batch, n
+        self._ps = _dbl(np.broadcast_to(np.asarray(pixelscale, float), (batch,)))
+        self._lam = _dbl(np.broadcast_to(np.asarray(wavelength, float), (batch,)))
+        d.pixelscale, d.wavelength = self._ps, self._lam
+        d.n_planes = len(distances) + 1
+        self._dist = _dbl(distances) if len(distances) else None
+        d.distance = self._dist
+        if methods is not None:
+            self._meth = (ct.c_int * len(methods))(*methods)
+            d.method = self._meth
+        self._els = (Element * max(1, len(elements)))(*elements)
+        self._keep = list(elements)
+        d.n_elements = len(elements)
+        d.elements = self._els
+        d.flags = PLAN_INIT_UNIFORM if init_uniform else 0
+        h = ct.c_void_p()
+        ctx.lib.check(ctx.lib.coro_fresnel_plan_create(ctx.handle, ct.byref(d), ct.byref(h)))
+        self.handle = h
+
+    def execute(self, field) -> np.ndarray:
+        ps = (ct.c_double * self.batch)()
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_execute(self.handle, ct.c_void_p(field.data_ptr()), ps))
+        return np.array(ps[:])
+
+    def execute_range(self, field, first: int, count: int = 1):
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_execute_range(
+            self.handle, ct.c_void_p(field.data_ptr()), first, count))
+
+    def pass_info(self, i: int) -> tuple[bool, float]:
+        """(is_row_pass, algorithmic HBM bytes) of pass i."""
+        r, b = ct.c_int(), ct.c_double()
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_info(self.handle, i, ct.byref(r), ct.byref(b)))
+        return bool(r.value), b.value
+
+    @property
+    def launch_count(self) -> int:
+        c = ct.c_int()
+        self.ctx.lib.check(self.ctx.lib.coro_plan_launch_count(self.handle, ct.byref(c)))
+        return c.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.coro_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

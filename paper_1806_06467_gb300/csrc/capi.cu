@@ -1,0 +1,912 @@
+// capi.cu -- C ABI of libcoro: context, wavefront elements, Fresnel propagation, fused
+// Fresnel plans and detector reductions. Every compute step runs in the kernels of this
+// library; the host side only validates arguments, builds small parameter blocks and
+// launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "capi_common.h"
+#include "passes.cuh"
+
+using namespace coro;
+
+// =========================================================================== errors
+
+namespace coro {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+coro_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    return e == cudaErrorMemoryAllocation ? CORO_ENOMEM : CORO_ECUDA;
+}
+
+long long disk_threshold(double r, double pitch, bool strict) {
+    if (!(r >= 0.0)) return -1;
+    const double p2 = pitch * pitch, rr = r * r;
+    auto ok = [&](long long m) { return strict ? (double)m * p2 < rr : (double)m * p2 <= rr; };
+    double guess = std::floor(rr / p2);
+    if (guess > 4.0e9) guess = 4.0e9;     // beyond any grid: everything passes
+    long long m = (long long)guess;
+    while (ok(m + 1) && m < 4000000000LL) ++m;
+    while (m >= 0 && !ok(m)) --m;
+    return m;
+}
+
+long long band_threshold(double half, double pitch) {
+    if (!(half > 0.0)) return -1;
+    double guess = std::floor(half / pitch);
+    if (guess > 1.0e9) guess = 1.0e9;
+    long long k = (long long)guess;
+    while ((double)(k + 1) * pitch < half && k < 1000000000LL) ++k;
+    while (k >= 0 && !((double)k * pitch < half)) --k;
+    return k;
+}
+
+}  // namespace coro
+
+extern "C" const char* coro_last_error(void) { return g_err.c_str(); }
+extern "C" int coro_version(void) { return CORO_VERSION; }
+
+// =========================================================================== FP64 table kernels
+
+namespace {
+
+// tw[m] = exp(-2 pi i m / n), evaluated in FP64 (sincospi of an exact rational) and rounded.
+template <typename C>
+__global__ void twiddle_kernel(C* tw, int n) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)n, &s, &c);
+    tw[m] = mk<C>((typename real_of<C>::type)c, (typename real_of<C>::type)s);
+}
+
+// Separable phase table: value[k] = mag * (-1)^(checker*k) * exp(2 pi i sign frac(k'^2 c)),
+// k' = k - n/2. The cycle count k'^2 c is reduced to its fractional part in FP64 before the
+// sine and cosine (Sec. 2.3: quadratic phase factors reach 1e6-1e7 radians at the array edge).
+struct TabSpec {
+    double c;        // cycles per k'^2
+    double mag_re, mag_im;
+    int sign;        // +1 / -1
+    int checker;     // multiply by (-1)^k
+};
+
+template <typename C>
+__global__ void sep_table_kernel(C* out, int n, const TabSpec* spec) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (k >= n) return;
+    const TabSpec sp = spec[b];
+    const long long kk = (long long)k - n / 2;
+    double cyc = (double)(kk * kk) * sp.c;
+    cyc -= rint(cyc);
+    double s, c;
+    sincospi(2.0 * cyc, &s, &c);
+    if (sp.sign < 0) s = -s;
+    double re = sp.mag_re * c - sp.mag_im * s;
+    double im = sp.mag_re * s + sp.mag_im * c;
+    if (sp.checker && (k & 1)) { re = -re; im = -im; }
+    using R = typename real_of<C>::type;
+    out[(size_t)b * n + k] = mk<C>((R)re, (R)im);
+}
+
+}  // namespace
+
+namespace coro {
+
+const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st) {
+    auto& cache = dbl ? ctx->tw64 : ctx->tw32;
+    auto it = cache.find(n);
+    if (it != cache.end()) return it->second;
+    void* p = nullptr;
+    const size_t bytes = (size_t)n * (dbl ? sizeof(double2) : sizeof(float2));
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) { *st = cuda_fail(e, "cudaMalloc(twiddles)"); return nullptr; }
+    const int th = 256;
+    if (dbl) twiddle_kernel<double2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((double2*)p, n);
+    else twiddle_kernel<float2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((float2*)p, n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { cudaFree(p); *st = cuda_fail(e, "twiddle_kernel"); return nullptr; }
+    cache[n] = p;
+    return p;
+}
+
+void* upload_async(coro_ctx ctx, const void* host, size_t bytes, coro_status* st) {
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+    if (e != cudaSuccess) { *st = cuda_fail(e, "cudaMallocAsync"); return nullptr; }
+    if (host) {
+        e = cudaMemcpyAsync(p, host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) { cudaFreeAsync(p, ctx->stream); *st = cuda_fail(e, "cudaMemcpyAsync"); return nullptr; }
+    }
+    return p;
+}
+
+void free_async(coro_ctx ctx, void* p) {
+    if (p) cudaFreeAsync(p, ctx->stream);
+}
+
+void* ctx_work(coro_ctx ctx, size_t bytes, coro_status* st) {
+    if (ctx->work_bytes >= bytes) return ctx->work;
+    if (ctx->work) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->work);
+        ctx->work = nullptr;
+        ctx->work_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->work, bytes);
+    if (e != cudaSuccess) { ctx->work = nullptr; *st = cuda_fail(e, "cudaMalloc(work)"); return nullptr; }
+    ctx->work_bytes = bytes;
+    return ctx->work;
+}
+
+}  // namespace coro
+
+// =========================================================================== context
+
+extern "C" coro_status coro_ctx_create(int device, void* stream, coro_ctx* out) {
+    clear_error();
+    if (!out) { set_error("coro_ctx_create: out is NULL"); return CORO_EINVAL; }
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        set_error("coro_ctx_create: no CUDA device (%s)", cudaGetErrorString(e));
+        return CORO_ECUDA;
+    }
+    if (device < 0 || device >= count) { set_error("coro_ctx_create: device %d of %d", device, count); return CORO_EINVAL; }
+    DeviceGuard g(device);
+    if (!g.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    auto* c = new (std::nothrow) coro_ctx_s;
+    if (!c) { set_error("coro_ctx_create: out of host memory"); return CORO_ENOMEM; }
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    *out = c;
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_ctx_destroy(coro_ctx ctx) {
+    clear_error();
+    if (!ctx) return CORO_OK;
+    {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        for (auto& kv : ctx->tw32) cudaFree(kv.second);
+        for (auto& kv : ctx->tw64) cudaFree(kv.second);
+        if (ctx->work) cudaFree(ctx->work);
+    }
+    delete ctx;
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_ctx_set_stream(coro_ctx ctx, void* stream) {
+    clear_error();
+    if (!ctx) { set_error("coro_ctx_set_stream: ctx is NULL"); return CORO_EINVAL; }
+    ctx->stream = (cudaStream_t)stream;
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_ctx_synchronize(coro_ctx ctx) {
+    clear_error();
+    if (!ctx) { set_error("coro_ctx_synchronize: ctx is NULL"); return CORO_EINVAL; }
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return CORO_OK;
+}
+
+// =========================================================================== validation
+
+static coro_status check_wf(const char* fn, coro_ctx ctx, const coro_wavefront* wf, bool need_ps = true) {
+    if (!ctx) { set_error("%s: ctx is NULL", fn); return CORO_EINVAL; }
+    if (!wf) { set_error("%s: wavefront is NULL", fn); return CORO_EINVAL; }
+    if (!wf->data) { set_error("%s: wavefront data is NULL", fn); return CORO_EINVAL; }
+    if (wf->dtype != CORO_C64 && wf->dtype != CORO_C128) { set_error("%s: bad dtype %d", fn, wf->dtype); return CORO_EINVAL; }
+    if (wf->batch < 1 || wf->batch > 65535) { set_error("%s: batch %d outside [1, 65535]", fn, wf->batch); return CORO_ESIZE; }
+    const int nmax = wf->dtype == CORO_C64 ? 8192 : 4096;
+    if (!is_pow2(wf->n) || wf->n < 32 || wf->n > nmax) {
+        set_error("%s: n = %d must be a power of two in [32, %d]", fn, wf->n, nmax);
+        return CORO_ESIZE;
+    }
+    if (need_ps) {
+        if (!wf->pixelscale || !wf->wavelength) { set_error("%s: pixelscale/wavelength arrays are NULL", fn); return CORO_EINVAL; }
+        for (int b = 0; b < wf->batch; ++b) {
+            if (!(wf->pixelscale[b] > 0.0) || !std::isfinite(wf->pixelscale[b])) { set_error("%s: pixelscale[%d] must be > 0", fn, b); return CORO_EINVAL; }
+            if (!(wf->wavelength[b] > 0.0) || !std::isfinite(wf->wavelength[b])) { set_error("%s: wavelength[%d] must be > 0", fn, b); return CORO_EINVAL; }
+        }
+    }
+    return CORO_OK;
+}
+
+// =========================================================================== element compiler
+
+namespace {
+
+// Owns the device parameter blocks of compiled elements. Stream-ordered frees unless the
+// owner is a plan (then freed at destroy, after a synchronize).
+struct DevBlocks {
+    coro_ctx ctx = nullptr;
+    std::vector<void*> blocks;
+    bool plan_owned = false;
+    void* add(const void* host, size_t bytes, coro_status* st) {
+        void* p = nullptr;
+        if (plan_owned) {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess) { *st = cuda_fail(e, "cudaMalloc(plan params)"); return nullptr; }
+            if (host) {
+                e = cudaMemcpyAsync(p, host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+                if (e != cudaSuccess) { cudaFree(p); *st = cuda_fail(e, "cudaMemcpyAsync"); return nullptr; }
+            }
+        } else {
+            p = upload_async(ctx, host, bytes, st);
+            if (!p) return nullptr;
+        }
+        blocks.push_back(p);
+        return p;
+    }
+    void release() {
+        if (plan_owned) {
+            for (void* p : blocks) cudaFree(p);
+        } else {
+            for (void* p : blocks) free_async(ctx, p);
+        }
+        blocks.clear();
+    }
+};
+
+// Separable complex table [batch][n] generated on the device from per-item specs.
+void* make_table(DevBlocks& db, bool dbl, int n, const std::vector<TabSpec>& specs, coro_status* st) {
+    const int batch = (int)specs.size();
+    const size_t elt = dbl ? sizeof(double2) : sizeof(float2);
+    void* spec_d = upload_async(db.ctx, specs.data(), specs.size() * sizeof(TabSpec), st);
+    if (!spec_d) return nullptr;
+    void* tab = db.add(nullptr, (size_t)batch * n * elt, st);
+    if (!tab) { free_async(db.ctx, spec_d); return nullptr; }
+    dim3 grid((n + 255) / 256, batch);
+    if (dbl) sep_table_kernel<double2><<<grid, 256, 0, db.ctx->stream>>>((double2*)tab, n, (const TabSpec*)spec_d);
+    else sep_table_kernel<float2><<<grid, 256, 0, db.ctx->stream>>>((float2*)tab, n, (const TabSpec*)spec_d);
+    cudaError_t e = cudaGetLastError();
+    free_async(db.ctx, spec_d);
+    if (e != cudaSuccess) { *st = cuda_fail(e, "sep_table_kernel"); return nullptr; }
+    return tab;
+}
+
+int clamp_thr(long long v) { return v > 0x3fffffffLL ? 0x3fffffff : (int)v; }
+
+// Noll index -> (n, m), m > 0 cosine, m < 0 sine (Noll 1976 ordering).
+void noll_nm(int j, int* n_out, int* m_out) {
+    int count = 0;
+    for (int n = 0;; ++n) {
+        for (int am = n % 2; am <= n; am += 2) {
+            if (am == 0) {
+                if (++count == j) { *n_out = n; *m_out = 0; return; }
+            } else {
+                const int first = count + 1, second = count + 2;
+                count += 2;
+                if (j == first || j == second) { *n_out = n; *m_out = (j % 2 == 0) ? am : -am; return; }
+            }
+        }
+    }
+}
+
+double factorial(int k) { double f = 1; for (int i = 2; i <= k; ++i) f *= i; return f; }
+
+// Combined Zernike polynomial table: A_m(rho^2) multiplies Re(z^m), B_m(rho^2) Im(z^m).
+bool zernike_table(const coro_element* el, std::vector<float>& out) {
+    std::vector<double> acc(2 * ZM * ZD, 0.0);
+    for (int i = 0; i < el->n_coeffs; ++i) {
+        int n, m;
+        noll_nm(el->j_first + i, &n, &m);
+        const int am = m < 0 ? -m : m;
+        if (am >= ZM || (n - am) / 2 >= ZD) return false;
+        const double norm = m == 0 ? std::sqrt((double)(n + 1)) : std::sqrt(2.0 * (n + 1));
+        double* dst = acc.data() + (m < 0 ? ZM * ZD : 0) + am * ZD;
+        for (int s = 0; s <= (n - am) / 2; ++s) {
+            const double a = ((s % 2) ? -1.0 : 1.0) * factorial(n - s)
+                             / (factorial(s) * factorial((n + am) / 2 - s) * factorial((n - am) / 2 - s));
+            dst[(n - am) / 2 - s] += el->coeffs[i] * norm * a;
+        }
+    }
+    out.assign(acc.begin(), acc.end());
+    return true;
+}
+
+// Compile one API element for a batch at the given per-item pixel scales.
+coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int n, int batch,
+                            const double* ps, const double* lam, DevElem* out) {
+    coro_status st = CORO_OK;
+    std::memset(out, 0, sizeof(DevElem));
+    std::vector<int> ithr((size_t)batch * 4, 0);
+    std::vector<float> fpar((size_t)batch * 4, 0.f);
+    switch (el->kind) {
+        case CORO_EL_APERTURE: {
+            if (!(el->radius > 0)) { set_error("aperture: radius must be > 0"); return CORO_EINVAL; }
+            if (el->n_spiders != 0 && el->n_spiders != 4) { set_error("aperture: n_spiders must be 0 or 4"); return CORO_ENOTIMPL; }
+            if (el->obscuration < 0 || el->obscuration >= 1) { set_error("aperture: obscuration in [0, 1)"); return CORO_EINVAL; }
+            for (int b = 0; b < batch; ++b) {
+                ithr[4 * b + 0] = clamp_thr(disk_threshold(el->radius, ps[b], false));
+                const double ro = el->obscuration * el->radius;
+                ithr[4 * b + 1] = el->obscuration > 0 ? clamp_thr(disk_threshold(ro, ps[b], true)) : -1;
+                ithr[4 * b + 2] = el->n_spiders ? clamp_thr(band_threshold(el->spider_width / 2.0, ps[b])) : -1;
+            }
+            out->kind = DK_APERTURE;
+            break;
+        }
+        case CORO_EL_CIRCLE: {
+            for (int b = 0; b < batch; ++b) ithr[4 * b] = clamp_thr(disk_threshold(el->radius, ps[b], false));
+            out->kind = DK_CIRCLE;
+            out->flags = (el->flags & CORO_ELF_OPAQUE_INSIDE) ? 1 : 0;
+            break;
+        }
+        case CORO_EL_LENS: {
+            if (el->focal_length == 0 || !std::isfinite(el->focal_length)) { set_error("lens: focal length must be finite and nonzero"); return CORO_EINVAL; }
+            std::vector<TabSpec> sp(batch);
+            for (int b = 0; b < batch; ++b)
+                sp[b] = TabSpec{ps[b] * ps[b] / (2.0 * lam[b] * el->focal_length), 1.0, 0.0, -1, 0};
+            out->tab = make_table(db, dbl, n, sp, &st);
+            if (!out->tab) return st;
+            out->kind = DK_TABLE;
+            return CORO_OK;
+        }
+        case CORO_EL_OPD_MAP: {
+            if (!el->opd) { set_error("opd map: opd pointer is NULL"); return CORO_EINVAL; }
+            for (int b = 0; b < batch; ++b) fpar[4 * b] = (float)(2.0 / lam[b]);
+            out->kind = DK_OPD_MAP;
+            out->map = el->opd;
+            out->amp = el->amplitude;
+            out->map_bstride = (el->flags & CORO_ELF_MAP_BATCHED) ? (long long)n * n : 0;
+            break;
+        }
+        case CORO_EL_ZERNIKE: {
+            if (!el->coeffs || el->n_coeffs < 1 || el->j_first < 1) { set_error("zernike: need coeffs, n_coeffs >= 1, j_first >= 1"); return CORO_EINVAL; }
+            if (!(el->radius > 0)) { set_error("zernike: radius must be > 0"); return CORO_EINVAL; }
+            std::vector<float> zt;
+            if (!zernike_table(el, zt)) { set_error("zernike: Noll index beyond 36 (radial order 7)"); return CORO_ENOTIMPL; }
+            for (int b = 0; b < batch; ++b) {
+                ithr[4 * b] = clamp_thr(disk_threshold(el->radius, ps[b], false));
+                fpar[4 * b] = (float)(2.0 / lam[b]);
+                fpar[4 * b + 1] = (float)(ps[b] / el->radius);
+            }
+            out->zpoly = (const float*)db.add(zt.data(), zt.size() * sizeof(float), &st);
+            if (!out->zpoly) return st;
+            out->kind = DK_ZERNIKE;
+            break;
+        }
+        case CORO_EL_SINE: {
+            for (int b = 0; b < batch; ++b) {
+                const double f = el->sine_freq * ps[b];                 // cycles per pixel
+                const double fhi = (double)(float)(std::ldexp(std::rint(std::ldexp(f, 11)), -11));
+                fpar[4 * b] = (float)(2.0 * el->sine_amplitude / lam[b]);
+                fpar[4 * b + 1] = (float)fhi;
+                fpar[4 * b + 2] = (float)(f - fhi);
+            }
+            out->kind = DK_SINE;
+            out->flags = el->axis ? 1 : 0;
+            break;
+        }
+        case CORO_EL_SCALAR: {
+            for (int b = 0; b < batch; ++b) fpar[4 * b] = (float)el->scalar;
+            out->kind = DK_SCALAR;
+            break;
+        }
+        default:
+            set_error("unknown element kind %d", el->kind);
+            return CORO_EINVAL;
+    }
+    out->ithr = (const int*)db.add(ithr.data(), ithr.size() * sizeof(int), &st);
+    if (!out->ithr) return st;
+    out->fpar = (const float*)db.add(fpar.data(), fpar.size() * sizeof(float), &st);
+    if (!out->fpar) return st;
+    return CORO_OK;
+}
+
+DevElem checker_elem() { DevElem e; std::memset(&e, 0, sizeof(e)); e.kind = DK_CHECKER; return e; }
+
+DevElem table_elem(const void* tab) { DevElem e; std::memset(&e, 0, sizeof(e)); e.kind = DK_TABLE; e.tab = tab; return e; }
+
+// ------------------------------------------------------------------------------ pass ops
+
+struct Op {
+    bool row = true;
+    int row_flags = 0;
+    int col_flags = 0;
+    PassElems elems{};
+    const void* tab_x = nullptr;
+    const void* tab_y = nullptr;
+    int lines = 0;
+};
+
+template <typename C>
+coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, void* field) {
+    coro_status st = CORO_OK;
+    const C* tw = (const C*)get_twiddles(ctx, n, sizeof(C) == sizeof(double2), &st);
+    if (!tw) return st;
+    PassLaunch pl{ctx->stream, batch};
+    for (const Op& op : ops) {
+        cudaError_t e;
+        if (op.row) {
+            RowArgs<C> a;
+            a.in = (const C*)field;
+            a.out = (C*)field;
+            a.tw = tw;
+            a.flags = op.row_flags;
+            a.elems = op.elems;
+            e = launch_row_pass<C>(n, a, pl);
+        } else {
+            ColArgs<C> a;
+            a.in = (const C*)field;
+            a.out = (C*)field;
+            a.tw = tw;
+            a.tab_x = (const C*)op.tab_x;
+            a.tab_y = (const C*)op.tab_y;
+            a.flags = op.col_flags;
+            e = launch_col_pass<C>(n, op.lines, a, pl);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, op.row ? "row pass" : "column pass");
+    }
+    return CORO_OK;
+}
+
+coro_status run_ops_any(coro_ctx ctx, int dtype, int n, int batch, const std::vector<Op>& ops, void* field) {
+    return dtype == CORO_C64 ? run_ops<float2>(ctx, n, batch, ops, field)
+                             : run_ops<double2>(ctx, n, batch, ops, field);
+}
+
+// ------------------------------------------------------------------------------ hop tables
+
+// Angular-spectrum transfer function per axis, 1/n folded in (1/n^2 overall for the IDFT).
+coro_status as_table(DevBlocks& db, bool dbl, int n, int batch, const double* ps, const double* lam,
+                     double z, const void** out) {
+    coro_status st = CORO_OK;
+    std::vector<TabSpec> sp(batch);
+    for (int b = 0; b < batch; ++b) {
+        const double L = n * ps[b];
+        sp[b] = TabSpec{lam[b] * z / (2.0 * L * L), 1.0 / n, 0.0, -1, 0};
+    }
+    *out = make_table(db, dbl, n, sp, &st);
+    return *out ? CORO_OK : st;
+}
+
+// Direct Fresnel: input QPF exp(+i pi x^2/(lambda z)); output QPF with (-1)^k folded in, the
+// y-table also carrying dx^2 / (i lambda z).
+coro_status direct_tables(DevBlocks& db, bool dbl, int n, int batch, const double* ps, const double* lam,
+                          double z, const void** qin, const void** qx, const void** qy, std::vector<double>& ps_out) {
+    coro_status st = CORO_OK;
+    std::vector<TabSpec> a(batch), bx(batch), by(batch);
+    ps_out.resize(batch);
+    for (int b = 0; b < batch; ++b) {
+        const double dx = ps[b];
+        const double du = lam[b] * z / (n * dx);
+        ps_out[b] = std::fabs(du);
+        a[b] = TabSpec{dx * dx / (2.0 * lam[b] * z), 1.0, 0.0, +1, 0};
+        bx[b] = TabSpec{du * du / (2.0 * lam[b] * z), 1.0, 0.0, +1, 1};
+        by[b] = TabSpec{du * du / (2.0 * lam[b] * z), 0.0, -dx * dx / (lam[b] * z), +1, 1};
+    }
+    if (!(*qin = make_table(db, dbl, n, a, &st))) return st;
+    if (!(*qx = make_table(db, dbl, n, bx, &st))) return st;
+    if (!(*qy = make_table(db, dbl, n, by, &st))) return st;
+    return CORO_OK;
+}
+
+coro_status sign_tables(DevBlocks& db, bool dbl, int n, int batch, double mag, const void** out) {
+    coro_status st = CORO_OK;
+    std::vector<TabSpec> sp(batch, TabSpec{0.0, mag, 0.0, 1, 1});
+    *out = make_table(db, dbl, n, sp, &st);
+    return *out ? CORO_OK : st;
+}
+
+}  // namespace
+
+// =========================================================================== a1: init
+
+namespace {
+template <typename C>
+__global__ void fill_kernel(C* p, size_t count, double amp) {
+    using R = typename real_of<C>::type;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = mk<C>((R)amp, (R)0);
+}
+}  // namespace
+
+extern "C" coro_status coro_wavefront_init(coro_ctx ctx, const coro_wavefront* wf, double amplitude) {
+    clear_error();
+    coro_status st = check_wf("coro_wavefront_init", ctx, wf, false);
+    if (st != CORO_OK) return st;
+    DeviceGuard g(ctx->device);
+    const size_t count = (size_t)wf->batch * wf->n * wf->n;
+    const int blocks = (int)std::min<size_t>((count + 255) / 256, 152 * 16);
+    if (wf->dtype == CORO_C64) fill_kernel<float2><<<blocks, 256, 0, ctx->stream>>>((float2*)wf->data, count, amplitude);
+    else fill_kernel<double2><<<blocks, 256, 0, ctx->stream>>>((double2*)wf->data, count, amplitude);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CORO_OK : cuda_fail(e, "fill_kernel");
+}
+
+// =========================================================================== a2/a3: elements
+
+extern "C" coro_status coro_apply_element(coro_ctx ctx, const coro_wavefront* wf, const coro_element* el) {
+    clear_error();
+    coro_status st = check_wf("coro_apply_element", ctx, wf);
+    if (st != CORO_OK) return st;
+    if (!el) { set_error("coro_apply_element: element is NULL"); return CORO_EINVAL; }
+    DeviceGuard g(ctx->device);
+    DevBlocks db;
+    db.ctx = ctx;
+    Op op;
+    op.row = true;
+    op.elems.count = 1;
+    st = compile_element(db, el, wf->dtype == CORO_C128, wf->n, wf->batch, wf->pixelscale, wf->wavelength, &op.elems.e[0]);
+    if (st == CORO_OK) st = run_ops_any(ctx, wf->dtype, wf->n, wf->batch, {op}, wf->data);
+    db.release();
+    return st;
+}
+
+// =========================================================================== a4-a6: Fresnel
+
+extern "C" coro_status coro_propagate_fresnel(coro_ctx ctx, coro_wavefront* wf, double z, int method) {
+    clear_error();
+    coro_status st = check_wf("coro_propagate_fresnel", ctx, wf);
+    if (st != CORO_OK) return st;
+    if (!(z != 0.0) || !std::isfinite(z)) { set_error("coro_propagate_fresnel: z must be finite and nonzero"); return CORO_EINVAL; }
+    if (method != CORO_FRESNEL_AS && method != CORO_FRESNEL_DIRECT) { set_error("coro_propagate_fresnel: bad method %d", method); return CORO_EINVAL; }
+    DeviceGuard g(ctx->device);
+    const bool dbl = wf->dtype == CORO_C128;
+    const int n = wf->n, batch = wf->batch;
+    DevBlocks db;
+    db.ctx = ctx;
+    std::vector<Op> ops;
+    std::vector<double> ps_out;
+    if (method == CORO_FRESNEL_AS) {
+        const void* h = nullptr;
+        st = as_table(db, dbl, n, batch, wf->pixelscale, wf->wavelength, z, &h);
+        if (st == CORO_OK) {
+            Op r0; r0.row = true; r0.row_flags = RF_FWD_AFTER; r0.elems.count = 1; r0.elems.e[0] = checker_elem();
+            Op c; c.row = false; c.col_flags = CF_FWD | CF_TABLE | CF_INV; c.tab_x = h; c.tab_y = h;
+            Op r1; r1.row = true; r1.row_flags = RF_INV_FIRST; r1.elems.count = 1; r1.elems.e[0] = checker_elem();
+            ops = {r0, c, r1};
+        }
+    } else {
+        const void *qin = nullptr, *qx = nullptr, *qy = nullptr;
+        st = direct_tables(db, dbl, n, batch, wf->pixelscale, wf->wavelength, z, &qin, &qx, &qy, ps_out);
+        if (st == CORO_OK) {
+            Op r0; r0.row = true; r0.row_flags = RF_FWD_AFTER; r0.elems.count = 2;
+            r0.elems.e[0] = table_elem(qin); r0.elems.e[1] = checker_elem();
+            Op c; c.row = false; c.col_flags = CF_FWD | CF_TABLE; c.tab_x = qx; c.tab_y = qy;
+            ops = {r0, c};
+        }
+    }
+    if (st == CORO_OK) st = run_ops_any(ctx, wf->dtype, n, batch, ops, wf->data);
+    db.release();
+    if (st == CORO_OK && method == CORO_FRESNEL_DIRECT)
+        for (int b = 0; b < batch; ++b) wf->pixelscale[b] = ps_out[b];
+    return st;
+}
+
+extern "C" coro_status coro_fft2(coro_ctx ctx, const coro_wavefront* wf, int direction) {
+    clear_error();
+    coro_status st = check_wf("coro_fft2", ctx, wf, false);
+    if (st != CORO_OK) return st;
+    if (direction != -1 && direction != 1) { set_error("coro_fft2: direction must be -1 or +1"); return CORO_EINVAL; }
+    DeviceGuard g(ctx->device);
+    const bool dbl = wf->dtype == CORO_C128;
+    DevBlocks db;
+    db.ctx = ctx;
+    const void* sgn = nullptr;
+    st = sign_tables(db, dbl, wf->n, wf->batch, direction < 0 ? 1.0 : 1.0 / wf->n, &sgn);
+    std::vector<Op> ops;
+    if (st == CORO_OK) {
+        if (direction < 0) {
+            Op r; r.row = true; r.row_flags = RF_FWD_AFTER; r.elems.count = 1; r.elems.e[0] = checker_elem();
+            Op c; c.row = false; c.col_flags = CF_FWD | CF_TABLE; c.tab_x = sgn; c.tab_y = sgn;
+            ops = {r, c};
+        } else {
+            Op c; c.row = false; c.col_flags = CF_TABLE | CF_INV; c.tab_x = sgn; c.tab_y = sgn;
+            Op r; r.row = true; r.row_flags = RF_INV_FIRST; r.elems.count = 1; r.elems.e[0] = checker_elem();
+            ops = {c, r};
+        }
+        st = run_ops_any(ctx, wf->dtype, wf->n, wf->batch, ops, wf->data);
+    }
+    db.release();
+    return st;
+}
+
+// =========================================================================== fused Fresnel plan
+
+struct coro_plan_s {
+    virtual ~coro_plan_s() {}
+    virtual int kind() const = 0;
+    virtual int launches() const = 0;
+};
+
+namespace {
+
+struct FresnelPlan : coro_plan_s {
+    coro_ctx ctx = nullptr;
+    int dtype = CORO_C64, n = 0, batch = 0;
+    std::vector<Op> ops;
+    DevBlocks db;
+    std::vector<double> ps_final;
+    int kind() const override { return 1; }
+    int launches() const override { return (int)ops.size(); }
+    ~FresnelPlan() override {
+        if (ctx) {
+            DeviceGuard g(ctx->device);
+            cudaStreamSynchronize(ctx->stream);
+            db.release();
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" coro_status coro_fresnel_plan_create(coro_ctx ctx, const coro_fresnel_desc* d, coro_plan* out) {
+    clear_error();
+    if (!ctx || !d || !out) { set_error("coro_fresnel_plan_create: NULL argument"); return CORO_EINVAL; }
+    *out = nullptr;
+    coro_wavefront probe{(void*)1, d->dtype, d->batch, d->n, const_cast<double*>(d->pixelscale), d->wavelength};
+    coro_status st = check_wf("coro_fresnel_plan_create", ctx, &probe);
+    if (st != CORO_OK) return st;
+    if (d->n_planes < 1) { set_error("coro_fresnel_plan_create: n_planes must be >= 1"); return CORO_EINVAL; }
+    if (d->n_planes > 1 && !d->distance) { set_error("coro_fresnel_plan_create: distance is NULL"); return CORO_EINVAL; }
+    if (d->n_elements < 0 || (d->n_elements > 0 && !d->elements)) { set_error("coro_fresnel_plan_create: bad element list"); return CORO_EINVAL; }
+    for (int p = 0; p + 1 < d->n_planes; ++p) {
+        if (!(d->distance[p] != 0.0) || !std::isfinite(d->distance[p])) { set_error("distance[%d] must be finite and nonzero", p); return CORO_EINVAL; }
+        const int m = d->method ? d->method[p] : CORO_FRESNEL_AS;
+        if (m != CORO_FRESNEL_AS && m != CORO_FRESNEL_DIRECT) { set_error("method[%d] = %d", p, m); return CORO_EINVAL; }
+    }
+    for (int i = 0; i < d->n_elements; ++i)
+        if (d->elements[i].plane < 0 || d->elements[i].plane >= d->n_planes) { set_error("element %d: plane %d out of range", i, d->elements[i].plane); return CORO_EINVAL; }
+
+    DeviceGuard g(ctx->device);
+    auto plan = std::unique_ptr<FresnelPlan>(new (std::nothrow) FresnelPlan);
+    if (!plan) { set_error("out of host memory"); return CORO_ENOMEM; }
+    plan->ctx = ctx;
+    plan->dtype = d->dtype;
+    plan->n = d->n;
+    plan->batch = d->batch;
+    plan->db.ctx = ctx;
+    plan->db.plan_owned = true;
+    const bool dbl = d->dtype == CORO_C128;
+    const int n = d->n, batch = d->batch;
+    std::vector<double> ps(d->pixelscale, d->pixelscale + batch);
+    const double* lam = d->wavelength;
+
+    enum { NATURAL, UNIFORM, SPECTRUM } state = (d->flags & CORO_PLAN_INIT_UNIFORM) ? UNIFORM : NATURAL;
+    for (int p = 0; p < d->n_planes; ++p) {
+        PassElems pe{};
+        for (int i = 0; i < d->n_elements; ++i) {
+            if (d->elements[i].plane != p) continue;
+            if (pe.count >= kMaxPassElems - 2) { set_error("plane %d: more than %d elements", p, kMaxPassElems - 2); return CORO_ENOTIMPL; }
+            st = compile_element(plan->db, &d->elements[i], dbl, n, batch, ps.data(), lam, &pe.e[pe.count]);
+            if (st != CORO_OK) return st;
+            ++pe.count;
+        }
+        Op r;
+        r.row = true;
+        r.elems = pe;
+        if (state == SPECTRUM) r.row_flags |= RF_INV_FIRST;
+        if (state == UNIFORM) r.row_flags |= RF_INIT_ONE;
+        if (p + 1 < d->n_planes) {
+            const int m = d->method ? d->method[p] : CORO_FRESNEL_AS;
+            const double z = d->distance[p];
+            r.row_flags |= RF_FWD_AFTER;
+            Op c;
+            c.row = false;
+            if (m == CORO_FRESNEL_AS) {
+                const void* h = nullptr;
+                if ((st = as_table(plan->db, dbl, n, batch, ps.data(), lam, z, &h)) != CORO_OK) return st;
+                if (state != SPECTRUM) r.elems.e[r.elems.count++] = checker_elem();
+                c.col_flags = CF_FWD | CF_TABLE | CF_INV;
+                c.tab_x = c.tab_y = h;
+                state = SPECTRUM;
+            } else {
+                const void *qin = nullptr, *qx = nullptr, *qy = nullptr;
+                std::vector<double> ps_next;
+                if ((st = direct_tables(plan->db, dbl, n, batch, ps.data(), lam, z, &qin, &qx, &qy, ps_next)) != CORO_OK) return st;
+                r.elems.e[r.elems.count++] = table_elem(qin);
+                if (state != SPECTRUM) r.elems.e[r.elems.count++] = checker_elem();
+                c.col_flags = CF_FWD | CF_TABLE;
+                c.tab_x = qx;
+                c.tab_y = qy;
+                ps = ps_next;
+                state = NATURAL;
+            }
+            plan->ops.push_back(r);
+            plan->ops.push_back(c);
+        } else {
+            if (state == SPECTRUM) r.elems.e[r.elems.count++] = checker_elem();
+            if (r.row_flags || r.elems.count) plan->ops.push_back(r);
+            state = NATURAL;
+        }
+    }
+    plan->ps_final = ps;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);   // tables ready; plan owns them
+    if (e != cudaSuccess) return cuda_fail(e, "coro_fresnel_plan_create");
+    *out = plan.release();
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_fresnel_plan_execute(coro_plan plan, void* field, double* pixelscale_out) {
+    clear_error();
+    if (!plan || plan->kind() != 1) { set_error("coro_fresnel_plan_execute: not a Fresnel plan"); return CORO_EINVAL; }
+    if (!field) { set_error("coro_fresnel_plan_execute: field is NULL"); return CORO_EINVAL; }
+    auto* p = static_cast<FresnelPlan*>(plan);
+    DeviceGuard g(p->ctx->device);
+    coro_status st = run_ops_any(p->ctx, p->dtype, p->n, p->batch, p->ops, field);
+    if (st == CORO_OK && pixelscale_out)
+        for (int b = 0; b < p->batch; ++b) pixelscale_out[b] = p->ps_final[b];
+    return st;
+}
+
+extern "C" coro_status coro_fresnel_plan_execute_range(coro_plan plan, void* field, int first, int count) {
+    clear_error();
+    if (!plan || plan->kind() != 1) { set_error("coro_fresnel_plan_execute_range: not a Fresnel plan"); return CORO_EINVAL; }
+    auto* p = static_cast<FresnelPlan*>(plan);
+    if (!field || first < 0 || count < 0 || first + count > (int)p->ops.size()) {
+        set_error("coro_fresnel_plan_execute_range: bad field or range [%d, %d) of %d", first, first + count, (int)p->ops.size());
+        return CORO_EINVAL;
+    }
+    DeviceGuard g(p->ctx->device);
+    std::vector<Op> sub(p->ops.begin() + first, p->ops.begin() + first + count);
+    return run_ops_any(p->ctx, p->dtype, p->n, p->batch, sub, field);
+}
+
+extern "C" coro_status coro_fresnel_plan_pass_info(coro_plan plan, int i, int* is_row, double* bytes) {
+    clear_error();
+    if (!plan || plan->kind() != 1 || !is_row || !bytes) { set_error("coro_fresnel_plan_pass_info: bad argument"); return CORO_EINVAL; }
+    auto* p = static_cast<FresnelPlan*>(plan);
+    if (i < 0 || i >= (int)p->ops.size()) { set_error("coro_fresnel_plan_pass_info: pass %d of %d", i, (int)p->ops.size()); return CORO_EINVAL; }
+    const Op& op = p->ops[i];
+    const double field = (double)p->batch * p->n * p->n * (p->dtype == CORO_C64 ? 8.0 : 16.0);
+    const double plane = (double)p->n * p->n * 4.0;
+    double b = field;                                   // write
+    if (!op.row || !(op.row_flags & RF_INIT_ONE)) b += field;   // read
+    if (op.row) {
+        for (int k = 0; k < op.elems.count; ++k) {
+            const DevElem& e = op.elems.e[k];
+            if (e.kind != DK_OPD_MAP) continue;
+            const double maps = e.map_bstride ? (double)p->batch : 1.0;
+            b += plane * maps * (e.amp ? 2.0 : 1.0);
+        }
+    }
+    *is_row = op.row ? 1 : 0;
+    *bytes = b;
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_plan_launch_count(coro_plan plan, int* out) {
+    clear_error();
+    if (!plan || !out) { set_error("coro_plan_launch_count: NULL argument"); return CORO_EINVAL; }
+    *out = plan->launches();
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_plan_destroy(coro_plan plan) {
+    clear_error();
+    delete plan;
+    return CORO_OK;
+}
+
+// =========================================================================== a9: detector
+
+namespace {
+
+template <typename C>
+__global__ void intensity_kernel(const C* __restrict__ e, float* __restrict__ out, size_t per_item,
+                                 int batch, const double* __restrict__ inv_norm) {
+    const size_t total = per_item * batch;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const C v = e[i];
+        const double s = inv_norm[i / per_item];
+        out[i] = (float)(((double)v.x * v.x + (double)v.y * v.y) * s);
+    }
+}
+
+// Dark-hole sum: one block row per item; pixels with lo <= r2 <= hi (integer radii squared).
+template <typename C>
+__global__ void darkhole_kernel(const C* __restrict__ e, int n, const long long* __restrict__ lohi,
+                                const double* __restrict__ inv_norm, double* __restrict__ acc) {
+    const int b = blockIdx.y;
+    const long long lo = lohi[2 * b], hi = lohi[2 * b + 1];
+    const C* f = e + (size_t)b * n * n;
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x) {
+        const long long kx = i % n - n / 2, ky = i / n - n / 2;
+        const long long r2 = kx * kx + ky * ky;
+        if (r2 >= lo && r2 <= hi) {
+            const C v = f[i];
+            s += (double)v.x * v.x + (double)v.y * v.y;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(acc + b, s * inv_norm[b]);
+    }
+}
+
+}  // namespace
+
+extern "C" coro_status coro_intensity(coro_ctx ctx, const coro_wavefront* wf, const double* norm, float* out) {
+    clear_error();
+    coro_status st = check_wf("coro_intensity", ctx, wf, false);
+    if (st != CORO_OK) return st;
+    if (!out) { set_error("coro_intensity: out is NULL"); return CORO_EINVAL; }
+    std::vector<double> inv(wf->batch, 1.0);
+    for (int b = 0; b < wf->batch && norm; ++b) {
+        if (!(norm[b] > 0)) { set_error("coro_intensity: norm[%d] must be > 0", b); return CORO_EINVAL; }
+        inv[b] = 1.0 / norm[b];
+    }
+    DeviceGuard g(ctx->device);
+    void* inv_d = upload_async(ctx, inv.data(), inv.size() * sizeof(double), &st);
+    if (!inv_d) return st;
+    const size_t per = (size_t)wf->n * wf->n;
+    const int blocks = (int)std::min<size_t>((per * wf->batch + 255) / 256, 152 * 8);
+    if (wf->dtype == CORO_C64) intensity_kernel<float2><<<blocks, 256, 0, ctx->stream>>>((const float2*)wf->data, out, per, wf->batch, (const double*)inv_d);
+    else intensity_kernel<double2><<<blocks, 256, 0, ctx->stream>>>((const double2*)wf->data, out, per, wf->batch, (const double*)inv_d);
+    cudaError_t e = cudaGetLastError();
+    free_async(ctx, inv_d);
+    return e == cudaSuccess ? CORO_OK : cuda_fail(e, "intensity_kernel");
+}
+
+extern "C" coro_status coro_darkhole_sum(coro_ctx ctx, const coro_wavefront* wf, const double* du, double r_in,
+                                         double r_out, const double* norm, double* host_out) {
+    clear_error();
+    coro_status st = check_wf("coro_darkhole_sum", ctx, wf, false);
+    if (st != CORO_OK) return st;
+    if (!du || !host_out) { set_error("coro_darkhole_sum: du/host_out is NULL"); return CORO_EINVAL; }
+    if (!(r_in >= 0) || !(r_out >= r_in)) { set_error("coro_darkhole_sum: need 0 <= r_in <= r_out"); return CORO_EINVAL; }
+    const int batch = wf->batch;
+    std::vector<long long> lohi(2 * batch);
+    std::vector<double> inv(batch, 1.0);
+    for (int b = 0; b < batch; ++b) {
+        if (!(du[b] > 0)) { set_error("coro_darkhole_sum: du[%d] must be > 0", b); return CORO_EINVAL; }
+        if (norm) {
+            if (!(norm[b] > 0)) { set_error("coro_darkhole_sum: norm[%d] must be > 0", b); return CORO_EINVAL; }
+            inv[b] = 1.0 / norm[b];
+        }
+        // lo = smallest m with m du^2 >= r_in^2 = (largest m with m du^2 < r_in^2) + 1
+        lohi[2 * b] = disk_threshold(r_in, du[b], true) + 1;
+        lohi[2 * b + 1] = disk_threshold(r_out, du[b], false);
+    }
+    DeviceGuard g(ctx->device);
+    void* lohi_d = upload_async(ctx, lohi.data(), lohi.size() * sizeof(long long), &st);
+    if (!lohi_d) return st;
+    void* inv_d = upload_async(ctx, inv.data(), inv.size() * sizeof(double), &st);
+    void* acc_d = inv_d ? upload_async(ctx, nullptr, batch * sizeof(double), &st) : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (acc_d) {
+        e = cudaMemsetAsync(acc_d, 0, batch * sizeof(double), ctx->stream);
+        const int n = wf->n;
+        dim3 grid((unsigned)std::min(64, (n * n + 255) / 256), batch);
+        if (e == cudaSuccess) {
+            if (wf->dtype == CORO_C64) darkhole_kernel<float2><<<grid, 256, 0, ctx->stream>>>((const float2*)wf->data, n, (const long long*)lohi_d, (const double*)inv_d, (double*)acc_d);
+            else darkhole_kernel<double2><<<grid, 256, 0, ctx->stream>>>((const double2*)wf->data, n, (const long long*)lohi_d, (const double*)inv_d, (double*)acc_d);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, acc_d, batch * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "coro_darkhole_sum");
+    }
+    free_async(ctx, lohi_d);
+    free_async(ctx, inv_d);
+    free_async(ctx, acc_d);
+    return st;
+}

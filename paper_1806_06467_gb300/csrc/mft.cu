@@ -1,0 +1,121 @@
+// mft.cu -- matrix Fourier transform (Sec. 1.1: the semi-analytic coronagraph method of
+// Soummer et al. uses "discrete matrix Fourier transforms of modest sized arrays"; Sec. 2.3:
+// the "sines and cosines ... needed in the matrix DFT").
+//
+//   out = s * A_y . in . A_x^T,   A[u][j] = exp(-+ 2 pi i X_j U_u)
+//
+// evaluated as two batched complex GEMMs. The bases are generated on the device in FP64
+// (the phase X_j U_u = j' u' du / npix is an exact integer times one FP64 constant, reduced
+// to its fractional cycle before sincospi) and rounded to complex64.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "capi_common.h"
+#include "fft_engine.cuh"
+#include "mft_gemm.cuh"
+
+using namespace coro;
+
+namespace {
+
+// basis[b][u][j] = exp(sign 2 pi i (j - n/2)(u - m/2) c_b), c_b = du_b / npix.
+__global__ void mft_basis_kernel(float2* basis, int m, int n, const double* __restrict__ c, int sign) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int u = blockIdx.y;
+    const int b = blockIdx.z;
+    if (j >= n) return;
+    const long long jj = (long long)j - n / 2, uu = (long long)u - m / 2;
+    double cyc = (double)(jj * uu) * c[b];
+    cyc -= rint(cyc);
+    double s, co;
+    sincospi(2.0 * cyc, &s, &co);
+    if (sign < 0) s = -s;
+    basis[((size_t)b * m + u) * n + j] = make_float2((float)co, (float)s);
+}
+
+coro_status check_mft_wf(const char* fn, const coro_wavefront* wf) {
+    if (!wf || !wf->data) { coro::set_error("%s: wavefront or data is NULL", fn); return CORO_EINVAL; }
+    if (wf->dtype != CORO_C64) { coro::set_error("%s: the MFT is implemented for complex64 fields", fn); return CORO_ENOTIMPL; }
+    if (wf->batch < 1 || wf->batch > 65535) { coro::set_error("%s: batch %d", fn, wf->batch); return CORO_ESIZE; }
+    if (wf->n < 1 || wf->n > 8192) { coro::set_error("%s: size %d outside [1, 8192]", fn, wf->n); return CORO_ESIZE; }
+    return CORO_OK;
+}
+
+}  // namespace
+
+extern "C" coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in, double npix, int direction,
+                                          int m, const double* du, int precision, coro_wavefront* out) {
+    coro::clear_error();
+    if (!ctx) { coro::set_error("coro_propagate_mft: ctx is NULL"); return CORO_EINVAL; }
+    coro_status st = check_mft_wf("coro_propagate_mft(in)", in);
+    if (st != CORO_OK) return st;
+    if ((st = check_mft_wf("coro_propagate_mft(out)", out)) != CORO_OK) return st;
+    if (direction != -1 && direction != 1) { coro::set_error("coro_propagate_mft: direction must be -1 or +1"); return CORO_EINVAL; }
+    if (!(npix > 0)) { coro::set_error("coro_propagate_mft: npix must be > 0"); return CORO_EINVAL; }
+    if (!du) { coro::set_error("coro_propagate_mft: du is NULL"); return CORO_EINVAL; }
+    if (out->batch != in->batch) { coro::set_error("coro_propagate_mft: batch mismatch"); return CORO_EINVAL; }
+    if (out->n != m) { coro::set_error("coro_propagate_mft: out->n (%d) must equal m (%d)", out->n, m); return CORO_EINVAL; }
+    if (precision != CORO_MFT_FP32 && precision != CORO_MFT_3XTF32 && precision != CORO_MFT_3XBF16) {
+        coro::set_error("coro_propagate_mft: bad precision %d", precision);
+        return CORO_EINVAL;
+    }
+    const int batch = in->batch;
+    std::vector<double> c(batch);
+    for (int b = 0; b < batch; ++b) {
+        if (!(du[b] > 0) || !std::isfinite(du[b])) { coro::set_error("coro_propagate_mft: du[%d] must be > 0", b); return CORO_EINVAL; }
+        c[b] = du[b] / npix;
+    }
+    coro::DeviceGuard g(ctx->device);
+    // focal-plane side has m (forward) or in->n (inverse) samples; pupil side the other
+    const int nf = direction < 0 ? m : in->n;     // focal samples per axis
+    const int np = direction < 0 ? in->n : m;     // pupil samples per axis
+    const size_t basis_elems = (size_t)batch * nf * np;
+    const size_t t_elems = (size_t)batch * (direction < 0 ? (size_t)np * nf : (size_t)nf * np);
+    float2* work = (float2*)coro::ctx_work(ctx, (basis_elems + t_elems) * sizeof(float2), &st);
+    if (!work) return st;
+    float2* basis = work;
+    float2* tmp = work + basis_elems;
+    void* c_d = coro::upload_async(ctx, c.data(), c.size() * sizeof(double), &st);
+    if (!c_d) return st;
+    dim3 bg((np + 127) / 128, nf, batch);
+    mft_basis_kernel<<<bg, 128, 0, ctx->stream>>>(basis, nf, np, (const double*)c_d, direction < 0 ? -1 : 1);
+    cudaError_t e = cudaGetLastError();
+    coro::free_async(ctx, c_d);
+    if (e != cudaSuccess) return coro::cuda_fail(e, "mft_basis_kernel");
+
+    const float2* x = (const float2*)in->data;
+    float2* y = (float2*)out->data;
+    const long long sb = (long long)nf * np;   // basis batch stride
+    GemmDesc g1{}, g2{};
+    if (direction < 0) {
+        // T[i][u] = sum_j in[i][j] A[u][j]            (M = np, N = nf, K = np)
+        g1 = GemmDesc{np, nf, np, x, (long long)np * np, np, false, basis, sb, np, true,
+                      tmp, (long long)np * nf, nf, 1.0f};
+        // out[v][u] = s sum_i A[v][i] T[i][u]         (M = nf, N = nf, K = np)
+        g2 = GemmDesc{nf, nf, np, basis, sb, np, false, tmp, (long long)np * nf, nf, false,
+                      y, (long long)nf * nf, nf, 0.0f};
+    } else {
+        // T[v][j] = sum_u in[v][u] B[u][j]            (M = nf, N = np, K = nf)
+        g1 = GemmDesc{nf, np, nf, x, (long long)nf * nf, nf, false, basis, sb, np, false,
+                      tmp, (long long)nf * np, np, 1.0f};
+        // out[i][j] = s sum_v B[v][i] T[v][j]         (M = np, N = np, K = nf)
+        g2 = GemmDesc{np, np, nf, basis, sb, np, true, tmp, (long long)nf * np, np, false,
+                      y, (long long)np * np, np, 0.0f};
+    }
+    std::vector<float> scale(batch);
+    for (int b = 0; b < batch; ++b) scale[b] = (float)c[b];
+    void* s_d = coro::upload_async(ctx, scale.data(), batch * sizeof(float), &st);
+    if (!s_d) return st;
+    g2.scale_per_item = (const float*)s_d;
+    e = launch_cgemm(g1, batch, precision, ctx->stream);
+    if (e == cudaSuccess) e = launch_cgemm(g2, batch, precision, ctx->stream);
+    coro::free_async(ctx, s_d);
+    if (e == cudaErrorNotSupported) {
+        coro::set_error("coro_propagate_mft: precision %d is not available in this build", precision);
+        return CORO_ENOTIMPL;
+    }
+    if (e != cudaSuccess) return coro::cuda_fail(e, "mft gemm");
+    return CORO_OK;
+}

@@ -1,0 +1,296 @@
+// passes.cuh -- the two HBM passes of a 2-D FFT with fused pointwise work.
+//
+// A Fresnel hop (Sec. 1.1) is E -> IDFT2[H . DFT2[E]] with H separable, H = h(kx) h(ky).
+// Written as row and column 1-D transforms, consecutive hops fuse into two passes per hop:
+//   row pass     load -> [IFFT rows] -> elements (Eq. 3 phasors, masks, lens) -> [FFT rows] -> store
+//   column pass  load -> [FFT cols] -> * tab_x[col] tab_y[row] -> [IFFT cols] -> store
+// The fftshift of the centred DFT is folded in as a (-1)^(x+y) sign flip (Sec. 2.4: the paper
+// moved fftshift to the GPU; here it costs no memory pass at all).
+#pragma once
+#include "fft_engine.cuh"
+
+namespace coro {
+
+// ------------------------------------------------------------------------------ elements
+
+enum DevElemKind : int {
+    DK_NONE = 0,
+    DK_APERTURE = 1,   // ithr: [outer r2 max, obscuration r2 max (-1 none), spider |k| max (-1 none)]
+    DK_CIRCLE = 2,     // ithr: [r2 max]; flags bit0: opaque inside
+    DK_TABLE = 3,      // separable table tab[b][x] * tab[b][y] (lens, QPF)
+    DK_OPD_MAP = 4,    // fpar: [2 / lambda]; map [n][n] or [b][n][n]; optional amplitude
+    DK_ZERNIKE = 5,    // ithr: [r2 max]; fpar: [2 / lambda, dx/R]; zpoly: combined polynomials
+    DK_SINE = 6,       // fpar: [2 amp / lambda, f_hi, f_lo] (cycles per pixel split), flags: axis
+    DK_SCALAR = 7,     // fpar: [s]
+    DK_CHECKER = 8     // (-1)^(x+y)
+};
+
+// Zernike evaluation table: OPD = sum_{m=0}^{ZM-1} A_m(rho^2) Re(z^m) + B_m(rho^2) Im(z^m),
+// z = (x + i y)/R, A_m and B_m polynomials of degree < ZD in rho^2 (coefficients in metres).
+constexpr int ZM = 8;
+constexpr int ZD = 4;
+
+struct DevElem {
+    int kind;
+    int flags;
+    const int* ithr;          // [batch][4] integer thresholds
+    const float* fpar;        // [batch][4] float parameters
+    const void* tab;          // [batch][n] complex separable table
+    const float* map;         // OPD map
+    const float* amp;         // amplitude map (nullable)
+    long long map_bstride;    // 0 (shared) or n*n
+    const float* zpoly;       // [2][ZM][ZD]
+};
+
+constexpr int kMaxPassElems = 6;
+
+struct PassElems {
+    int count;
+    DevElem e[kMaxPassElems];
+};
+
+// Multiply the 16 samples a thread holds (row y of item b, columns x0 + s*XS) by every
+// element of the list. The element loop is outermost and uniform across the block.
+template <typename C, int N, int XS>
+__device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, const PassElems& pe) {
+    using R = typename real_of<C>::type;
+    const int ky = y - N / 2;
+    for (int i = 0; i < pe.count; ++i) {
+        const DevElem& e = pe.e[i];
+        switch (e.kind) {
+            case DK_APERTURE: {
+                const int* th = e.ithr + 4 * b;
+                const int t0 = th[0], t1 = th[1], t2 = th[2];
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int kx = x0 + s * XS - N / 2;
+                    const int r2 = kx * kx + ky * ky;
+                    bool pass = r2 <= t0;
+                    if (t1 >= 0 && r2 <= t1) pass = false;
+                    if (t2 >= 0 && (abs(kx) <= t2 || abs(ky) <= t2)) pass = false;
+                    if (!pass) v[s] = mk<C>(0, 0);
+                }
+                break;
+            }
+            case DK_CIRCLE: {
+                const int t0 = e.ithr[4 * b];
+                const bool opaque_inside = e.flags & 1;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int kx = x0 + s * XS - N / 2;
+                    const bool inside = kx * kx + ky * ky <= t0;
+                    if (inside == opaque_inside) v[s] = mk<C>(0, 0);
+                }
+                break;
+            }
+            case DK_TABLE: {
+                const C* t = reinterpret_cast<const C*>(e.tab) + (size_t)b * N;
+                const C ty = t[y];
+#pragma unroll
+                for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], cmul(__ldg(t + x0 + s * XS), ty));
+                break;
+            }
+            case DK_OPD_MAP: {
+                const float k = e.fpar[4 * b];
+                const size_t off = (size_t)b * e.map_bstride + (size_t)y * N + x0;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    // phase / pi = (2 / lambda) * OPD
+                    const float ph = k * __ldg(e.map + off + s * XS);
+                    float sn, cs;
+                    sincospif(ph, &sn, &cs);
+                    R am = 1;
+                    if (e.amp) am = (R)__ldg(e.amp + off + s * XS);
+                    v[s] = cmul(v[s], mk<C>(am * (R)cs, am * (R)sn));
+                }
+                break;
+            }
+            case DK_ZERNIKE: {
+                const int t0 = e.ithr[4 * b];
+                const float k = e.fpar[4 * b], sc = e.fpar[4 * b + 1];
+                const float zy = ky * sc;
+#pragma unroll 4
+                for (int s = 0; s < 16; ++s) {
+                    const int kx = x0 + s * XS - N / 2;
+                    if (kx * kx + ky * ky > t0) continue;   // zero OPD outside the disk
+                    const float zx = kx * sc;
+                    const float rho2 = zx * zx + zy * zy;
+                    float pr = 1.f, pim = 0.f, opd = 0.f;
+#pragma unroll
+                    for (int m = 0; m < ZM; ++m) {
+                        const float* A = e.zpoly + m * ZD;
+                        const float* Bc = e.zpoly + ZM * ZD + m * ZD;
+                        float a = A[ZD - 1], bb = Bc[ZD - 1];
+#pragma unroll
+                        for (int d = ZD - 2; d >= 0; --d) { a = fmaf(a, rho2, A[d]); bb = fmaf(bb, rho2, Bc[d]); }
+                        opd += a * pr + bb * pim;
+                        const float nr = pr * zx - pim * zy;
+                        pim = pr * zy + pim * zx;
+                        pr = nr;
+                    }
+                    float sn, cs;
+                    sincospif(k * opd, &sn, &cs);
+                    v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
+                }
+                break;
+            }
+            case DK_SINE: {
+                const float* p = e.fpar + 4 * b;
+                const bool along_y = e.flags & 1;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int kk = along_y ? ky : x0 + s * XS - N / 2;
+                    // cycles = kk * f with f = f_hi + f_lo and kk * f_hi exact in FP32
+                    float a = (float)kk * p[1];
+                    a -= rintf(a);
+                    a += (float)kk * p[2];
+                    float sn, cs;
+                    sincospif(p[0] * sinpif(2.f * a), &sn, &cs);
+                    v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
+                }
+                break;
+            }
+            case DK_SCALAR: {
+                const R sc = (R)e.fpar[4 * b];
+#pragma unroll
+                for (int s = 0; s < 16; ++s) v[s] = cscale(v[s], sc);
+                break;
+            }
+            case DK_CHECKER: {
+#pragma unroll
+                for (int s = 0; s < 16; ++s)
+                    if ((x0 + s * XS + y) & 1) v[s] = mk<C>(-v[s].x, -v[s].y);
+                break;
+            }
+            default:
+                break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ row pass
+
+enum RowFlags : int {
+    RF_INV_FIRST = 1,     // inverse row FFT before the elements
+    RF_FWD_AFTER = 2,     // forward row FFT after the elements
+    RF_INIT_ONE = 4       // do not read: the field starts as 1 + 0i
+};
+
+template <typename C>
+struct RowArgs {
+    const C* in;
+    C* out;
+    const C* tw;          // twiddles for N
+    int flags;
+    PassElems elems;
+};
+
+template <int N> struct RowCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int L0 = TPL >= 256 ? 1 : 256 / TPL;
+    static constexpr int L = L0 < N ? L0 : N;                      // lines per block
+    static constexpr int THREADS = TPL * L;
+    static constexpr int STRIDE = LineGeom<N>::STRIDE;
+};
+
+// grid: (N / L, batch); one block = L consecutive rows of one item.
+template <typename C, int N>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS)
+row_pass_kernel(const __grid_constant__ RowArgs<C> a) {
+    using Cfg = RowCfg<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* smem = reinterpret_cast<C*>(smem_raw);
+    const int line = threadIdx.x / Cfg::TPL;
+    const int t = threadIdx.x % Cfg::TPL;
+    const int b = blockIdx.y;
+    const int y = blockIdx.x * Cfg::L + line;
+    C* buf = smem + line * Cfg::STRIDE;
+    const size_t row_off = ((size_t)b * N + y) * N;
+
+    C v[16];
+    if (a.flags & RF_INIT_ONE) {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) v[s] = mk<C>(1, 0);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) v[s] = a.in[row_off + t + s * Cfg::TPL];
+    }
+    if (a.flags & RF_INV_FIRST) line_fft<C, N, true>(v, buf, t, a.tw);
+    if (a.elems.count) apply_elems<C, N, Cfg::TPL>(v, t, y, b, a.elems);
+    if (a.flags & RF_FWD_AFTER) line_fft<C, N, false>(v, buf, t, a.tw);
+#pragma unroll
+    for (int s = 0; s < 16; ++s) a.out[row_off + t + s * Cfg::TPL] = v[s];
+}
+
+// ------------------------------------------------------------------------------ column pass
+
+enum ColFlags : int {
+    CF_FWD = 1,           // forward column FFT first
+    CF_INV = 2,           // inverse column FFT last
+    CF_TABLE = 4          // multiply by tab_x[b][col] * tab_y[b][row] between them
+};
+
+template <typename C>
+struct ColArgs {
+    const C* in;
+    C* out;
+    const C* tw;
+    const C* tab_x;       // [batch][N]
+    const C* tab_y;       // [batch][N]
+    int flags;
+};
+
+template <int N, int L> struct ColCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int THREADS = TPL * L;
+    // column c's region starts at c * STRIDE; STRIDE = 16/L (mod 16) spreads the L columns a
+    // half-warp touches over distinct banks.
+    static constexpr int STRIDE = LineGeom<N>::STRIDE + ((16 / L) & 15);
+};
+
+// grid: (N / L, batch); one block = L adjacent columns of one item. Thread (t, c) = t*L + c,
+// so a warp reads 32/L rows x L contiguous columns.
+template <typename C, int N, int L>
+__global__ void __launch_bounds__(ColCfg<N, L>::THREADS)
+col_pass_kernel(const __grid_constant__ ColArgs<C> a) {
+    using Cfg = ColCfg<N, L>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* smem = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % L;
+    const int t = threadIdx.x / L;
+    const int b = blockIdx.y;
+    const int col = blockIdx.x * L + c;
+    C* buf = smem + c * Cfg::STRIDE;
+    const size_t base = (size_t)b * N * N + col;
+
+    C v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = a.in[base + (size_t)(t + s * Cfg::TPL) * N];
+    if (a.flags & CF_FWD) line_fft<C, N, false>(v, buf, t, a.tw);
+    if (a.flags & CF_TABLE) {
+        const C hx = a.tab_x[(size_t)b * N + col];
+        const C* ty = a.tab_y + (size_t)b * N;
+#pragma unroll
+        for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], cmul(hx, ty[t + s * Cfg::TPL]));
+    }
+    if (a.flags & CF_INV) line_fft<C, N, true>(v, buf, t, a.tw);
+#pragma unroll
+    for (int s = 0; s < 16; ++s) a.out[base + (size_t)(t + s * Cfg::TPL) * N] = v[s];
+}
+
+// ------------------------------------------------------------------------------ launchers
+
+struct PassLaunch {
+    cudaStream_t stream;
+    int batch;
+};
+
+// Implemented per precision in passes_f32.cu / passes_f64.cu.
+template <typename C>
+cudaError_t launch_row_pass(int n, const RowArgs<C>& a, const PassLaunch& l);
+template <typename C>
+cudaError_t launch_col_pass(int n, int lines, const ColArgs<C>& a, const PassLaunch& l);
+// Supported column widths for a given n (first = default).
+int col_lines_default(int n, bool dbl);
+
+}  // namespace coro

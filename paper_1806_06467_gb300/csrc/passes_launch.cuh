@@ -1,0 +1,50 @@
+// passes_launch.cuh -- instantiation and launch of the row/column pass kernels for one
+// complex type. Included once per precision (passes_f32.cu, passes_f64.cu).
+#pragma once
+#include "passes.cuh"
+
+namespace coro {
+namespace detail {
+
+// Raise the dynamic shared-memory limit of a kernel once per device.
+template <typename K>
+inline cudaError_t ensure_smem(K kernel, size_t bytes, unsigned& done_mask) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned bit = 1u << (dev & 31);
+    if (done_mask & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done_mask |= bit;
+    return e;
+}
+
+template <typename C, int N>
+cudaError_t row_launch(const RowArgs<C>& a, const PassLaunch& l) {
+    using Cfg = RowCfg<N>;
+    static unsigned done = 0;
+    // without a transform the shared exchange buffer is never touched
+    const bool fft = a.flags & (RF_INV_FIRST | RF_FWD_AFTER);
+    const size_t smem = fft ? (size_t)Cfg::L * Cfg::STRIDE * sizeof(C) : 0;
+    cudaError_t e = ensure_smem(row_pass_kernel<C, N>, smem, done);
+    if (e != cudaSuccess) return e;
+    dim3 grid(N / Cfg::L, l.batch);
+    row_pass_kernel<C, N><<<grid, Cfg::THREADS, smem, l.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename C, int N, int L>
+cudaError_t col_launch(const ColArgs<C>& a, const PassLaunch& l) {
+    using Cfg = ColCfg<N, L>;
+    static unsigned done = 0;
+    const size_t smem = (size_t)L * Cfg::STRIDE * sizeof(C);
+    cudaError_t e = ensure_smem(col_pass_kernel<C, N, L>, smem, done);
+    if (e != cudaSuccess) return e;
+    dim3 grid(N / L, l.batch);
+    col_pass_kernel<C, N, L><<<grid, Cfg::THREADS, smem, l.stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace detail
+}  // namespace coro

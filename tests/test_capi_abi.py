@@ -1,0 +1,59 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every entry point the header
+declares, and rejects bad arguments on the host without touching a GPU."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "coro.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:coro_status|const char\*|int)\s+(coro_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def dll():
+    from paper_1806_06467_gb300 import build, coro
+    build.build()
+    return coro.Library(coro.LIB_PATH)
+
+
+def test_every_declared_symbol_is_exported(dll):
+    syms = header_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(dll.dll, s), s
+
+
+def test_binding_covers_header(dll):
+    from paper_1806_06467_gb300 import coro
+    assert set(header_symbols()) == set(coro.declared_symbols())
+
+
+def test_version_and_error_string(dll):
+    assert dll.coro_version() == 1
+    assert isinstance(dll.coro_last_error(), bytes)
+
+
+def test_host_side_argument_checks(dll):
+    from paper_1806_06467_gb300 import coro
+    # NULL out pointer is rejected before any CUDA call
+    assert dll.coro_ctx_create(0, None, None) == coro.EINVAL
+    assert b"NULL" in dll.coro_last_error()
+    # a NULL context is rejected by every compute entry point
+    w = coro.Wavefront(1, coro.C64, 1, 64, None, None)
+    assert dll.coro_wavefront_init(None, ct.byref(w), 1.0) == coro.EINVAL
+    assert dll.coro_propagate_fresnel(None, ct.byref(w), 1.0, 0) == coro.EINVAL
+    assert dll.coro_plan_destroy(None) == coro.OK
+
+
+def test_no_device_reports_ecuda(dll):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1806_06467_gb300 import coro
+    h = ct.c_void_p()
+    assert dll.coro_ctx_create(0, None, ct.byref(h)) == coro.ECUDA

@@ -1,0 +1,297 @@
+"""GPU parity: centred 2-D DFT, Fresnel hops, elements and the fused Fresnel plan against
+the FP64 oracle, element by element, through the C ABI.
+
+Tolerance: relative L2 field error <= 1e-5 for complex64 and <= 1e-12 for complex128. Binary
+masks are compared exactly (which samples are zeroed).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import optics, propagation
+from paper_1806_06467_gb300 import coro, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.complex64: 1e-5, torch.complex128: 1e-12}
+EPS64 = np.finfo(np.float64).eps
+
+
+def tol(dtype, phase_max=0.0):
+    """complex64: 1e-5. complex128: 1e-12, widened by the rounding the FP64 oracle itself
+    commits when it evaluates a quadratic phase of magnitude phase_max (Sec. 2.3: these
+    arguments reach 1e6-1e7 rad), i.e. a few eps * |phase|."""
+    if dtype == torch.complex64:
+        return TOL[dtype]
+    return TOL[dtype] + 8 * EPS64 * phase_max
+
+
+def rel_l2(got, ref):
+    got = np.asarray(got, dtype=np.complex128)
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def to_dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda().contiguous()
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    return coro.Context(0)
+
+
+SIZES = [32, 64, 128, 256, 512, 1024, 2048]
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+@pytest.mark.parametrize("n", SIZES)
+def test_centred_dft_forward_inverse(ctx, n, dtype):
+    batch = 2
+    f = inputs.random_field((batch, n, n), seed=n)
+    x = to_dev(f, dtype)
+    coro.fft2(ctx, x, -1)
+    ref = propagation.centred_dft2(f)
+    assert rel_l2(x.cpu().numpy(), ref) < TOL[dtype]
+    coro.fft2(ctx, x, +1)
+    assert rel_l2(x.cpu().numpy(), f) < TOL[dtype]
+
+
+@pytest.mark.parametrize("n", [4096, 8192])
+def test_centred_dft_large(ctx, n):
+    f = inputs.random_field((1, n, n), seed=7)
+    x = to_dev(f, torch.complex64)
+    coro.fft2(ctx, x, -1)
+    assert rel_l2(x.cpu().numpy(), propagation.centred_dft2(f)) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+@pytest.mark.parametrize("n", [64, 256, 1024])
+def test_angular_spectrum_hop(ctx, n, dtype):
+    lams = np.array([500e-9, 600e-9])
+    dxs = np.array([1.0 / 200, 1.3 / 200])
+    f = inputs.random_field((2, n, n), seed=3 * n)
+    x = to_dev(f, dtype)
+    ps = coro.propagate_fresnel(ctx, x, dxs, lams, 2.7, coro.FRESNEL_AS)
+    np.testing.assert_array_equal(ps, dxs)
+    got = x.cpu().numpy()
+    for b in range(2):
+        ref = propagation.angular_spectrum(f[b], dxs[b], lams[b], 2.7)
+        assert rel_l2(got[b], ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+@pytest.mark.parametrize("n", [64, 512])
+def test_direct_fresnel_hop(ctx, n, dtype):
+    lams = np.array([500e-9, 550e-9])
+    dx = 1.0 / 128
+    f = inputs.random_field((2, n, n), seed=5 * n)
+    x = to_dev(f, dtype)
+    ps = coro.propagate_fresnel(ctx, x, dx, lams, -3.5, coro.FRESNEL_DIRECT)
+    got = x.cpu().numpy()
+    for b in range(2):
+        ref, du = propagation.direct_fresnel(f[b], dx, lams[b], -3.5)
+        assert abs(ps[b] - abs(du)) < 1e-15 * abs(du)
+        r2max = 2 * (n / 2) ** 2 * max(dx, abs(du)) ** 2
+        assert rel_l2(got[b], ref) < tol(dtype, np.pi * r2max / (lams[b] * 3.5))
+
+
+def apply(ctx, n, dtype, el, dx=1.0 / 300, lam=550e-9, batch=1, seed=0):
+    f = inputs.random_field((batch, n, n), seed=seed)
+    x = to_dev(f, dtype)
+    coro.apply_element(ctx, x, dx, lam, el)
+    return f, x.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_aperture_mask_exact(ctx, n):
+    dx = 1.0 / (n // 2 - 1)   # a pitch with no exact binary representation
+    el = coro.element(coro.EL_APERTURE, radius=0.5, obscuration=0.3, n_spiders=4, spider_width=0.01)
+    f, got = apply(ctx, n, torch.complex64, el, dx=dx)
+    mask = optics.circular_aperture(n, dx, 0.5, 0.3, 4, 0.01)
+    np.testing.assert_array_equal(got[0] == 0, mask == 0)
+    np.testing.assert_array_equal(got[0][mask == 1], f[0][mask == 1].astype(np.complex64))
+
+
+@pytest.mark.parametrize("opaque", [False, True])
+def test_circle_stop_exact(ctx, opaque):
+    n, dx = 512, 1.0 / 200
+    el = coro.element(coro.EL_CIRCLE, radius=0.45, flags=coro.ELF_OPAQUE_INSIDE if opaque else 0)
+    f, got = apply(ctx, n, torch.complex64, el, dx=dx)
+    mask = optics.circle_stop(n, dx, 0.45, opaque_inside=opaque)
+    np.testing.assert_array_equal(got[0] == 0, mask == 0)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_lens(ctx, dtype):
+    n, dx, lam, fl = 1024, 1.0 / 400, 550e-9, 5.0
+    f, got = apply(ctx, n, dtype, coro.element(coro.EL_LENS, focal_length=fl), dx=dx, lam=lam)
+    ref = f[0] * optics.thin_lens(n, dx, lam, fl)
+    phase_max = np.pi * 2 * (n / 2 * dx) ** 2 / (lam * fl)
+    assert rel_l2(got[0], ref) < (2e-7 if dtype == torch.complex64 else tol(dtype, phase_max))
+
+
+def test_opd_map_and_amplitude(ctx):
+    n, lam = 256, 600e-9
+    opd = inputs.psd_surface(n, 4) * 10
+    amp = inputs.rng(2).uniform(0.5, 1.0, (n, n))
+    opd_t = torch.from_numpy(opd.astype(np.float32)).cuda()
+    amp_t = torch.from_numpy(amp.astype(np.float32)).cuda()
+    el = coro.element(coro.EL_OPD_MAP, opd=opd_t, amplitude=amp_t)
+    f, got = apply(ctx, n, torch.complex64, el, lam=lam)
+    ref = f[0] * optics.phasor(opd.astype(np.float32), lam, amp.astype(np.float32))
+    assert rel_l2(got[0], ref) < 1e-6
+
+
+def test_opd_map_batched(ctx):
+    n, lams = 128, np.array([500e-9, 700e-9, 650e-9])
+    opd = np.stack([inputs.psd_surface(n, s) for s in range(3)]).astype(np.float32)
+    el = coro.element(coro.EL_OPD_MAP, opd=torch.from_numpy(opd).cuda(), flags=coro.ELF_MAP_BATCHED)
+    f = inputs.random_field((3, n, n), seed=1)
+    x = to_dev(f, torch.complex64)
+    coro.apply_element(ctx, x, 1e-3, lams, el)
+    got = x.cpu().numpy()
+    for b in range(3):
+        assert rel_l2(got[b], f[b] * optics.phasor(opd[b], lams[b])) < 1e-6
+
+
+def test_zernike(ctx):
+    n, dx, lam = 512, 1.0 / 500, 550e-9
+    c = inputs.zernike_coefficients(3, 4, 21, 50e-9)
+    el = coro.element(coro.EL_ZERNIKE, radius=0.5, coeffs=c, j_first=4)
+    f, got = apply(ctx, n, torch.complex64, el, dx=dx, lam=lam)
+    ref = f[0] * optics.phasor(optics.zernike_opd(n, dx, 0.5, c, 4), lam)
+    assert rel_l2(got[0], ref) < 1e-6
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_sine_wfe(ctx, axis):
+    n, dx, lam = 2048, 0.04 / 256, 0.5e-6
+    el = coro.element(coro.EL_SINE, sine_freq=500.0, sine_amplitude=5e-9, axis=axis)
+    f, got = apply(ctx, n, torch.complex64, el, dx=dx, lam=lam)
+    ref = f[0] * optics.phasor(optics.sine_wfe(n, dx, 500.0, 5e-9, axis=1 if axis == 0 else 0), lam)
+    assert rel_l2(got[0], ref) < 1e-6
+
+
+def test_scalar_and_init(ctx):
+    x = torch.empty((2, 64, 64), dtype=torch.complex64, device="cuda")
+    coro.wavefront_init(ctx, x, 1.0)
+    coro.apply_element(ctx, x, 1e-3, 5e-7, coro.element(coro.EL_SCALAR, scalar=0.25))
+    assert torch.all(x == 0.25)
+
+
+# ------------------------------------------------------------------------------ fused plan
+
+def relay_elements(w, maps):
+    r = w.diam_m / 2
+    return [
+        coro.element(coro.EL_APERTURE, plane=0, radius=r, obscuration=w.obscuration,
+                     n_spiders=w.n_spiders, spider_width=w.spider_width_frac * w.diam_m),
+        coro.element(coro.EL_LENS, plane=1, focal_length=w.lens1_m),
+        coro.element(coro.EL_OPD_MAP, plane=2, opd=maps[0]),
+        coro.element(coro.EL_LENS, plane=3, focal_length=w.lens2_m),
+        coro.element(coro.EL_OPD_MAP, plane=4, opd=maps[1]),
+        coro.element(coro.EL_CIRCLE, plane=5, radius=w.field_stop_frac * r),
+    ]
+
+
+def relay_oracle(w, maps_np):
+    n, dx, lam = w.n, w.dx, w.wavelength_m
+    r = w.diam_m / 2
+    els = [optics.circular_aperture(n, dx, r, w.obscuration, w.n_spiders, w.spider_width_frac * w.diam_m),
+           optics.thin_lens(n, dx, lam, w.lens1_m),
+           optics.phasor(maps_np[0], lam),
+           optics.thin_lens(n, dx, lam, w.lens2_m),
+           optics.phasor(maps_np[1], lam),
+           optics.circle_stop(n, dx, w.field_stop_frac * r)]
+    return propagation.fresnel_chain(np.ones((n, n), complex), dx, lam, els, list(w.distances()))
+
+
+@pytest.mark.parametrize("n", [256, 2048])
+def test_relay_chain_plan(ctx, n):
+    """Six-plane relay (obscured spidered aperture, two lenses, two PSD surfaces, field
+    stop), five angular-spectrum hops of 0.5-5 m, fused into 11 passes."""
+    w = inputs.RelayWorkload(n=n, npix=n // 2, seed=1)
+    maps = [m.astype(np.float32) for m in w.psd_maps()]
+    maps_t = [torch.from_numpy(m).cuda() for m in maps]
+    plan = coro.FresnelPlan(ctx, n=n, batch=1, pixelscale=w.dx, wavelength=w.wavelength_m,
+                            distances=list(w.distances()), elements=relay_elements(w, maps_t),
+                            init_uniform=True)
+    assert plan.launch_count == 11
+    x = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
+    plan.execute(x)
+    ref = relay_oracle(w, maps)
+    assert rel_l2(x.cpu().numpy()[0], ref) < 1e-5
+
+
+@pytest.mark.slow
+def test_relay_chain_plan_4096(ctx):
+    """The full-size relay at 4096^2 (the benchmarked configuration), whole field."""
+    w = inputs.RelayWorkload(n=4096, npix=1024, seed=0)
+    maps = [m.astype(np.float32) for m in w.psd_maps()]
+    maps_t = [torch.from_numpy(m).cuda() for m in maps]
+    plan = coro.FresnelPlan(ctx, n=4096, batch=1, pixelscale=w.dx, wavelength=w.wavelength_m,
+                            distances=list(w.distances()), elements=relay_elements(w, maps_t),
+                            init_uniform=True)
+    x = torch.empty((1, 4096, 4096), dtype=torch.complex64, device="cuda")
+    plan.execute(x)
+    ref = relay_oracle(w, maps)
+    assert rel_l2(x.cpu().numpy()[0], ref) < 1e-5
+
+
+def test_mixed_plan_direct_then_as(ctx):
+    """Lens, direct hop to focus, focal stop, angular-spectrum hop, on a batch of two
+    wavelengths (the direct hop changes the pixel scale per item)."""
+    n, npix = 256, 128
+    dx = 1.0 / npix
+    lams = np.array([500e-9, 600e-9])
+    els = [coro.element(coro.EL_APERTURE, plane=0, radius=0.5),
+           coro.element(coro.EL_LENS, plane=0, focal_length=10.0),
+           coro.element(coro.EL_CIRCLE, plane=1, radius=40e-6, flags=coro.ELF_OPAQUE_INSIDE)]
+    plan = coro.FresnelPlan(ctx, n=n, batch=2, pixelscale=dx, wavelength=lams, distances=[10.0, 0.05],
+                            methods=[coro.FRESNEL_DIRECT, coro.FRESNEL_AS], elements=els, init_uniform=True)
+    x = torch.empty((2, n, n), dtype=torch.complex64, device="cuda")
+    ps = plan.execute(x)
+    got = x.cpu().numpy()
+    for b in range(2):
+        e = optics.circular_aperture(n, dx, 0.5) * optics.thin_lens(n, dx, lams[b], 10.0)
+        e, du = propagation.direct_fresnel(e, dx, lams[b], 10.0)
+        e = e * optics.circle_stop(n, du, 40e-6, opaque_inside=True)
+        e = propagation.angular_spectrum(e, du, lams[b], 0.05)
+        assert abs(ps[b] - du) < 1e-15 * du
+        assert rel_l2(got[b], e) < 1e-5
+
+
+def test_airy_fp64_direct(ctx):
+    """128-px 1 m aperture on 256^2 complex128, lens 10 m, direct Fresnel 10 m to focus."""
+    n, npix, lam = 256, 128, 500e-9
+    dx = 1.0 / npix
+    els = [coro.element(coro.EL_APERTURE, plane=0, radius=0.5),
+           coro.element(coro.EL_LENS, plane=0, focal_length=10.0)]
+    plan = coro.FresnelPlan(ctx, n=n, batch=1, pixelscale=dx, wavelength=lam, distances=[10.0],
+                            methods=[coro.FRESNEL_DIRECT], elements=els, dtype=coro.C128, init_uniform=True)
+    x = torch.empty((1, n, n), dtype=torch.complex128, device="cuda")
+    ps = plan.execute(x)
+    e = optics.circular_aperture(n, dx, 0.5) * optics.thin_lens(n, dx, lam, 10.0)
+    ref, du = propagation.direct_fresnel(e, dx, lam, 10.0)
+    assert abs(ps[0] / (lam * 10.0) - 0.5) < 1e-14
+    phase_max = np.pi * 2 * (n / 2 * du) ** 2 / (lam * 10.0)
+    assert rel_l2(x.cpu().numpy()[0], ref) < tol(torch.complex128, phase_max)
+
+
+# ------------------------------------------------------------------------------ reductions
+
+def test_intensity_and_darkhole(ctx):
+    du = 0.25
+    f = inputs.random_field((3, 256, 256), seed=12)
+    x = to_dev(f, torch.complex64)
+    norm = np.array([2.0, 3.0, 5.0])
+    i = coro.intensity(ctx, x, norm).cpu().numpy()
+    f32 = f.astype(np.complex64).astype(np.complex128)
+    for b in range(3):
+        ref = np.abs(f32[b]) ** 2 / norm[b]
+        np.testing.assert_allclose(i[b], ref, rtol=2e-7)
+    s = coro.darkhole_sum(ctx, x, du, 6.0, 20.0, norm)
+    from oracle import coronagraph
+    for b in range(3):
+        ref = coronagraph.dark_hole_sum(np.abs(f32[b]) ** 2 / norm[b], du, 6.0, 20.0)
+        assert abs(s[b] - ref) < 1e-12 * ref
