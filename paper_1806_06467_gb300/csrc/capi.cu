@@ -175,6 +175,9 @@ extern "C" coro_status coro_ctx_create(int device, void* stream, coro_ctx* out) 
     if (!c) { set_error("coro_ctx_create: out of host memory"); return CORO_ENOMEM; }
     c->device = device;
     c->stream = (cudaStream_t)stream;
+    e = cudaMalloc(&c->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "coro_ctx_create"); }
     *out = c;
     return CORO_OK;
 }
@@ -188,6 +191,7 @@ extern "C" coro_status coro_ctx_destroy(coro_ctx ctx) {
         for (auto& kv : ctx->tw32) cudaFree(kv.second);
         for (auto& kv : ctx->tw64) cudaFree(kv.second);
         if (ctx->work) cudaFree(ctx->work);
+        if (ctx->err) cudaFree(ctx->err);
     }
     delete ctx;
     return CORO_OK;
@@ -206,6 +210,14 @@ extern "C" coro_status coro_ctx_synchronize(coro_ctx ctx) {
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error flag");
+    if (flag) {
+        cudaMemset(ctx->err, 0, sizeof(int));
+        set_error("a bounded device-side wait expired (code %d); results of the affected launch are invalid", flag);
+        return CORO_ETIMEOUT;
+    }
     return CORO_OK;
 }
 

@@ -17,6 +17,7 @@ struct coro_ctx_s {
     std::map<int, void*> tw64;   // same, complex128
     void* work = nullptr;        // MFT work buffer (grown on demand)
     size_t work_bytes = 0;
+    int* err = nullptr;          // device flag set by kernels whose bounded waits expired
 };
 
 namespace coro {

@@ -7,7 +7,6 @@
 #include "mft_gemm.cuh"
 
 namespace coro {
-cudaError_t launch_cgemm_tc(const GemmDesc& g, int batch, int precision, cudaStream_t stream);
 
 namespace {
 
@@ -82,7 +81,7 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(const GemmDesc g) {
 }  // namespace
 
 cudaError_t launch_cgemm(const GemmDesc& g, int batch, int precision, cudaStream_t stream) {
-    if (precision != CORO_MFT_FP32) return launch_cgemm_tc(g, batch, precision, stream);
+    if (precision != CORO_MFT_FP32) return cudaErrorNotSupported;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch);
     cgemm_simt_kernel<<<grid, 256, 0, stream>>>(g);
     return cudaGetLastError();

@@ -15,6 +15,7 @@
 #include "capi_common.h"
 #include "fft_engine.cuh"
 #include "mft_gemm.cuh"
+#include "tc_gemm.cuh"
 
 using namespace coro;
 
@@ -43,6 +44,72 @@ coro_status check_mft_wf(const char* fn, const coro_wavefront* wf) {
     return CORO_OK;
 }
 
+// Split-precision tensor-core MFT: Y1 = X . W^T written transposed and split, then
+// out = s (Y1^T . W^T)^T, with W[r][k] = exp(-+2 pi i r' k' du/npix) the MFT basis.
+coro_status mft_tensor_core(coro_ctx ctx, const coro_wavefront* in, int direction, int m, const std::vector<double>& c,
+                            bool bf16, coro_wavefront* out) {
+    coro_status st = CORO_OK;
+    const int batch = in->batch;
+    const int nin = in->n;                       // X1 rows = cols
+    const int nout = m;                          // W rows, output size
+    const size_t es = tc_elem_size(bf16);
+    const int ld = tc_ld(nin, bf16);
+    const size_t x_bytes = (size_t)4 * batch * nin * ld * es;
+    const size_t w_bytes = (size_t)4 * batch * nout * ld * es;
+    const size_t z_bytes = w_bytes;
+    auto align = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
+    unsigned char* work = (unsigned char*)coro::ctx_work(ctx, align(x_bytes) + align(w_bytes) + align(z_bytes), &st);
+    if (!work) return st;
+    TcOperand X{work, batch, nin, nin, ld};
+    TcOperand W{work + align(x_bytes), batch, nout, nin, ld};
+    TcOperand Z{work + align(x_bytes) + align(w_bytes), batch, nout, nin, ld};
+    void* c_d = coro::upload_async(ctx, c.data(), c.size() * sizeof(double), &st);
+    if (!c_d) return st;
+    std::vector<TcItem> it1(batch), it2(batch);
+    for (int b = 0; b < batch; ++b) {
+        it1[b] = TcItem{nin, nout, nin, b, b, 0, 0x7fffffff, 1.0f, 1.0f};
+        it2[b] = TcItem{nout, nout, nin, b, b, 0, 0x7fffffff, (float)c[b], 1.0f};
+    }
+    void* i1 = coro::upload_async(ctx, it1.data(), batch * sizeof(TcItem), &st);
+    void* i2 = i1 ? coro::upload_async(ctx, it2.data(), batch * sizeof(TcItem), &st) : nullptr;
+    cudaError_t e = (i1 && i2) ? cudaSuccess : cudaErrorMemoryAllocation;
+    CUtensorMap mx, mw, mz;
+    if (e == cudaSuccess) e = tc_split(bf16, (const float2*)in->data, (long long)nin * nin, nin, X, ctx->stream);
+    if (e == cudaSuccess) e = tc_basis(bf16, (const double*)c_d, direction < 0 ? -1 : 1, W, ctx->stream);
+    if (e == cudaSuccess) e = tc_make_operand_map(X, bf16, &mx);
+    if (e == cudaSuccess) e = tc_make_operand_map(W, bf16, &mw);
+    if (e == cudaSuccess) e = tc_make_operand_map(Z, bf16, &mz);
+    if (e == cudaSuccess) {
+        TcArgs a{};
+        a.items = (const TcItem*)i1;
+        a.err = ctx->err;
+        a.dst = Z.base;
+        a.dst_bstride = (long long)4 * nout * ld;
+        a.dst_rows = nout;
+        a.dst_ld = ld;
+        e = tc_launch(bf16, TC_EPI_SPLITT, mx, mw, nin, nout, nin, batch, a, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        TcArgs a{};
+        a.items = (const TcItem*)i2;
+        a.err = ctx->err;
+        a.dst = out->data;
+        a.dst_bstride = (long long)nout * nout;
+        a.dst_rows = nout;
+        a.dst_ld = nout;
+        e = tc_launch(bf16, TC_EPI_C64T, mz, mw, nout, nout, nin, batch, a, ctx->stream);
+    }
+    coro::free_async(ctx, c_d);
+    coro::free_async(ctx, i1);
+    coro::free_async(ctx, i2);
+    if (e == cudaErrorNotSupported) {
+        coro::set_error("coro_propagate_mft: tensor maps unavailable (driver entry point missing)");
+        return CORO_ENOTIMPL;
+    }
+    if (e != cudaSuccess) return coro::cuda_fail(e, "tensor-core MFT");
+    return CORO_OK;
+}
+
 }  // namespace
 
 extern "C" coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in, double npix, int direction,
@@ -68,6 +135,7 @@ extern "C" coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in
         c[b] = du[b] / npix;
     }
     coro::DeviceGuard g(ctx->device);
+    if (precision != CORO_MFT_FP32) return mft_tensor_core(ctx, in, direction, m, c, precision == CORO_MFT_3XBF16, out);
     // focal-plane side has m (forward) or in->n (inverse) samples; pupil side the other
     const int nf = direction < 0 ? m : in->n;     // focal samples per axis
     const int np = direction < 0 ? in->n : m;     // pupil samples per axis

@@ -1,0 +1,314 @@
+// tc_gemm.cu -- tcgen05 split-precision complex GEMM, its operand producers and launcher.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+namespace coro {
+namespace {
+
+constexpr int BM = 128;                  // rows of X per tile (UMMA M)
+constexpr int BN = 128;                  // rows of W per tile (UMMA N), complex outputs
+constexpr int STAGES = 3;
+constexpr int PLANE_BYTES = 128 * 64;    // 128 rows x 64-byte K slice
+constexpr int OPER_BYTES = 4 * PLANE_BYTES;
+constexpr int STAGE_BYTES = 2 * OPER_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int THREADS = 192;             // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr uint32_t TMEM_COLS = 256;
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Split (re, im) into hi/lo and store the four planes at element offset `off`.
+template <bool BF16>
+__device__ __forceinline__ void store_split(void* base, size_t plane, size_t off, float re, float im) {
+    if constexpr (BF16) {
+        __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(base);
+        const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi = __float2bfloat16_rn(im);
+        p[off] = hr;
+        p[plane + off] = hi;
+        p[2 * plane + off] = __float2bfloat16_rn(re - __bfloat162float(hr));
+        p[3 * plane + off] = __float2bfloat16_rn(im - __bfloat162float(hi));
+    } else {
+        float* p = reinterpret_cast<float*>(base);
+        const float hr = tf32_rna(re), hi = tf32_rna(im);
+        p[off] = hr;
+        p[plane + off] = hi;
+        p[2 * plane + off] = tf32_rna(re - hr);
+        p[3 * plane + off] = tf32_rna(im - hi);
+    }
+}
+
+template <bool BF16, int EPI>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw, const TcArgs a) {
+    const int b = blockIdx.z;
+    const TcItem it = a.items[b];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (m0 >= it.M || n0 >= it.N) return;            // uniform: uneven items skip empty tiles
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int KE = BF16 ? 32 : 16;               // real elements per 64-byte K slice
+    const int kblocks = (it.K + KE - 1) / KE;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        tc::mbar_init(accf, 1);
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&mx);
+        tc::prefetch_tmap(&mw);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tslot, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int k = 0; k < kblocks; ++k) {
+                const int s = k % STAGES;
+                const uint32_t ph = (k / STAGES) & 1;
+                if (!tc::mbar_wait(&empty[s], ph ^ 1, a.err, 1)) break;
+                unsigned char* st = smem + s * STAGE_BYTES;
+                tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                tc::tma_load_4d(st, &mx, &full[s], k * KE, m0, 0, it.x_idx);
+                tc::tma_load_4d(st + OPER_BYTES, &mw, &full[s], k * KE, n0, 0, it.w_idx);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t ID_POS = tc::idesc<BF16>(BM, BN, false);
+            constexpr uint32_t ID_NEG = tc::idesc<BF16>(BM, BN, true);
+            const uint32_t d_re = tbase, d_im = tbase + 128;
+            bool ok = true;
+            for (int k = 0; k < kblocks && ok; ++k) {
+                const int s = k % STAGES;
+                const uint32_t ph = (k / STAGES) & 1;
+                if (!(ok = tc::mbar_wait(&full[s], ph, a.err, 2))) break;
+                tc::tc_fence_after();
+                const uint32_t xa = tc::smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t wa = xa + OPER_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {           // two MMA K-steps of 32 bytes per slice
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {          // hi.hi, hi.lo, lo.hi
+                        const int xs = (t == 2) ? 1 : 0, ws = (t == 1) ? 1 : 0;
+                        const uint64_t ar = tc::sdesc_sw64(xa + (2 * xs + 0) * PLANE_BYTES + kk * 32);
+                        const uint64_t ai = tc::sdesc_sw64(xa + (2 * xs + 1) * PLANE_BYTES + kk * 32);
+                        const uint64_t br = tc::sdesc_sw64(wa + (2 * ws + 0) * PLANE_BYTES + kk * 32);
+                        const uint64_t bi = tc::sdesc_sw64(wa + (2 * ws + 1) * PLANE_BYTES + kk * 32);
+                        const uint32_t acc = (k | kk | t) ? 1u : 0u;
+                        tc::umma<BF16>(d_re, ar, br, ID_POS, acc);
+                        tc::umma<BF16>(d_re, ai, bi, ID_NEG, 1u);
+                        tc::umma<BF16>(d_im, ar, bi, ID_POS, acc);
+                        tc::umma<BF16>(d_im, ai, br, ID_POS, 1u);
+                    }
+                }
+                tc::umma_commit(&empty[s]);             // frees the stage once these MMAs retire
+            }
+            if (ok) tc::umma_commit(accf);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (warps 2..5)
+        const int q = warp & 3;                          // TMEM lane quarter this warp may read
+        const int row = q * 32 + lane;
+        const int m = m0 + row;
+        const bool ok = tc::mbar_wait(accf, 0, a.err, 3);
+        __syncwarp();
+        tc::tc_fence_after();
+        double dh = 0.0;
+        if (ok) {
+            const int kx = m - it.M / 2;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t rr[32], ri[32];
+                tc::tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + c, rr);
+                tc::tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + 128 + c, ri);
+                tc::tmem_ld_wait();
+                if (m >= it.M) continue;
+#pragma unroll 4
+                for (int j = 0; j < 32; ++j) {
+                    const int n = n0 + c + j;
+                    if (n >= it.N) break;
+                    float re = __uint_as_float(rr[j]) * it.scale, im = __uint_as_float(ri[j]) * it.scale;
+                    const int ky = n - it.N / 2;
+                    const int r2 = kx * kx + ky * ky;
+                    const bool keep = r2 >= it.mask_lo && r2 <= it.mask_hi;
+                    if constexpr (EPI == TC_EPI_C64T) {
+                        float2* d = reinterpret_cast<float2*>(a.dst) + b * a.dst_bstride + (size_t)n * a.dst_ld + m;
+                        *d = make_float2(re, im);
+                    } else if constexpr (EPI == TC_EPI_SPLITT) {
+                        if (!keep) { re = 0.f; im = 0.f; }
+                        const size_t plane = (size_t)a.dst_rows * a.dst_ld;
+                        store_split<BF16>(a.dst, plane, b * a.dst_bstride + (size_t)n * a.dst_ld + m, re, im);
+                    } else if constexpr (EPI == TC_EPI_BABINET) {
+                        const float2 e = a.ea[b * a.ea_bstride + (size_t)n * a.ea_ld + m];
+                        re = keep ? e.x - re : 0.f;
+                        im = keep ? e.y - im : 0.f;
+                        const size_t plane = (size_t)a.dst_rows * a.dst_ld;
+                        store_split<BF16>(a.dst, plane, b * a.dst_bstride + (size_t)n * a.dst_ld + m, re, im);
+                        if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(re, im);
+                    } else {
+                        const float inten = (re * re + im * im) * it.inv_peak;
+                        if (a.dst) reinterpret_cast<float*>(a.dst)[b * a.dst_bstride + (size_t)n * a.dst_ld + m] = inten;
+                        if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(re, im);
+                        if (keep) dh += (double)inten;
+                    }
+                }
+            }
+        }
+        if constexpr (EPI == TC_EPI_INTENSITY) {
+            for (int o = 16; o > 0; o >>= 1) dh += __shfl_down_sync(0xffffffffu, dh, o);
+            if (lane == 0 && dh != 0.0 && a.dh_acc) atomicAdd(a.dh_acc + b, dh);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tbase, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- operand producers
+
+template <bool BF16>
+__global__ void split_kernel(const float2* __restrict__ src, long long sb, int sld, void* dst, int rows, int cols,
+                             int ld) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y, b = blockIdx.z;
+    if (k >= ld) return;
+    float2 v = make_float2(0.f, 0.f);
+    if (k < cols) v = src[b * sb + (size_t)r * sld + k];
+    const size_t plane = (size_t)rows * ld;
+    store_split<BF16>(dst, plane, (size_t)b * 4 * plane + (size_t)r * ld + k, v.x, v.y);
+}
+
+// W[r][k] = exp(sign 2 pi i (r - rows/2)(k - cols/2) c_b): FP64 phase reduced to its
+// fractional cycle, then rounded to FP32 and split.
+template <bool BF16>
+__global__ void basis_kernel(const double* __restrict__ c, int sign, void* dst, int rows, int cols, int ld) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y, b = blockIdx.z;
+    if (k >= ld) return;
+    float re = 0.f, im = 0.f;
+    if (k < cols) {
+        const long long rr = (long long)r - rows / 2, kk = (long long)k - cols / 2;
+        double cyc = (double)(rr * kk) * c[b];
+        cyc -= rint(cyc);
+        double s, co;
+        sincospi(2.0 * cyc, &s, &co);
+        re = (float)co;
+        im = (float)(sign < 0 ? -s : s);
+    }
+    const size_t plane = (size_t)rows * ld;
+    store_split<BF16>(dst, plane, (size_t)b * 4 * plane + (size_t)r * ld + k, re, im);
+}
+
+// ---------------------------------------------------------------- driver entry point
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+template <bool BF16, int EPI>
+cudaError_t launch_t(const CUtensorMap& mx, const CUtensorMap& mw, int max_m, int max_n, int batch, const TcArgs& args,
+                     cudaStream_t stream) {
+    static int attr_done = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_done != dev) {
+        cudaError_t e = cudaFuncSetAttribute(tc_cgemm_kernel<BF16, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_done = dev;
+    }
+    dim3 grid((max_n + BN - 1) / BN, (max_m + BM - 1) / BM, batch);
+    tc_cgemm_kernel<BF16, EPI><<<grid, THREADS, SMEM_BYTES, stream>>>(mx, mw, args);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_make_operand_map(const TcOperand& op, bool bf16, CUtensorMap* map) {
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const size_t es = tc_elem_size(bf16);
+    if (((uintptr_t)op.base & 15) || (op.ld * es) % 16) return cudaErrorInvalidValue;
+    cuuint64_t dims[4] = {(cuuint64_t)op.ld, (cuuint64_t)op.rows, 4, (cuuint64_t)op.batch};
+    cuuint64_t strides[3] = {(cuuint64_t)op.ld * es, (cuuint64_t)op.rows * op.ld * es, (cuuint64_t)4 * op.rows * op.ld * es};
+    cuuint32_t box[4] = {(cuuint32_t)(64 / es), 128, 4, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, op.base, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t tc_launch(bool bf16, int epi, const CUtensorMap& mx, const CUtensorMap& mw, int max_m, int max_n,
+                      int max_k, int batch, const TcArgs& args, cudaStream_t stream) {
+    (void)max_k;
+    if (bf16) {
+        switch (epi) {
+            case TC_EPI_C64T: return launch_t<true, TC_EPI_C64T>(mx, mw, max_m, max_n, batch, args, stream);
+            case TC_EPI_SPLITT: return launch_t<true, TC_EPI_SPLITT>(mx, mw, max_m, max_n, batch, args, stream);
+            case TC_EPI_BABINET: return launch_t<true, TC_EPI_BABINET>(mx, mw, max_m, max_n, batch, args, stream);
+            case TC_EPI_INTENSITY: return launch_t<true, TC_EPI_INTENSITY>(mx, mw, max_m, max_n, batch, args, stream);
+        }
+    } else {
+        switch (epi) {
+            case TC_EPI_C64T: return launch_t<false, TC_EPI_C64T>(mx, mw, max_m, max_n, batch, args, stream);
+            case TC_EPI_SPLITT: return launch_t<false, TC_EPI_SPLITT>(mx, mw, max_m, max_n, batch, args, stream);
+            case TC_EPI_BABINET: return launch_t<false, TC_EPI_BABINET>(mx, mw, max_m, max_n, batch, args, stream);
+            case TC_EPI_INTENSITY: return launch_t<false, TC_EPI_INTENSITY>(mx, mw, max_m, max_n, batch, args, stream);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_split(bool bf16, const float2* src, long long src_bstride, int src_ld, const TcOperand& dst,
+                     cudaStream_t stream) {
+    dim3 grid((dst.ld + 127) / 128, dst.rows, dst.batch);
+    if (bf16) split_kernel<true><<<grid, 128, 0, stream>>>(src, src_bstride, src_ld, dst.base, dst.rows, dst.cols, dst.ld);
+    else split_kernel<false><<<grid, 128, 0, stream>>>(src, src_bstride, src_ld, dst.base, dst.rows, dst.cols, dst.ld);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_basis(bool bf16, const double* c, int sign, const TcOperand& dst, cudaStream_t stream) {
+    dim3 grid((dst.ld + 127) / 128, dst.rows, dst.batch);
+    if (bf16) basis_kernel<true><<<grid, 128, 0, stream>>>(c, sign, dst.base, dst.rows, dst.cols, dst.ld);
+    else basis_kernel<false><<<grid, 128, 0, stream>>>(c, sign, dst.base, dst.rows, dst.cols, dst.ld);
+    return cudaGetLastError();
+}
+
+}  // namespace coro

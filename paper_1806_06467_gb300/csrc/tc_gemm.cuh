@@ -1,0 +1,78 @@
+// tc_gemm.cuh -- split-precision complex GEMM on the 5th-generation tensor cores.
+//
+// Computes, for every batch item b,
+//     Y[m][n] = sum_k X[m][k] W[n][k]                     (complex, FP32 accumulate)
+// from "planar split" operands: a complex matrix Z is stored as four real planes
+// [hi_re, hi_im, lo_re, lo_im], hi = round(Z) to TF32 or BF16, lo = round(Z - hi). The product
+// keeps the three leading terms hi.hi + hi.lo + lo.hi; each is four real products
+// (re.re - im.im, re.im + im.re), the minus sign taken by the A-negate bit of the MMA.
+//
+// One CTA owns a 128 x 128 complex output tile: two 128x128 FP32 accumulators in TMEM
+// (real at columns 0-127, imaginary at 128-255). Warp 0 streams 64-byte-wide K slices of all
+// four planes of X and W through a 3-stage shared-memory ring with one 4-D TMA per operand;
+// warp 1 issues tcgen05.mma (24 per slice); warps 2-5 drain TMEM and run the epilogue, which
+// always writes the TRANSPOSED tile (Y^T), so that chained GEMMs X.W^T then (X.W^T)^T.W^T
+// realise A . E . A^T without any separate transpose.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace coro {
+
+enum TcEpi : int {
+    TC_EPI_C64T = 0,       // complex64 Y^T * scale
+    TC_EPI_SPLITT = 1,     // planar split of (Y^T * scale * mask) -> operand of the next GEMM
+    TC_EPI_BABINET = 2,    // (E_A - Y^T * scale) * mask -> planar split (+ optional complex64 copy)
+    TC_EPI_INTENSITY = 3   // |Y^T * scale|^2 * inv_peak -> float image + dark-hole sum
+};
+
+// Per-item geometry and epilogue constants.
+struct TcItem {
+    int M, N, K;           // complex: rows of X (and of Y), rows of W, inner length
+    int x_idx, w_idx;      // batch coordinate of X and of W inside their tensor maps
+    int mask_lo, mask_hi;  // epilogue keeps samples with mask_lo <= r^2 <= mask_hi (integer px^2)
+    float scale;           // multiplies Y
+    float inv_peak;        // intensity normalisation
+};
+
+struct TcArgs {
+    const TcItem* items;
+    int* err;                        // nonzero after a bounded wait expired
+    void* dst;                       // split planes [b][4][dst_rows][dst_ld] or complex64/float [b][dst_rows][dst_ld]
+    long long dst_bstride;           // elements per item
+    int dst_rows, dst_ld;
+    const float2* ea;                // Babinet minuend [b][ea_rows][ea_ld]
+    long long ea_bstride;
+    int ea_ld;
+    float2* c64;                     // optional complex64 copy [b][rows][c64_ld]
+    long long c64_bstride;
+    int c64_ld;
+    double* dh_acc;                  // dark-hole sums [b]
+};
+
+// Host side (tc_gemm.cu).
+struct TcOperand {                   // a planar split operand in global memory
+    void* base;                      // [batch][4][rows][ld] elements (float or bf16)
+    int batch, rows, cols, ld;       // cols = valid K extent (complex), ld >= cols, 16-byte rows
+};
+
+cudaError_t tc_make_operand_map(const TcOperand& op, bool bf16, CUtensorMap* map);
+cudaError_t tc_launch(bool bf16, int epi, const CUtensorMap& mx, const CUtensorMap& mw, int max_m, int max_n,
+                      int max_k, int batch, const TcArgs& args, cudaStream_t stream);
+
+// complex64 [batch][rows][cols] (leading dimension src_ld) -> planar split operand
+cudaError_t tc_split(bool bf16, const float2* src, long long src_bstride, int src_ld, const TcOperand& dst,
+                     cudaStream_t stream);
+// W[r][k] = exp(sign 2 pi i (r - rows/2)(k - cols/2) c[b]) straight into planar split form
+cudaError_t tc_basis(bool bf16, const double* c, int sign, const TcOperand& dst, cudaStream_t stream);
+
+inline size_t tc_elem_size(bool bf16) { return bf16 ? 2 : 4; }
+inline int tc_ld(int cols, bool bf16) {          // 16-byte rows, at least 64 bytes
+    const int q = bf16 ? 8 : 4;
+    int ld = (cols + q - 1) / q * q;
+    const int mn = bf16 ? 32 : 16;
+    return ld < mn ? mn : ld;
+}
+
+}  // namespace coro
