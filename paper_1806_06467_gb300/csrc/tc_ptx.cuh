@@ -10,7 +10,7 @@
 namespace coro {
 namespace tc {
 
-constexpr long long kSpinLimit = 1LL << 24;
+constexpr long long kSpinLimit = 1LL << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
