@@ -227,6 +227,30 @@ coro_status coro_intensity(coro_ctx ctx, const coro_wavefront* wf, const double*
 coro_status coro_darkhole_sum(coro_ctx ctx, const coro_wavefront* wf, const double* du,
                               double r_in, double r_out, const double* norm, double* host_out);
 
+/* ------------------------------------------------------------------------------------------
+ * Allocation-free dark-hole sum. The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory while they run -- a real-time wavefront-control loop that must
+ * not see allocator latency or jitter between frames, an application whose device heap is
+ * owned by another framework, or a process with a memory budget fixed at start-up.
+ * Same result as coro_darkhole_sum (same arguments, no context): the field and host_out
+ * belong to the caller; the reduction's scratch (bounds, normalisation, accumulators for up
+ * to CORO_NOALLOC_MAX_BATCH items, 32 KiB) is one fixed device array inside the library,
+ * held by every GPU that loads it until the process exits. No cudaMalloc/cudaFree or other
+ * allocating routine is called.
+ *   - Runs on the calling thread's current device and on `stream` (a cudaStream_t, NULL =
+ *     legacy default stream); synchronises that stream to return the host values.
+ *   - The first call on a device looks up the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the one array: calls that overlap on the GPU (other threads, other
+ *     streams) race and must be serialised by the caller. Each call clears the accumulators
+ *     it uses before the reduction.
+ *   - batch > CORO_NOALLOC_MAX_BATCH returns CORO_ESIZE with a message; nothing is launched.
+ * ------------------------------------------------------------------------------------------ */
+#define CORO_NOALLOC_MAX_BATCH 1024
+coro_status coro_darkhole_sum_noalloc(const coro_wavefront* wf, const double* du, double r_in,
+                                      double r_out, const double* norm, void* stream,
+                                      double* host_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,8 @@ _SIGS = {
     "coro_intensity": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.POINTER(ct.c_double), _P]),
     "coro_darkhole_sum": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.POINTER(ct.c_double), ct.c_double,
                                      ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
+    "coro_darkhole_sum_noalloc": (ct.c_int, [ct.POINTER(Wavefront), ct.POINTER(ct.c_double), ct.c_double,
+                                             ct.c_double, ct.POINTER(ct.c_double), _P, ct.POINTER(ct.c_double)]),
 }
 
 
@@ -250,6 +252,24 @@ def darkhole_sum(ctx: Context, field, du, r_in: float, r_out: float, norm=None) 
     nrm = None if norm is None else _dbl(np.broadcast_to(np.asarray(norm, float), (b,)))
     out = (ct.c_double * b)()
     ctx.lib.check(ctx.lib.coro_darkhole_sum(ctx.handle, ct.byref(w.s), du_arr, r_in, r_out, nrm, out))
+    return np.array(out[:])
+
+
+def darkhole_sum_noalloc(field, du, r_in: float, r_out: float, norm=None, stream=None) -> np.ndarray:
+    """coro_darkhole_sum_noalloc: same sums as darkhole_sum, with no device allocation (for
+    callers that must not allocate while they run). Uses the current device and torch's current
+    stream unless one is given; calls that overlap on the GPU race (one shared scratch array)."""
+    import torch
+    lib = Library.get()
+    w = WF(field)
+    b = w.s.batch
+    du_arr = _dbl(np.broadcast_to(np.asarray(du, float), (b,)))
+    nrm = None if norm is None else _dbl(np.broadcast_to(np.asarray(norm, float), (b,)))
+    if stream is None:
+        stream = torch.cuda.current_stream(field.device)
+    out = (ct.c_double * b)()
+    lib.check(lib.coro_darkhole_sum_noalloc(ct.byref(w.s), du_arr, r_in, r_out, nrm,
+                                            ct.c_void_p(stream.cuda_stream), out))
     return np.array(out[:])
 
 
