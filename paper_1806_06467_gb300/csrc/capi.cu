@@ -65,14 +65,28 @@ extern "C" int coro_version(void) { return CORO_VERSION; }
 
 namespace {
 
-// tw[m] = exp(-2 pi i m / n), evaluated in FP64 (sincospi of an exact rational) and rounded.
+// Per-pass twiddle blocks of an n-point line FFT (radix 16 then one smaller radix): entry
+// m of the block with span ns is W_{ns R}^{r k}, r = 1 + m / ns, k = m % ns, evaluated in FP64
+// (sincospi of an exact rational) and rounded. Entries past the last block stay unused.
 template <typename C>
 __global__ void twiddle_kernel(C* tw, int n) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
-    double s, c;
-    sincospi(-2.0 * (double)m / (double)n, &s, &c);
-    tw[m] = mk<C>((typename real_of<C>::type)c, (typename real_of<C>::type)s);
+    int ns = 16, off = 0;
+    while (ns < n) {
+        const int r_pass = (n / ns) >= 16 ? 16 : n / ns;
+        const int len = (r_pass - 1) * ns;
+        if (m < off + len) {
+            const int r = 1 + (m - off) / ns, k = (m - off) % ns;
+            double s, c;
+            sincospi(-2.0 * (double)((long long)r * k) / (double)(ns * r_pass), &s, &c);
+            tw[m] = mk<C>((typename real_of<C>::type)c, (typename real_of<C>::type)s);
+            return;
+        }
+        off += len;
+        ns *= 16;
+    }
+    tw[m] = mk<C>(0, 0);
 }
 
 // Separable phase table: value[k] = mag * (-1)^(checker*k) * exp(2 pi i sign frac(k'^2 c)),

@@ -133,7 +133,16 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C (&v
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
-// Twiddle table: tw[m] = exp(-2 pi i m / N) for m in [0, N), built in FP64 and rounded.
+// Twiddle table: one block per pass with span NS > 1, laid out [r - 1][k] (r in [1, R),
+// k in [0, NS)) holding W_{NS R}^{r k} = exp(-2 pi i r k / (NS R)), built in FP64 and rounded.
+// Threads of a warp hold consecutive k, so each load is one or two contiguous wavefronts.
+// Every pass but the last has R = 16, so the block of span NS starts at 15 (16 + 256 + ...).
+__host__ __device__ constexpr int twiddle_offset(int ns) {
+    int off = 0;
+    for (int s = 16; s < ns; s *= 16) off += 15 * s;
+    return off;
+}
+
 template <bool INV, typename C> __device__ __forceinline__ C twiddle(const C* __restrict__ tw, int m) {
     C w = __ldg(tw + m);
     if (INV) w.y = -w.y;
@@ -157,9 +166,9 @@ __device__ __forceinline__ void line_fft_pass(C (&v)[16], C* buf, int t, const C
 #pragma unroll
         for (int r = 0; r < R; ++r) u[r] = v[b + r * B];
         if constexpr (NS > 1) {
-            constexpr int STEP = N / (NS * R);
+            const C* blk = tw + twiddle_offset(NS) + k;
 #pragma unroll
-            for (int r = 1; r < R; ++r) u[r] = cmul(u[r], twiddle<INV>(tw, r * k * STEP));
+            for (int r = 1; r < R; ++r) u[r] = cmul(u[r], twiddle<INV>(blk, (r - 1) * NS));
         }
         dft<R, INV>(u);
         if constexpr (LAST) {
@@ -167,14 +176,29 @@ __device__ __forceinline__ void line_fft_pass(C (&v)[16], C* buf, int t, const C
             for (int r = 0; r < R; ++r) v[b + r * B] = u[r];
         } else {
             const int base = (j / NS) * NS * R + k;
+            // positions base + r*NS: for NS a multiple of 16 (or NS = 1 with base a multiple
+            // of 16) the padded addresses advance by a compile-time stride
+            if constexpr (NS % 16 == 0 || (NS == 1 && R == 16)) {
+                constexpr int PS = NS == 1 ? 1 : NS + NS / 16;
+                C* p = buf + pad16(base);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[pad16(base + r * NS)] = u[r];
+                for (int r = 0; r < R; ++r) p[r * PS] = u[r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) buf[pad16(base + r * NS)] = u[r];
+            }
         }
     }
     if constexpr (!LAST) {
         __syncthreads();
+        if constexpr (TPL % 16 == 0) {
+            const C* p = buf + pad16(t);
 #pragma unroll
-        for (int s = 0; s < 16; ++s) v[s] = buf[pad16(t + s * TPL)];
+            for (int s = 0; s < 16; ++s) v[s] = p[s * (TPL + TPL / 16)];
+        } else {
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = buf[pad16(t + s * TPL)];
+        }
         __syncthreads();
         line_fft_pass<C, N, INV, NS * R>(v, buf, t, tw);
     }
