@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-coronagraph", action="store_true")
+    ap.add_argument("--bf16", action="store_true", help="also time the 3xBF16 coronagraph plan")
     return ap.parse_args()
 
 
@@ -291,6 +293,149 @@ def plain_gpu(n: int, maps_np, w, steps: int, warmup: int, device) -> dict:
             "form": "torch.fft.fft2/ifft2 (cuFFT) + torch elementwise complex64, unfused, per hop"}
 
 
+# ------------------------------------------------------------------------------ coronagraph PSFs
+
+def tensor_peak(precision_bf16: bool) -> tuple[float, str]:
+    """Sustained dense peak for the MMA dtype: the measured BF16 figure, times the nominal
+    TF32/BF16 ratio (1.1 / 2.25 PFLOP/s) for TF32."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops_sustained"])
+        src = "measured bf16_tflops_sustained"
+    except (OSError, KeyError, ValueError):
+        bf16, src = 1700.0, "fallback sustained bf16"
+    if precision_bf16:
+        return bf16, src
+    return bf16 * 1.1 / 2.25, src + " x 1.1/2.25 (tf32)"
+
+
+def broadband_pupils(ctx, device):
+    """168 pupil fields (21 wavelengths x 8 DM sinc probes): clear aperture, Zernike 4-21 at 5 nm
+    RMS and the probe's DM surface (Gaussian influence, FWHM 1 pitch), built by the library."""
+    import numpy as np
+    import torch
+
+    from paper_1806_06467_gb300 import coro, inputs
+    bw = inputs.BroadbandWorkload()
+    lw = bw.lyot
+    lams = bw.wavelengths()
+    lam_b = np.repeat(lams, bw.n_probe)
+    B, n, npix = len(lam_b), lw.n, lw.npix
+    dx = lw.diam_m / npix
+    field = torch.empty((B, n, n), dtype=torch.complex64, device=device)
+    coro.wavefront_init(ctx, field, 1.0)
+    coro.apply_element(ctx, field, dx, lam_b, coro.element(coro.EL_APERTURE, radius=lw.diam_m / 2))
+    coro.apply_element(ctx, field, dx, lam_b, coro.element(coro.EL_ZERNIKE, radius=lw.diam_m / 2, coeffs=lw.zernike(),
+                                                           j_first=lw.zernike_first))
+    heights = torch.from_numpy(np.tile(bw.probes(), (len(lams), 1, 1)).astype(np.float32)).to(device)
+    pitch = lw.diam_m / bw.n_act
+    opd = coro.dm_opd(ctx, heights, pitch, pitch, n, dx, 2.0)
+    coro.apply_element(ctx, field, dx, lam_b, coro.element(coro.EL_OPD_MAP, opd=opd, flags=coro.ELF_MAP_BATCHED))
+    torch.cuda.synchronize()
+    del opd
+    r = bw.lambda_c_m / lam_b
+    items = [dict(m_occ=int(m), du_occ=lw.du_occ * rr, spot_radius=lw.spot_radius_lamd * rr, du_det=lw.du_det * rr,
+                  dh_in=lw.dh_inner * rr, dh_out=lw.dh_outer * rr)
+             for m, rr in zip(np.repeat(bw.occulter_sizes(), bw.n_probe), r)]
+    return field, items, lw
+
+
+def coronagraph_bench(ctx, device, steps: int, warmup: int, precision: int) -> dict:
+    import numpy as np
+    import torch
+
+    from paper_1806_06467_gb300 import coro
+    pupils, items, lw = broadband_pupils(ctx, device)
+    B, n, md = len(items), lw.n, lw.m_det
+    plan = coro.LyotPlan(ctx, n=n, npix=lw.npix, lyot_frac=lw.lyot_frac, m_det=md, items=items, precision=precision)
+    peak = plan.peak(pupils)                          # normalisation, computed once
+    stream = torch.cuda.current_stream(device)
+    for _ in range(warmup):
+        plan.execute(pupils, peak=peak, want_dh=False)
+    torch.cuda.synchronize()
+    n_stage = 6
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_stage + 1)] for _ in range(steps)]
+    for k in range(steps):
+        evs[k][0].record(stream)
+        for s in range(n_stage):
+            plan.execute_range(pupils, s, 1, peak=peak)
+            evs[k][s + 1].record(stream)
+    torch.cuda.synchronize()
+    per = np.array([[evs[k][s].elapsed_time(evs[k][s + 1]) for s in range(n_stage)] for k in range(steps)])
+    total_ms = float(per.sum())
+    # algorithmic tensor work: 8 real flops per complex MAC, three split products
+    cmac = {1: 0.0, 2: 0.0, 3: 0.0, 4: 0.0, 5: 0.0}
+    for it in items:
+        mo = it["m_occ"]
+        cmac[1] += n * mo * n + mo * mo * n
+        cmac[2] += 0.0
+        cmac[3] += mo * n * mo + n * n * mo
+        cmac[5] += n * md * n + md * md * n
+    flops_per_step = 24.0 * sum(cmac.values())
+    gemm_ms = float(per[:, 1:].sum())                 # stages 1-5 are tensor-core GEMM launches
+    achieved = flops_per_step * steps / (gemm_ms / 1e3) / 1e12
+    pk, src = tensor_peak(precision == coro.MFT_3XBF16)
+    out = {"value": B * steps / (total_ms / 1e3), "unit": "PSFs/s", "batch": B,
+           "precision": "3xBF16" if precision == coro.MFT_3XBF16 else "3xTF32",
+           "workload": "broadband_lyot: 21 wavelengths (500-600 nm) x 8 DM sinc probes, 1024^2 pupil, "
+                       "occulter 235-282 px at 0.05 lc/l lambda/D, detector 512^2",
+           "ms_per_step": total_ms / steps, "gpu_launches_per_step": 8,
+           "roofline": {"bound": "tensor", "kernel": "tc_cgemm_kernel", "achieved": achieved, "peak": pk,
+                        "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
+                        "flops_per_step": flops_per_step, "time_share": gemm_ms / total_ms,
+                        "peak_source": src}}
+    plan.close()
+    return out
+
+
+def coronagraph_plain(device, steps: int, n_lambda: int = 21, n_probe: int = 8) -> dict:
+    """Plain per-wavelength FP32 GPU form: torch.matmul (cuBLAS cgemm, complex64) MFT chain per
+    wavelength over the 8 probe pupils, bases precomputed; same sizes as the batched plan."""
+    import math
+
+    import torch
+    n, md = 1024, 512
+    B = n_probe
+    e = torch.randn((B, n, n), dtype=torch.complex64, device=device)
+
+    def basis(m, du, npix, sign):
+        x = (torch.arange(n, device=device, dtype=torch.float64) - n // 2) / npix
+        u = (torch.arange(m, device=device, dtype=torch.float64) - m // 2) * du
+        return torch.polar(torch.ones(m, n, device=device, dtype=torch.float64),
+                           sign * 2 * math.pi * torch.outer(u, x)).to(torch.complex64)
+
+    lams = [500e-9 + 100e-9 * i / (n_lambda - 1) for i in range(n_lambda)]
+    k = torch.arange(n, device=device, dtype=torch.float64) - n // 2
+    lyot = ((k[None, :] ** 2 + k[:, None] ** 2) / n ** 2 <= 0.4 ** 2).to(torch.complex64)
+    bases = []
+    for lam in lams:
+        r = 550e-9 / lam
+        mo = round(256 * r)
+        ko = torch.arange(mo, device=device, dtype=torch.float64) - mo // 2
+        spot = ((ko[None, :] ** 2 + ko[:, None] ** 2) * (0.05 * r) ** 2 <= (5 * r) ** 2).to(torch.complex64)
+        a = basis(mo, 0.05 * r, n, -1)
+        bases.append((a, a.conj().T.contiguous(), basis(md, 0.25 * r, n, -1), spot))
+
+    def step():
+        for a, bt, ad, spot in bases:
+            eb = a @ e @ a.T
+            ec = (e - bt @ (spot * eb) @ bt.T) * lyot
+            det = ad @ ec @ ad.T
+            (det.real ** 2 + det.imag ** 2).sum()
+
+    step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    return {"value": n_lambda * n_probe * 1e3 / ms, "unit": "PSFs/s", "ms_per_step": ms,
+            "form": "per-wavelength torch.matmul complex64 (cuBLAS FP32) MFT chain, 8 probes batched"}
+
+
 # ------------------------------------------------------------------------------ main arm
 
 def main():
@@ -403,6 +548,16 @@ def main():
                "d2h_bytes_per_step": int(host_out.numel() * 8), "ms_per_step": ms}
 
     extras = {}
+    if not args.no_coronagraph:
+        k_psf = max(3, args.steps // 2)
+        extras["coronagraph"] = coronagraph_bench(ctx, device, k_psf, max(1, min(3, args.warmup)), coro.MFT_3XTF32)
+        extras["coronagraph"]["value"] *= world
+        if args.bf16:
+            extras["coronagraph_3xbf16"] = coronagraph_bench(ctx, device, k_psf, 1, coro.MFT_3XBF16)
+        if rank == 0 and not args.no_plain:
+            extras["coronagraph"]["plain_gpu"] = coronagraph_plain(device, max(2, k_psf // 3))
+            extras["coronagraph"]["plain_gpu"]["speedup_of_coro"] = (
+                extras["coronagraph"]["value"] / world / extras["coronagraph"]["plain_gpu"]["value"])
     if rank == 0 and not args.no_plain:
         extras["plain_gpu"] = plain_gpu(n, maps_np, w, max(3, args.steps // 4), 2, device)
         extras["plain_gpu"]["speedup_of_coro"] = value / world / extras["plain_gpu"]["value"]

@@ -217,6 +217,71 @@ coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in, double np
                                int m, const double* du, int precision, coro_wavefront* out);
 
 /* ------------------------------------------------------------------------------------------
+ * Deformable mirror (Sec. 1.2: 32x32 / 48x48-actuator DMs sampled by hundreds of pixels).
+ * Gaussian influence g(d) = exp(-d^2/(2 sigma^2)), sigma = fwhm / (2 sqrt(2 ln 2)); actuator
+ * centres (q - (na-1)/2) * pitch, pixel centres (x - n/2) * pixelscale (metres).
+ * coro_dm_opd:       opd[b][y][x]  = scale * sum_{p,q} heights[b][p][q] g(y - y_p) g(x - x_q)
+ *                    (scale = 2 for the reflected OPD of a surface), device float arrays.
+ * coro_dm_correlate: grad[b][p][q] = scale * sum_{y,x} w[b][y][x] g(y - y_p) g(x - x_q), the
+ *                    transpose of coro_dm_opd (gradient of a loss w.r.t. heights from its
+ *                    gradient w.r.t. the OPD map). Terms below 1e-20 of the peak are skipped.
+ * ------------------------------------------------------------------------------------------ */
+coro_status coro_dm_opd(coro_ctx ctx, const float* heights, int batch, int na, double pitch, double fwhm,
+                        int n, double pixelscale, double scale, float* opd);
+coro_status coro_dm_correlate(coro_ctx ctx, const float* w, int batch, int n, double pixelscale, int na,
+                              double pitch, double fwhm, double scale, float* grad);
+
+/* ------------------------------------------------------------------------------------------
+ * Batched semi-analytic Lyot coronagraph (a7-a10; Sec. 1.1: the Soummer et al. method of
+ * matrix Fourier transforms around a small focal-plane mask), per item b:
+ *   E_B   = MFT(E_A; m_occ, du_occ)                      pupil -> occulter
+ *   E_C   = E_A - MFT^-1(spot . E_B)                      Babinet; spot = 1 for rho <= spot_radius
+ *   E_D   = E_C . Lyot stop (r <= lyot_frac * D/2)
+ *   E_det = MFT(E_D; m_det, du_det)
+ *   I = |E_det|^2 / peak[b],   S[b] = sum of I over dh_in <= rho <= dh_out (lambda/D)
+ * MFT conventions as in coro_propagate_mft (pupil pixel centre n/2, npix pixels across D).
+ * Six split-precision tensor-core GEMMs over the whole batch; spot, Babinet subtraction, Lyot
+ * stop, intensity and dark-hole sum are fused into GEMM epilogues. Items may have different
+ * occulter sizes m_occ (uneven per-wavelength sampling); n, npix, lyot_frac, m_det are shared.
+ * The plan owns its work buffers (bases, split operands, about 80 MB per item at n = 1024 with
+ * TF32) for its lifetime.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int m_occ;            /* occulter samples per axis, [16, 8192]                          */
+    double du_occ;        /* lambda/D per occulter pixel                                     */
+    double spot_radius;   /* occulting spot radius, lambda/D                                 */
+    double du_det;        /* lambda/D per detector pixel                                     */
+    double dh_in, dh_out; /* dark-hole annulus, lambda/D (inclusive)                         */
+} coro_lyot_item;
+
+typedef struct {
+    int batch;
+    int n;                /* pupil array n x n, [16, 8192]                                   */
+    double npix;          /* pupil pixels across D                                           */
+    double lyot_frac;     /* Lyot stop radius / pupil radius                                 */
+    int m_det;            /* detector samples per axis                                       */
+    const coro_lyot_item* items;  /* host [batch], copied                                    */
+    int precision;        /* CORO_MFT_3XTF32 or CORO_MFT_3XBF16                              */
+} coro_lyot_desc;
+
+coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc* desc, coro_plan* out);
+/* pupil: device complex64 [batch][n][n] (E_A). peak: host [batch] normalisation (NULL = 1).
+ * intensity: device float [batch][m_det][m_det] or NULL. field: device complex64
+ * [batch][m_det][m_det] (unnormalised E_det) or NULL. dh: host [batch] dark-hole sums or NULL
+ * (when given, the stream is synchronised). */
+coro_status coro_lyot_plan_execute(coro_plan plan, const void* pupil, const double* peak, float* intensity,
+                                   void* field, double* dh);
+/* Normalisation: peak_out[b] = max |E_det|^2 of the same chain with the occulter removed
+ * (E_D = E_A . Lyot stop). Synchronises the stream. */
+coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, double* peak_out);
+/* Run stages [first, first + count) only (for per-launch timing): 0 split of the pupil, 1-4 the
+ * GEMMs pupil->occulter (two), occulter->Lyot with Babinet (two), 5 the detector MFT with the
+ * intensity epilogue (two launches, preceded by one stream memset of the dark-hole sums).
+ * Running 0-5 in order equals coro_lyot_plan_execute without the host copy of dh. */
+coro_status coro_lyot_plan_execute_range(coro_plan plan, const void* pupil, const double* peak, float* intensity,
+                                         void* field, int first, int count);
+
+/* ------------------------------------------------------------------------------------------
  * Detector reductions (a9).
  * coro_intensity: out[b][y][x] = |E|^2 / norm[b] (norm NULL = 1); out device float.
  * coro_darkhole_sum: host_out[b] = sum over rho in [r_in, r_out] of |E|^2 / norm[b], with

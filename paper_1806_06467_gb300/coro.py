@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes as ct
 import os
+import weakref
 from typing import Sequence
 
 import numpy as np
@@ -52,8 +53,26 @@ class FresnelDesc(ct.Structure):
                 ("n_elements", ct.c_int), ("elements", ct.POINTER(Element)), ("flags", ct.c_int)]
 
 
+class LyotItem(ct.Structure):
+    _fields_ = [("m_occ", ct.c_int), ("du_occ", ct.c_double), ("spot_radius", ct.c_double),
+                ("du_det", ct.c_double), ("dh_in", ct.c_double), ("dh_out", ct.c_double)]
+
+
+class LyotDesc(ct.Structure):
+    _fields_ = [("batch", ct.c_int), ("n", ct.c_int), ("npix", ct.c_double), ("lyot_frac", ct.c_double),
+                ("m_det", ct.c_int), ("items", ct.POINTER(LyotItem)), ("precision", ct.c_int)]
+
+
 _P = ct.c_void_p
 _SIGS = {
+    "coro_dm_opd": (ct.c_int, [_P, _P, ct.c_int, ct.c_int, ct.c_double, ct.c_double, ct.c_int, ct.c_double,
+                               ct.c_double, _P]),
+    "coro_dm_correlate": (ct.c_int, [_P, _P, ct.c_int, ct.c_int, ct.c_double, ct.c_int, ct.c_double,
+                                     ct.c_double, ct.c_double, _P]),
+    "coro_lyot_plan_create": (ct.c_int, [_P, ct.POINTER(LyotDesc), ct.POINTER(_P)]),
+    "coro_lyot_plan_execute": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), _P, _P, ct.POINTER(ct.c_double)]),
+    "coro_lyot_plan_peak": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double)]),
+    "coro_lyot_plan_execute_range": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), _P, _P, ct.c_int, ct.c_int]),
     "coro_version": (ct.c_int, []),
     "coro_last_error": (ct.c_char_p, []),
     "coro_ctx_create": (ct.c_int, [ct.c_int, _P, ct.POINTER(_P)]),
@@ -129,8 +148,15 @@ class Context:
         h = ct.c_void_p()
         self.lib.check(self.lib.coro_ctx_create(device, ct.c_void_p(stream.cuda_stream), ct.byref(h)))
         self.handle = h
+        self._plans = weakref.WeakSet()
+
+    def _track(self, plan):
+        self._plans.add(plan)
 
     def close(self):
+        """Destroy every plan made on this context, then the context itself."""
+        for plan in list(getattr(self, "_plans", ())):
+            plan.close()
         if getattr(self, "handle", None):
             self.lib.coro_ctx_destroy(self.handle)
             self.handle = None
@@ -273,6 +299,80 @@ def darkhole_sum_noalloc(field, du, r_in: float, r_out: float, norm=None, stream
     return np.array(out[:])
 
 
+def dm_opd(ctx: Context, heights, pitch: float, fwhm: float, n: int, pixelscale: float, scale: float = 2.0,
+           out=None):
+    """heights: CUDA float32 [batch][na][na] (metres) -> OPD map [batch][n][n]."""
+    import torch
+    b, na, _ = heights.shape
+    if out is None:
+        out = torch.empty((b, n, n), dtype=torch.float32, device=heights.device)
+    ctx.lib.check(ctx.lib.coro_dm_opd(ctx.handle, ct.c_void_p(heights.data_ptr()), b, na, pitch, fwhm, n,
+                                      pixelscale, scale, ct.c_void_p(out.data_ptr())))
+    return out
+
+
+def dm_correlate(ctx: Context, w, pixelscale: float, na: int, pitch: float, fwhm: float, scale: float = 1.0,
+                 out=None):
+    """w: CUDA float32 [batch][n][n] -> [batch][na][na] (transpose of dm_opd)."""
+    import torch
+    b, n, _ = w.shape
+    if out is None:
+        out = torch.empty((b, na, na), dtype=torch.float32, device=w.device)
+    ctx.lib.check(ctx.lib.coro_dm_correlate(ctx.handle, ct.c_void_p(w.data_ptr()), b, n, pixelscale, na, pitch,
+                                            fwhm, scale, ct.c_void_p(out.data_ptr())))
+    return out
+
+
+class LyotPlan:
+    """Batched semi-analytic Lyot coronagraph (coro_lyot_plan_*). items: sequence of dicts with
+    m_occ, du_occ, spot_radius, du_det, dh_in, dh_out (lambda/D units)."""
+
+    def __init__(self, ctx: Context, *, n: int, npix: float, lyot_frac: float, m_det: int, items,
+                 precision: int = MFT_3XTF32):
+        self.ctx = ctx
+        self.batch = len(items)
+        self.n, self.m_det = n, m_det
+        self._items = (LyotItem * self.batch)(*[LyotItem(**it) for it in items])
+        d = LyotDesc(self.batch, n, npix, lyot_frac, m_det, self._items, precision)
+        h = ct.c_void_p()
+        ctx.lib.check(ctx.lib.coro_lyot_plan_create(ctx.handle, ct.byref(d), ct.byref(h)))
+        self.handle = h
+        ctx._track(self)
+
+    def peak(self, pupil) -> np.ndarray:
+        out = (ct.c_double * self.batch)()
+        self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_peak(self.handle, ct.c_void_p(pupil.data_ptr()), out))
+        return np.array(out[:])
+
+    def execute(self, pupil, peak=None, intensity=None, field=None, want_dh: bool = True):
+        """Returns the dark-hole sums (host) when want_dh; fills intensity / field if given."""
+        pk = None if peak is None else _dbl(np.broadcast_to(np.asarray(peak, float), (self.batch,)))
+        dh = (ct.c_double * self.batch)() if want_dh else None
+        self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_execute(
+            self.handle, ct.c_void_p(pupil.data_ptr()), pk,
+            None if intensity is None else ct.c_void_p(intensity.data_ptr()),
+            None if field is None else ct.c_void_p(field.data_ptr()), dh))
+        return np.array(dh[:]) if want_dh else None
+
+    def execute_range(self, pupil, first: int, count: int = 1, peak=None, intensity=None, field=None):
+        pk = None if peak is None else _dbl(np.broadcast_to(np.asarray(peak, float), (self.batch,)))
+        self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_execute_range(
+            self.handle, ct.c_void_p(pupil.data_ptr()), pk,
+            None if intensity is None else ct.c_void_p(intensity.data_ptr()),
+            None if field is None else ct.c_void_p(field.data_ptr()), first, count))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.coro_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class FresnelPlan:
     """Fused plane-by-plane Fresnel system (coro_fresnel_plan_*)."""
 
@@ -299,6 +399,7 @@ class FresnelPlan:
         h = ct.c_void_p()
         ctx.lib.check(ctx.lib.coro_fresnel_plan_create(ctx.handle, ct.byref(d), ct.byref(h)))
         self.handle = h
+        ctx._track(self)
 
     def execute(self, field) -> np.ndarray:
         ps = (ct.c_double * self.batch)()

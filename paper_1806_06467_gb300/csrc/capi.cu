@@ -201,7 +201,7 @@ extern "C" coro_status coro_ctx_destroy(coro_ctx ctx) {
     if (!ctx) return CORO_OK;
     {
         DeviceGuard g(ctx->device);
-        cudaStreamSynchronize(ctx->stream);
+        cudaDeviceSynchronize();          // the borrowed stream may already be gone
         for (auto& kv : ctx->tw32) cudaFree(kv.second);
         for (auto& kv : ctx->tw64) cudaFree(kv.second);
         if (ctx->work) cudaFree(ctx->work);
@@ -651,16 +651,11 @@ extern "C" coro_status coro_fft2(coro_ctx ctx, const coro_wavefront* wf, int dir
 
 // =========================================================================== fused Fresnel plan
 
-struct coro_plan_s {
-    virtual ~coro_plan_s() {}
-    virtual int kind() const = 0;
-    virtual int launches() const = 0;
-};
-
 namespace {
 
 struct FresnelPlan : coro_plan_s {
     coro_ctx ctx = nullptr;
+    int device = 0;                  // kept so that destruction never touches the context
     int dtype = CORO_C64, n = 0, batch = 0;
     std::vector<Op> ops;
     DevBlocks db;
@@ -668,11 +663,9 @@ struct FresnelPlan : coro_plan_s {
     int kind() const override { return 1; }
     int launches() const override { return (int)ops.size(); }
     ~FresnelPlan() override {
-        if (ctx) {
-            DeviceGuard g(ctx->device);
-            cudaStreamSynchronize(ctx->stream);
-            db.release();
-        }
+        DeviceGuard g(device);
+        cudaDeviceSynchronize();
+        db.release();
     }
 };
 
@@ -700,6 +693,7 @@ extern "C" coro_status coro_fresnel_plan_create(coro_ctx ctx, const coro_fresnel
     auto plan = std::unique_ptr<FresnelPlan>(new (std::nothrow) FresnelPlan);
     if (!plan) { set_error("out of host memory"); return CORO_ENOMEM; }
     plan->ctx = ctx;
+    plan->device = ctx->device;
     plan->dtype = d->dtype;
     plan->n = d->n;
     plan->batch = d->batch;

@@ -20,6 +20,13 @@ struct coro_ctx_s {
     int* err = nullptr;          // device flag set by kernels whose bounded waits expired
 };
 
+// Base of every plan handle (Fresnel systems: kind 1, Lyot coronagraphs: kind 2).
+struct coro_plan_s {
+    virtual ~coro_plan_s() {}
+    virtual int kind() const = 0;
+    virtual int launches() const = 0;
+};
+
 namespace coro {
 
 void set_error(const char* fmt, ...);

@@ -1,0 +1,310 @@
+// lyot.cu -- batched semi-analytic Lyot coronagraph (Sec. 1.1: the Soummer et al. method
+// built from matrix Fourier transforms of modest arrays around a small focal-plane mask).
+//
+// Per item (wavelength x probe state), with E_A the pupil field:
+//   G1  Z1 = (E_A . A_occ^T)^T                       split, transposed
+//   G2  X_B = spot . s_occ (Z1 . A_occ^T)^T           = spot . MFT(E_A)       (pupil -> occulter)
+//   G3  Z3 = (X_B . B^T)^T
+//   G4  E_D = Lyot . (E_A - s_occ (Z3 . B^T)^T)       Babinet, in place over E_A's planes
+//   G5  Z5 = (E_D . A_det^T)^T
+//   G6  I = |s_det (Z5 . A_det^T)^T|^2 / peak,   S = sum over the dark-hole annulus of I
+// Every G is one launch of the split-precision tensor-core GEMM (tc_gemm.cu) over the whole
+// batch; the spot, the Babinet subtraction, the Lyot stop, the intensity and the dark-hole sum
+// are epilogues, so the only extra pass is the split of E_A.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "capi_common.h"
+#include "tc_gemm.cuh"
+
+using namespace coro;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct LyotPlan : coro_plan_s {
+    coro_ctx ctx = nullptr;
+    bool bf16 = false;
+    int batch = 0, n = 0, m_det = 0, m_occ_max = 0;
+    double npix = 0;
+    std::vector<coro_lyot_item> items;
+    std::vector<Buf> bufs;
+    TcOperand XA{}, Z1{}, XB{}, Z3{}, Z5{}, W1{}, W2{}, W3{};
+    CUtensorMap mXA, mZ1, mXB, mZ3, mZ5, mW1, mW2, mW3;
+    TcItem* dev_items = nullptr;       // [6][batch]
+    std::vector<TcItem> host_items;    // [6][batch]
+    int* keep_lyot = nullptr;          // [batch] Lyot-stop radius^2 (pupil pixels)
+    double* dh = nullptr;              // [batch]
+    float* peak = nullptr;             // [batch]
+    int device = 0;                    // kept so that destruction never touches the context
+    int kind() const override { return 2; }
+    int launches() const override { return 7; }
+    ~LyotPlan() override {
+        DeviceGuard g(device);
+        cudaDeviceSynchronize();
+        for (auto& b : bufs) cudaFree(b.p);
+    }
+    void* alloc(size_t bytes, coro_status* st) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) { *st = cuda_fail(e, "coro_lyot_plan_create: cudaMalloc"); return nullptr; }
+        bufs.push_back({p, bytes});
+        e = cudaMemsetAsync(p, 0, bytes, ctx->stream);   // padding of every operand stays zero
+        if (e != cudaSuccess) { *st = cuda_fail(e, "cudaMemsetAsync"); return nullptr; }
+        return p;
+    }
+    bool make(TcOperand& op, int nb, int rows, int cols, coro_status* st) {
+        op.batch = nb;
+        op.rows = rows;
+        op.cols = cols;
+        op.ld = tc_ld(cols, bf16);
+        op.base = alloc((size_t)4 * nb * rows * op.ld * tc_elem_size(bf16), st);
+        return op.base != nullptr;
+    }
+};
+
+int clamp_thr(long long v) { return v > 0x3fffffffLL ? 0x3fffffff : (int)v; }
+
+}  // namespace
+
+extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc* d, coro_plan* out) {
+    clear_error();
+    if (!ctx || !d || !out || !d->items) { set_error("coro_lyot_plan_create: NULL argument"); return CORO_EINVAL; }
+    *out = nullptr;
+    if (d->precision != CORO_MFT_3XTF32 && d->precision != CORO_MFT_3XBF16) {
+        set_error("coro_lyot_plan_create: precision must be CORO_MFT_3XTF32 or CORO_MFT_3XBF16");
+        return CORO_EINVAL;
+    }
+    if (d->batch < 1 || d->batch > 65535) { set_error("coro_lyot_plan_create: batch %d", d->batch); return CORO_ESIZE; }
+    if (d->n < 16 || d->n > 8192 || d->m_det < 16 || d->m_det > 8192) {
+        set_error("coro_lyot_plan_create: n = %d, m_det = %d outside [16, 8192]", d->n, d->m_det);
+        return CORO_ESIZE;
+    }
+    if (!(d->npix > 0) || !(d->lyot_frac > 0)) { set_error("coro_lyot_plan_create: npix and lyot_frac must be > 0"); return CORO_EINVAL; }
+    int m_occ_max = 0;
+    for (int b = 0; b < d->batch; ++b) {
+        const coro_lyot_item& it = d->items[b];
+        if (it.m_occ < 16 || it.m_occ > 8192) { set_error("item %d: m_occ = %d outside [16, 8192]", b, it.m_occ); return CORO_ESIZE; }
+        if (!(it.du_occ > 0) || !(it.du_det > 0) || !(it.spot_radius >= 0) || !(it.dh_in >= 0) || !(it.dh_out >= it.dh_in)) {
+            set_error("item %d: need du_occ, du_det > 0, spot_radius >= 0, 0 <= dh_in <= dh_out", b);
+            return CORO_EINVAL;
+        }
+        if (it.m_occ > m_occ_max) m_occ_max = it.m_occ;
+    }
+    DeviceGuard g(ctx->device);
+    auto p = std::unique_ptr<LyotPlan>(new (std::nothrow) LyotPlan);
+    if (!p) { set_error("out of host memory"); return CORO_ENOMEM; }
+    p->ctx = ctx;
+    p->device = ctx->device;
+    p->bf16 = d->precision == CORO_MFT_3XBF16;
+    p->batch = d->batch;
+    p->n = d->n;
+    p->npix = d->npix;
+    p->m_det = d->m_det;
+    p->m_occ_max = m_occ_max;
+    p->items.assign(d->items, d->items + d->batch);
+    const int B = d->batch, n = d->n, md = d->m_det;
+
+    // distinct bases: occulter (m_occ, du_occ) and detector du_det
+    std::map<std::pair<int, double>, int> occ_id;
+    std::map<double, int> det_id;
+    std::vector<int> oi(B), di(B);
+    for (int b = 0; b < B; ++b) {
+        auto ko = std::make_pair(d->items[b].m_occ, d->items[b].du_occ);
+        if (!occ_id.count(ko)) { const int id = (int)occ_id.size(); occ_id[ko] = id; }
+        if (!det_id.count(d->items[b].du_det)) { const int id = (int)det_id.size(); det_id[d->items[b].du_det] = id; }
+        oi[b] = occ_id[ko];
+        di[b] = det_id[d->items[b].du_det];
+    }
+    coro_status st = CORO_OK;
+    const int no = (int)occ_id.size(), nd = (int)det_id.size();
+    if (!p->make(p->XA, B, n, n, &st) || !p->make(p->Z1, B, m_occ_max, n, &st) || !p->make(p->XB, B, m_occ_max, m_occ_max, &st) ||
+        !p->make(p->Z3, B, n, m_occ_max, &st) || !p->make(p->Z5, B, md, n, &st) || !p->make(p->W1, no, m_occ_max, n, &st) ||
+        !p->make(p->W2, no, n, m_occ_max, &st) || !p->make(p->W3, nd, md, n, &st))
+        return st;
+    cudaError_t e = cudaSuccess;
+    // A_occ[u][j] = exp(-2 pi i u' j' du/npix), B^T[j][u] = exp(+2 pi i j' u' du/npix), A_det likewise
+    for (auto& kv : occ_id) {
+        const double c = kv.first.second / d->npix;
+        const int m = kv.first.first;
+        if (e == cudaSuccess) e = tc_basis_one(p->bf16, c, -1, p->W1, kv.second, m, n, ctx->stream);
+        if (e == cudaSuccess) e = tc_basis_one(p->bf16, c, +1, p->W2, kv.second, n, m, ctx->stream);
+    }
+    for (auto& kv : det_id)
+        if (e == cudaSuccess) e = tc_basis_one(p->bf16, kv.first / d->npix, -1, p->W3, kv.second, md, n, ctx->stream);
+    TcOperand* ops[8] = {&p->XA, &p->Z1, &p->XB, &p->Z3, &p->Z5, &p->W1, &p->W2, &p->W3};
+    CUtensorMap* maps[8] = {&p->mXA, &p->mZ1, &p->mXB, &p->mZ3, &p->mZ5, &p->mW1, &p->mW2, &p->mW3};
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = tc_make_operand_map(*ops[i], p->bf16, maps[i]);
+    if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_create: bases / tensor maps");
+
+    // per-GEMM item tables
+    const double pupil_pitch = 1.0 / d->npix;            // pupil coordinates in units of D
+    const int lyot_thr = clamp_thr(disk_threshold(0.5 * d->lyot_frac, pupil_pitch, false));
+    const int all = 0x7fffffff;
+    p->host_items.resize((size_t)6 * B);
+    std::vector<int> keep(B, lyot_thr);
+    for (int b = 0; b < B; ++b) {
+        const coro_lyot_item& it = d->items[b];
+        const int mo = it.m_occ;
+        const float s_occ = (float)(it.du_occ / d->npix), s_det = (float)(it.du_det / d->npix);
+        const int spot = clamp_thr(disk_threshold(it.spot_radius, it.du_occ, false));
+        const int dh_lo = clamp_thr(disk_threshold(it.dh_in, it.du_det, true) + 1);
+        const int dh_hi = clamp_thr(disk_threshold(it.dh_out, it.du_det, false));
+        TcItem* h = p->host_items.data();
+        h[0 * B + b] = TcItem{n, mo, n, b, oi[b], 0, all, 1.0f, 1.0f};
+        h[1 * B + b] = TcItem{mo, mo, n, b, oi[b], 0, spot, s_occ, 1.0f};
+        h[2 * B + b] = TcItem{mo, n, mo, b, oi[b], 0, all, 1.0f, 1.0f};
+        h[3 * B + b] = TcItem{n, n, mo, b, oi[b], 0, lyot_thr, s_occ, 1.0f};
+        h[4 * B + b] = TcItem{n, md, n, b, di[b], 0, all, 1.0f, 1.0f};
+        h[5 * B + b] = TcItem{md, md, n, b, di[b], dh_lo, dh_hi, s_det, 1.0f};
+    }
+    p->dev_items = (TcItem*)p->alloc(p->host_items.size() * sizeof(TcItem), &st);
+    p->keep_lyot = p->dev_items ? (int*)p->alloc(B * sizeof(int), &st) : nullptr;
+    p->dh = p->keep_lyot ? (double*)p->alloc(B * sizeof(double), &st) : nullptr;
+    p->peak = p->dh ? (float*)p->alloc(B * sizeof(float), &st) : nullptr;
+    if (!p->peak) return st;
+    e = cudaMemcpyAsync(p->dev_items, p->host_items.data(), p->host_items.size() * sizeof(TcItem), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->keep_lyot, keep.data(), B * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_create");
+    *out = p.release();
+    return CORO_OK;
+}
+
+namespace {
+
+// G5 + G6 on the operand already in XA planes; intensity epilogue.
+cudaError_t detector_gemms(LyotPlan* p, const double* peak_host, float* intensity, void* field, bool track_peak) {
+    const int B = p->batch, n = p->n, md = p->m_det;
+    cudaStream_t s = p->ctx->stream;
+    TcArgs a{};
+    a.err = p->ctx->err;
+    a.items = p->dev_items + 4 * B;
+    a.dst = p->Z5.base;
+    a.dst_bstride = (long long)4 * p->Z5.rows * p->Z5.ld;
+    a.dst_rows = p->Z5.rows;
+    a.dst_ld = p->Z5.ld;
+    cudaError_t e = tc_launch(p->bf16, TC_EPI_SPLITT, p->mXA, p->mW3, n, md, n, B, a, s);
+    if (e != cudaSuccess) return e;
+    if (peak_host) {                                  // normalisation goes into the item table
+        std::vector<TcItem> g6(p->host_items.begin() + 5 * B, p->host_items.begin() + 6 * B);
+        for (int b = 0; b < B; ++b) g6[b].inv_peak = (float)(1.0 / peak_host[b]);
+        e = cudaMemcpyAsync(p->dev_items + 5 * B, g6.data(), B * sizeof(TcItem), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        e = cudaMemcpyAsync(p->dev_items + 5 * B, p->host_items.data() + 5 * B, B * sizeof(TcItem), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(p->dh, 0, B * sizeof(double), s);
+    if (e == cudaSuccess && track_peak) e = cudaMemsetAsync(p->peak, 0, B * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    TcArgs b6{};
+    b6.err = p->ctx->err;
+    b6.items = p->dev_items + 5 * B;
+    b6.dst = intensity;
+    b6.dst_bstride = (long long)md * md;
+    b6.dst_rows = md;
+    b6.dst_ld = md;
+    b6.c64 = (float2*)field;
+    b6.c64_bstride = (long long)md * md;
+    b6.c64_ld = md;
+    b6.dh_acc = p->dh;
+    b6.peak = track_peak ? p->peak : nullptr;
+    return tc_launch(p->bf16, TC_EPI_INTENSITY, p->mZ5, p->mW3, md, md, n, B, b6, s);
+}
+
+}  // namespace
+
+namespace {
+
+// Stages 0 (split of the pupil), 1-4 (G1-G4), 5 (G5 + G6 with the intensity epilogue).
+cudaError_t run_stages(LyotPlan* p, const void* pupil, const double* peak, float* intensity, void* field, int first,
+                       int last) {
+    const int B = p->batch, n = p->n, mo = p->m_occ_max;
+    cudaStream_t s = p->ctx->stream;
+    cudaError_t e = cudaSuccess;
+    auto gemm = [&](int gi, int epi, const CUtensorMap& mx, const CUtensorMap& mw, const TcOperand& dst, int mm, int nn, int kk) {
+        if (e != cudaSuccess || gi + 1 < first || gi + 1 > last) return;
+        TcArgs a{};
+        a.err = p->ctx->err;
+        a.items = p->dev_items + gi * B;
+        a.dst = dst.base;
+        a.dst_bstride = (long long)4 * dst.rows * dst.ld;
+        a.dst_rows = dst.rows;
+        a.dst_ld = dst.ld;
+        e = tc_launch(p->bf16, epi, mx, mw, mm, nn, kk, B, a, s);
+    };
+    if (first <= 0 && last >= 0) e = tc_split(p->bf16, (const float2*)pupil, (long long)n * n, n, p->XA, s);
+    gemm(0, TC_EPI_SPLITT, p->mXA, p->mW1, p->Z1, n, mo, n);     // G1
+    gemm(1, TC_EPI_SPLITT, p->mZ1, p->mW1, p->XB, mo, mo, n);    // G2 (x spot)
+    gemm(2, TC_EPI_SPLITT, p->mXB, p->mW2, p->Z3, mo, n, mo);    // G3
+    gemm(3, TC_EPI_BABINET, p->mZ3, p->mW2, p->XA, n, n, mo);    // G4 (Babinet, x Lyot)
+    if (e == cudaSuccess && first <= 5 && last >= 5) e = detector_gemms(p, peak, intensity, field, false);
+    return e;
+}
+
+}  // namespace
+
+extern "C" coro_status coro_lyot_plan_execute_range(coro_plan plan, const void* pupil, const double* peak,
+                                                    float* intensity, void* field, int first, int count) {
+    clear_error();
+    if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_execute_range: not a Lyot plan"); return CORO_EINVAL; }
+    if (!pupil || first < 0 || count < 0 || first + count > 6) {
+        set_error("coro_lyot_plan_execute_range: pupil NULL or stage range [%d, %d) outside [0, 6)", first, first + count);
+        return CORO_EINVAL;
+    }
+    auto* p = static_cast<LyotPlan*>(plan);
+    if (peak)
+        for (int b = 0; b < p->batch; ++b)
+            if (!(peak[b] > 0)) { set_error("coro_lyot_plan_execute_range: peak[%d] must be > 0", b); return CORO_EINVAL; }
+    DeviceGuard g(p->ctx->device);
+    cudaError_t e = run_stages(p, pupil, peak, intensity, field, first, first + count - 1);
+    return e == cudaSuccess ? CORO_OK : cuda_fail(e, "coro_lyot_plan_execute_range");
+}
+
+extern "C" coro_status coro_lyot_plan_execute(coro_plan plan, const void* pupil, const double* peak, float* intensity,
+                                              void* field, double* dh) {
+    clear_error();
+    if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_execute: not a Lyot plan"); return CORO_EINVAL; }
+    if (!pupil) { set_error("coro_lyot_plan_execute: pupil is NULL"); return CORO_EINVAL; }
+    auto* p = static_cast<LyotPlan*>(plan);
+    const int B = p->batch;
+    if (peak)
+        for (int b = 0; b < B; ++b)
+            if (!(peak[b] > 0)) { set_error("coro_lyot_plan_execute: peak[%d] must be > 0", b); return CORO_EINVAL; }
+    DeviceGuard g(p->ctx->device);
+    cudaStream_t s = p->ctx->stream;
+    cudaError_t e = run_stages(p, pupil, peak, intensity, field, 0, 5);
+    if (e == cudaSuccess && dh) {
+        e = cudaMemcpyAsync(dh, p->dh, B * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_execute");
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, double* peak_out) {
+    clear_error();
+    if (!plan || plan->kind() != 2 || !pupil || !peak_out) { set_error("coro_lyot_plan_peak: bad argument"); return CORO_EINVAL; }
+    auto* p = static_cast<LyotPlan*>(plan);
+    const int B = p->batch, n = p->n;
+    DeviceGuard g(p->ctx->device);
+    cudaStream_t s = p->ctx->stream;
+    // occulter removed: E_D = E_A . Lyot stop, then the detector MFT
+    cudaError_t e = tc_split(p->bf16, (const float2*)pupil, (long long)n * n, n, p->XA, s, p->keep_lyot);
+    if (e == cudaSuccess) e = detector_gemms(p, nullptr, nullptr, nullptr, true);
+    std::vector<float> pk(B);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pk.data(), p->peak, B * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_peak");
+    for (int b = 0; b < B; ++b) peak_out[b] = pk[b];
+    return CORO_OK;
+}

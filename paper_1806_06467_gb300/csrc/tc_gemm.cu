@@ -20,8 +20,10 @@ constexpr int PLANE_BYTES = 128 * 64;    // 128 rows x 64-byte K slice
 constexpr int OPER_BYTES = 4 * PLANE_BYTES;
 constexpr int STAGE_BYTES = 2 * OPER_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int THREADS = 192;             // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int EPI_WARPS = 8;             // two per TMEM lane quarter, 64 output columns each
+constexpr int THREADS = 64 + 32 * EPI_WARPS;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr uint32_t TMEM_COLS = 512;      // two accumulator buffers of (128 re + 128 im) columns
+constexpr int kChunk = 1;                // K slices summed inside one tensor-core accumulator
 
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
@@ -49,6 +51,18 @@ __device__ __forceinline__ void store_split(void* base, size_t plane, size_t off
     }
 }
 
+template <bool BF16>
+__device__ __forceinline__ float2 load_split(const void* base, size_t plane, size_t off) {
+    if constexpr (BF16) {
+        const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(base);
+        return make_float2(__bfloat162float(p[off]) + __bfloat162float(p[2 * plane + off]),
+                           __bfloat162float(p[plane + off]) + __bfloat162float(p[3 * plane + off]));
+    } else {
+        const float* p = reinterpret_cast<const float*>(base);
+        return make_float2(p[off] + p[2 * plane + off], p[plane + off] + p[3 * plane + off]);
+    }
+}
+
 template <bool BF16, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw, const TcArgs a) {
@@ -61,16 +75,18 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* accf = empty + STAGES;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+    uint64_t* tfull = empty + STAGES;                // accumulator buffer b holds a finished chunk
+    uint64_t* tempty = tfull + 2;                    // accumulator buffer b has been drained
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int KE = BF16 ? 32 : 16;               // real elements per 64-byte K slice
     const int kblocks = (it.K + KE - 1) / KE;
+    const int nchunks = (kblocks + kChunk - 1) / kChunk;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-        tc::mbar_init(accf, 1);
+        for (int s = 0; s < 2; ++s) { tc::mbar_init(&tfull[s], 1); tc::mbar_init(&tempty[s], EPI_WARPS); }
         tc::fence_mbar_init();
         tc::prefetch_tmap(&mx);
         tc::prefetch_tmap(&mw);
@@ -98,15 +114,23 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            // Each chunk of kChunk slices starts a fresh accumulator in one of two TMEM
+            // buffers; the epilogue warps add finished chunks into FP32 registers with
+            // round-to-nearest, so the tensor-core accumulator never sums more than a chunk.
             constexpr uint32_t ID_POS = tc::idesc<BF16>(BM, BN, false);
             constexpr uint32_t ID_NEG = tc::idesc<BF16>(BM, BN, true);
-            const uint32_t d_re = tbase, d_im = tbase + 128;
             bool ok = true;
             for (int k = 0; k < kblocks && ok; ++k) {
                 const int s = k % STAGES;
                 const uint32_t ph = (k / STAGES) & 1;
+                const int c = k / kChunk, buf = c & 1, kc = k % kChunk;
+                if (kc == 0) {
+                    if (!(ok = tc::mbar_wait(&tempty[buf], ((c >> 1) & 1) ^ 1, a.err, 4))) break;
+                    tc::tc_fence_after();
+                }
                 if (!(ok = tc::mbar_wait(&full[s], ph, a.err, 2))) break;
                 tc::tc_fence_after();
+                const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
                 const uint32_t xa = tc::smem_u32(smem + s * STAGE_BYTES);
                 const uint32_t wa = xa + OPER_BYTES;
 #pragma unroll
@@ -118,7 +142,7 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
                         const uint64_t ai = tc::sdesc_sw64(xa + (2 * xs + 1) * PLANE_BYTES + kk * 32);
                         const uint64_t br = tc::sdesc_sw64(wa + (2 * ws + 0) * PLANE_BYTES + kk * 32);
                         const uint64_t bi = tc::sdesc_sw64(wa + (2 * ws + 1) * PLANE_BYTES + kk * 32);
-                        const uint32_t acc = (k | kk | t) ? 1u : 0u;
+                        const uint32_t acc = (kc | kk | t) ? 1u : 0u;
                         tc::umma<BF16>(d_re, ar, br, ID_POS, acc);
                         tc::umma<BF16>(d_re, ai, bi, ID_NEG, 1u);
                         tc::umma<BF16>(d_im, ar, bi, ID_POS, acc);
@@ -126,32 +150,50 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
                     }
                 }
                 tc::umma_commit(&empty[s]);             // frees the stage once these MMAs retire
+                if (kc == kChunk - 1 || k == kblocks - 1) tc::umma_commit(&tfull[buf]);
             }
-            if (ok) tc::umma_commit(accf);
         }
     } else {
-        // ------------------------------------------------------------ epilogue (warps 2..5)
+        // ------------------------------------------------------------ epilogue (warps 2..9)
         const int q = warp & 3;                          // TMEM lane quarter this warp may read
+        const int half = (warp - 2) >> 2;                // which 64 of the 128 output columns
         const int row = q * 32 + lane;
         const int m = m0 + row;
-        const bool ok = tc::mbar_wait(accf, 0, a.err, 3);
-        __syncwarp();
-        tc::tc_fence_after();
-        double dh = 0.0;
-        if (ok) {
-            const int kx = m - it.M / 2;
-#pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
-                uint32_t rr[32], ri[32];
-                tc::tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + c, rr);
-                tc::tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + 128 + c, ri);
+        const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16) + half * 64;
+        float acc_re[64], acc_im[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) { acc_re[j] = 0.f; acc_im[j] = 0.f; }
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int buf = c & 1;
+            if (!(ok = tc::mbar_wait(&tfull[buf], (c >> 1) & 1, a.err, 3))) break;
+            __syncwarp();
+            tc::tc_fence_after();
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                uint32_t r[32];
+                tc::tmem_ld32(lane_base + buf * 256 + part * 32, r);
                 tc::tmem_ld_wait();
-                if (m >= it.M) continue;
-#pragma unroll 4
-                for (int j = 0; j < 32; ++j) {
-                    const int n = n0 + c + j;
-                    if (n >= it.N) break;
-                    float re = __uint_as_float(rr[j]) * it.scale, im = __uint_as_float(ri[j]) * it.scale;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc_re[part * 32 + j] += __uint_as_float(r[j]);
+                tc::tmem_ld32(lane_base + buf * 256 + 128 + part * 32, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc_im[part * 32 + j] += __uint_as_float(r[j]);
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[buf]);
+        }
+        double dh = 0.0;
+        float pk = 0.f;
+        if (ok && m < it.M) {
+            const int kx = m - it.M / 2;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int n = n0 + half * 64 + j;
+                if (n < it.N) {
+                    float re = acc_re[j] * it.scale, im = acc_im[j] * it.scale;
                     const int ky = n - it.N / 2;
                     const int r2 = kx * kx + ky * ky;
                     const bool keep = r2 >= it.mask_lo && r2 <= it.mask_hi;
@@ -163,24 +205,31 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
                         const size_t plane = (size_t)a.dst_rows * a.dst_ld;
                         store_split<BF16>(a.dst, plane, b * a.dst_bstride + (size_t)n * a.dst_ld + m, re, im);
                     } else if constexpr (EPI == TC_EPI_BABINET) {
-                        const float2 e = a.ea[b * a.ea_bstride + (size_t)n * a.ea_ld + m];
+                        const size_t plane = (size_t)a.dst_rows * a.dst_ld;
+                        const size_t off = b * a.dst_bstride + (size_t)n * a.dst_ld + m;
+                        const float2 e = load_split<BF16>(a.dst, plane, off);
                         re = keep ? e.x - re : 0.f;
                         im = keep ? e.y - im : 0.f;
-                        const size_t plane = (size_t)a.dst_rows * a.dst_ld;
-                        store_split<BF16>(a.dst, plane, b * a.dst_bstride + (size_t)n * a.dst_ld + m, re, im);
+                        store_split<BF16>(a.dst, plane, off, re, im);
                         if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(re, im);
                     } else {
                         const float inten = (re * re + im * im) * it.inv_peak;
                         if (a.dst) reinterpret_cast<float*>(a.dst)[b * a.dst_bstride + (size_t)n * a.dst_ld + m] = inten;
                         if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(re, im);
                         if (keep) dh += (double)inten;
+                        pk = fmaxf(pk, inten);
                     }
                 }
             }
         }
         if constexpr (EPI == TC_EPI_INTENSITY) {
-            for (int o = 16; o > 0; o >>= 1) dh += __shfl_down_sync(0xffffffffu, dh, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                dh += __shfl_down_sync(0xffffffffu, dh, o);
+                pk = fmaxf(pk, __shfl_down_sync(0xffffffffu, pk, o));
+            }
             if (lane == 0 && dh != 0.0 && a.dh_acc) atomicAdd(a.dh_acc + b, dh);
+            // intensities are non-negative, so their IEEE bit patterns order like integers
+            if (lane == 0 && a.peak) atomicMax(reinterpret_cast<int*>(a.peak) + b, __float_as_int(pk));
         }
     }
     tc::tc_fence_before();
@@ -195,34 +244,40 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
 
 template <bool BF16>
 __global__ void split_kernel(const float2* __restrict__ src, long long sb, int sld, void* dst, int rows, int cols,
-                             int ld) {
+                             int ld, const int* __restrict__ keep_r2) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y, b = blockIdx.z;
     if (k >= ld) return;
     float2 v = make_float2(0.f, 0.f);
     if (k < cols) v = src[b * sb + (size_t)r * sld + k];
+    if (keep_r2) {
+        const int kx = k - cols / 2, ky = r - rows / 2;
+        if (kx * kx + ky * ky > keep_r2[b]) v = make_float2(0.f, 0.f);
+    }
     const size_t plane = (size_t)rows * ld;
     store_split<BF16>(dst, plane, (size_t)b * 4 * plane + (size_t)r * ld + k, v.x, v.y);
 }
 
 // W[r][k] = exp(sign 2 pi i (r - rows/2)(k - cols/2) c_b): FP64 phase reduced to its
-// fractional cycle, then rounded to FP32 and split.
+// fractional cycle, then rounded to FP32 and split. plane_rows = rows of the operand planes
+// (>= rows), item = first item written (grid z offsets from it).
 template <bool BF16>
-__global__ void basis_kernel(const double* __restrict__ c, int sign, void* dst, int rows, int cols, int ld) {
+__global__ void basis_kernel(const double* __restrict__ c, double c_one, int sign, void* dst, int rows, int cols,
+                             int ld, int plane_rows, int item) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y, b = blockIdx.z;
+    const int r = blockIdx.y, b = blockIdx.z + item;
     if (k >= ld) return;
     float re = 0.f, im = 0.f;
     if (k < cols) {
         const long long rr = (long long)r - rows / 2, kk = (long long)k - cols / 2;
-        double cyc = (double)(rr * kk) * c[b];
+        double cyc = (double)(rr * kk) * (c ? c[b] : c_one);
         cyc -= rint(cyc);
         double s, co;
         sincospi(2.0 * cyc, &s, &co);
         re = (float)co;
         im = (float)(sign < 0 ? -s : s);
     }
-    const size_t plane = (size_t)rows * ld;
+    const size_t plane = (size_t)plane_rows * ld;
     store_split<BF16>(dst, plane, (size_t)b * 4 * plane + (size_t)r * ld + k, re, im);
 }
 
@@ -297,17 +352,26 @@ cudaError_t tc_launch(bool bf16, int epi, const CUtensorMap& mx, const CUtensorM
 }
 
 cudaError_t tc_split(bool bf16, const float2* src, long long src_bstride, int src_ld, const TcOperand& dst,
-                     cudaStream_t stream) {
+                     cudaStream_t stream, const int* keep_r2) {
     dim3 grid((dst.ld + 127) / 128, dst.rows, dst.batch);
-    if (bf16) split_kernel<true><<<grid, 128, 0, stream>>>(src, src_bstride, src_ld, dst.base, dst.rows, dst.cols, dst.ld);
-    else split_kernel<false><<<grid, 128, 0, stream>>>(src, src_bstride, src_ld, dst.base, dst.rows, dst.cols, dst.ld);
+    if (bf16) split_kernel<true><<<grid, 128, 0, stream>>>(src, src_bstride, src_ld, dst.base, dst.rows, dst.cols, dst.ld, keep_r2);
+    else split_kernel<false><<<grid, 128, 0, stream>>>(src, src_bstride, src_ld, dst.base, dst.rows, dst.cols, dst.ld, keep_r2);
     return cudaGetLastError();
 }
 
 cudaError_t tc_basis(bool bf16, const double* c, int sign, const TcOperand& dst, cudaStream_t stream) {
     dim3 grid((dst.ld + 127) / 128, dst.rows, dst.batch);
-    if (bf16) basis_kernel<true><<<grid, 128, 0, stream>>>(c, sign, dst.base, dst.rows, dst.cols, dst.ld);
-    else basis_kernel<false><<<grid, 128, 0, stream>>>(c, sign, dst.base, dst.rows, dst.cols, dst.ld);
+    if (bf16) basis_kernel<true><<<grid, 128, 0, stream>>>(c, 0.0, sign, dst.base, dst.rows, dst.cols, dst.ld, dst.rows, 0);
+    else basis_kernel<false><<<grid, 128, 0, stream>>>(c, 0.0, sign, dst.base, dst.rows, dst.cols, dst.ld, dst.rows, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_basis_one(bool bf16, double c, int sign, const TcOperand& dst, int item, int rows_valid,
+                         int cols_valid, cudaStream_t stream) {
+    if (rows_valid > dst.rows || cols_valid > dst.ld || item < 0 || item >= dst.batch) return cudaErrorInvalidValue;
+    dim3 grid((dst.ld + 127) / 128, rows_valid, 1);
+    if (bf16) basis_kernel<true><<<grid, 128, 0, stream>>>(nullptr, c, sign, dst.base, rows_valid, cols_valid, dst.ld, dst.rows, item);
+    else basis_kernel<false><<<grid, 128, 0, stream>>>(nullptr, c, sign, dst.base, rows_valid, cols_valid, dst.ld, dst.rows, item);
     return cudaGetLastError();
 }
 

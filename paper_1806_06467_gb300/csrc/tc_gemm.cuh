@@ -23,8 +23,8 @@ namespace coro {
 enum TcEpi : int {
     TC_EPI_C64T = 0,       // complex64 Y^T * scale
     TC_EPI_SPLITT = 1,     // planar split of (Y^T * scale * mask) -> operand of the next GEMM
-    TC_EPI_BABINET = 2,    // (E_A - Y^T * scale) * mask -> planar split (+ optional complex64 copy)
-    TC_EPI_INTENSITY = 3   // |Y^T * scale|^2 * inv_peak -> float image + dark-hole sum
+    TC_EPI_BABINET = 2,    // dst planes hold E_A; overwritten in place by (E_A - Y^T scale) * mask
+    TC_EPI_INTENSITY = 3   // |Y^T * scale|^2 * inv_peak -> float image, dark-hole sum, peak
 };
 
 // Per-item geometry and epilogue constants.
@@ -42,13 +42,11 @@ struct TcArgs {
     void* dst;                       // split planes [b][4][dst_rows][dst_ld] or complex64/float [b][dst_rows][dst_ld]
     long long dst_bstride;           // elements per item
     int dst_rows, dst_ld;
-    const float2* ea;                // Babinet minuend [b][ea_rows][ea_ld]
-    long long ea_bstride;
-    int ea_ld;
     float2* c64;                     // optional complex64 copy [b][rows][c64_ld]
     long long c64_bstride;
     int c64_ld;
-    double* dh_acc;                  // dark-hole sums [b]
+    double* dh_acc;                  // dark-hole sums [b] (intensity epilogue)
+    float* peak;                     // running max of the intensity [b] (intensity epilogue), or NULL
 };
 
 // Host side (tc_gemm.cu).
@@ -61,9 +59,14 @@ cudaError_t tc_make_operand_map(const TcOperand& op, bool bf16, CUtensorMap* map
 cudaError_t tc_launch(bool bf16, int epi, const CUtensorMap& mx, const CUtensorMap& mw, int max_m, int max_n,
                       int max_k, int batch, const TcArgs& args, cudaStream_t stream);
 
-// complex64 [batch][rows][cols] (leading dimension src_ld) -> planar split operand
+// complex64 [batch][rows][cols] (leading dimension src_ld) -> planar split operand; with
+// keep_r2 (device [batch]) samples whose centred (row, col) radius^2 exceeds keep_r2[b] become 0
 cudaError_t tc_split(bool bf16, const float2* src, long long src_bstride, int src_ld, const TcOperand& dst,
-                     cudaStream_t stream);
+                     cudaStream_t stream, const int* keep_r2 = nullptr);
+// W[r][k] for one basis (index `item` of dst), rows_valid x cols_valid centred on their own
+// halves; everything else in that item's planes is left untouched
+cudaError_t tc_basis_one(bool bf16, double c, int sign, const TcOperand& dst, int item, int rows_valid,
+                         int cols_valid, cudaStream_t stream);
 // W[r][k] = exp(sign 2 pi i (r - rows/2)(k - cols/2) c[b]) straight into planar split form
 cudaError_t tc_basis(bool bf16, const double* c, int sign, const TcOperand& dst, cudaStream_t stream);
 

@@ -1,10 +1,13 @@
 """GPU parity of the split-precision tensor-core MFT (tcgen05, 3xTF32 and 3xBF16, FP32
 accumulate) against the FP64 oracle's direct sums.
 
-Tolerances (relative L2 over the output field): 3xTF32 keeps ~21-22 significant bits per
-product (hi, lo both TF32; the dropped lo*lo term is 2^-22 relative), so it meets the
-complex64 bar of 1e-5. 3xBF16 keeps ~16 bits (dropped term 2^-16 = 1.5e-5 relative per
-product, random across the K terms), so its bar is 1e-4; the per-result error is printed."""
+Tolerances (relative L2 over the output field). Operand splitting: 3xTF32 keeps ~22
+significant bits per product (dropped lo*lo term 2^-22), 3xBF16 ~16 bits (2^-16). On top,
+the tensor-core FP32 accumulator rounds every update of a K = 8 (TF32) / 16 (BF16) slice
+product, six updates per slice for the complex split product, each up to one FP32 ulp of the
+running sum with a common sign, so the relative error can grow linearly in K: about
+2^-23 * 6/8 * K ~ 9e-8 K for a chain of two GEMMs. The bar is max(1e-5, 6e-8 K) for TF32 and
+max(1e-4, 6e-8 K) for BF16, K the longest inner length; the per-result error is printed."""
 import numpy as np
 import pytest
 import torch
@@ -15,6 +18,10 @@ from paper_1806_06467_gb300 import coro, inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {coro.MFT_3XTF32: 1e-5, coro.MFT_3XBF16: 1e-4}
+
+
+def tol(prec, k):
+    return max(TOL[prec], 6e-8 * k)
 
 
 def rel_l2(got, ref):
@@ -39,7 +46,7 @@ def test_tc_mft_forward(ctx, n, npix, m, prec):
     for b in range(2):
         err = rel_l2(y[b], propagation.mft(f[b], npix, m, du[b]))
         print(f"prec {prec} n {n} m {m} item {b}: rel L2 {err:.3e}")
-        assert err < TOL[prec]
+        assert err < tol(prec, n)
 
 
 @pytest.mark.parametrize("prec", [coro.MFT_3XTF32, coro.MFT_3XBF16])
@@ -53,4 +60,4 @@ def test_tc_mft_inverse(ctx, m, n, npix, prec):
     for b in range(2):
         err = rel_l2(y[b], propagation.imft(f[b], npix, n, du[b]))
         print(f"prec {prec} m {m} n {n} item {b}: rel L2 {err:.3e}")
-        assert err < TOL[prec]
+        assert err < tol(prec, m)
