@@ -281,6 +281,51 @@ coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, double* peak_
 coro_status coro_lyot_plan_execute_range(coro_plan plan, const void* pupil, const double* peak, float* intensity,
                                          void* field, int first, int count);
 
+/* Pupil argument layout for execute / peak / gradient: item b, row i, column j of E_A at
+ * pupil[b * bstride + i * ld + j] (default ld = n, bstride = n * n), so the pupil can be the
+ * centre window of a larger Fresnel grid. */
+coro_status coro_lyot_plan_set_pupil_layout(coro_plan plan, int ld, long long bstride);
+/* Adjoint (a11): with S[b] the dark-hole sum and I normalised by peak[b] (held fixed),
+ * grad[b] = dS[b]/dconj(E_A[b]) (Wirtinger convention: dS = 2 Re sum conj(grad) dE), i.e. the
+ * conjugate-transpose chain  grad = G_C - MFT_occ^H(spot . IMFT_occ^H(G_C)),  G_C = Lyot . MFT_det^H
+ * (mask . E_det / peak), with MFT^H = the inverse MFT of the same pitch. Also returns the forward
+ * sums in dh_out (host [batch], may be NULL; given -> the stream is synchronised). grad is
+ * device complex64 written at grad[b * grad_bstride + i * grad_ld + j] for the n x n window only. */
+coro_status coro_lyot_plan_gradient(coro_plan plan, const void* pupil, const double* peak, double* dh_out,
+                                    void* grad, int grad_ld, long long grad_bstride);
+
+/* ------------------------------------------------------------------------------------------
+ * Differentiable wavefront control (a11). Two Gaussian-influence DMs: DM1 in the pupil plane
+ * of an n_fresnel^2 grid (pupil npix pixels across diam_m, centred), DM2 after an angular-
+ * spectrum hop z_m (Sec. 1.1); the field hops back -z_m, the centre npix^2 window is the pupil
+ * of a batched Lyot chain (one item per wavelength). Loss L = sum_b S[b] with S the dark-hole
+ * sum normalised by the peak of the zero-height system (computed once, held fixed).
+ * coro_wfc_plan_evaluate: heights device float [2][n_act][n_act] (metres of surface, DM1 then
+ * DM2); loss (host) and per_item (host [batch]) optional; grad device float [2][n_act][n_act]
+ * = dL/dheights, or NULL for the forward only. Synchronises the stream. The plan holds four
+ * batch x n_fresnel^2 complex64 fields (checkpoints E0, E1, work, adjoint).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int batch;                    /* wavelengths                                           */
+    const double* wavelength;     /* host [batch], metres                                  */
+    int n_fresnel;                /* Fresnel grid, power of two                            */
+    double diam_m;                /* pupil diameter                                        */
+    int npix;                     /* pupil pixels across diam (= Lyot pupil array size)    */
+    double z_m;                   /* DM1 -> DM2 distance                                   */
+    int n_act;                    /* actuators per axis                                    */
+    double act_pitch_m, act_fwhm_m;
+    double lyot_frac;
+    int m_det;
+    const coro_lyot_item* items;  /* host [batch], one Lyot item per wavelength            */
+    int precision;                /* CORO_MFT_3XTF32 or CORO_MFT_3XBF16                    */
+} coro_wfc_desc;
+
+coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* desc, coro_plan* out);
+/* Normalisation peaks of the zero-height system (host [batch]); computed on first use. */
+coro_status coro_wfc_plan_peak(coro_plan plan, double* peak_out);
+coro_status coro_wfc_plan_evaluate(coro_plan plan, const float* heights, double* loss, double* per_item,
+                                   float* grad);
+
 /* ------------------------------------------------------------------------------------------
  * Detector reductions (a9).
  * coro_intensity: out[b][y][x] = |E|^2 / norm[b] (norm NULL = 1); out device float.

@@ -63,8 +63,21 @@ class LyotDesc(ct.Structure):
                 ("m_det", ct.c_int), ("items", ct.POINTER(LyotItem)), ("precision", ct.c_int)]
 
 
+class WfcDesc(ct.Structure):
+    _fields_ = [("batch", ct.c_int), ("wavelength", ct.POINTER(ct.c_double)), ("n_fresnel", ct.c_int),
+                ("diam_m", ct.c_double), ("npix", ct.c_int), ("z_m", ct.c_double), ("n_act", ct.c_int),
+                ("act_pitch_m", ct.c_double), ("act_fwhm_m", ct.c_double), ("lyot_frac", ct.c_double),
+                ("m_det", ct.c_int), ("items", ct.POINTER(LyotItem)), ("precision", ct.c_int)]
+
+
 _P = ct.c_void_p
 _SIGS = {
+    "coro_lyot_plan_set_pupil_layout": (ct.c_int, [_P, ct.c_int, ct.c_longlong]),
+    "coro_lyot_plan_gradient": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), _P, ct.c_int,
+                                           ct.c_longlong]),
+    "coro_wfc_plan_create": (ct.c_int, [_P, ct.POINTER(WfcDesc), ct.POINTER(_P)]),
+    "coro_wfc_plan_peak": (ct.c_int, [_P, ct.POINTER(ct.c_double)]),
+    "coro_wfc_plan_evaluate": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), _P]),
     "coro_dm_opd": (ct.c_int, [_P, _P, ct.c_int, ct.c_int, ct.c_double, ct.c_double, ct.c_int, ct.c_double,
                                ct.c_double, _P]),
     "coro_dm_correlate": (ct.c_int, [_P, _P, ct.c_int, ct.c_int, ct.c_double, ct.c_int, ct.c_double,
@@ -353,6 +366,22 @@ class LyotPlan:
             None if intensity is None else ct.c_void_p(intensity.data_ptr()),
             None if field is None else ct.c_void_p(field.data_ptr()), dh))
         return np.array(dh[:]) if want_dh else None
+
+    def set_pupil_layout(self, ld: int, bstride: int):
+        self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_set_pupil_layout(self.handle, ld, bstride))
+
+    def gradient(self, pupil, peak, grad_out=None, grad_ld: int | None = None, grad_bstride: int | None = None):
+        """dS/dconj(E_A) per item (complex64 [batch][n][n] unless a strided window is given) and the
+        dark-hole sums."""
+        import torch
+        if grad_out is None:
+            grad_out = torch.empty((self.batch, self.n, self.n), dtype=torch.complex64, device=pupil.device)
+            grad_ld, grad_bstride = self.n, self.n * self.n
+        dh = (ct.c_double * self.batch)()
+        pk = _dbl(np.broadcast_to(np.asarray(peak, float), (self.batch,)))
+        self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_gradient(
+            self.handle, ct.c_void_p(pupil.data_ptr()), pk, dh, ct.c_void_p(grad_out.data_ptr()), grad_ld, grad_bstride))
+        return grad_out, np.array(dh[:])
 
     def execute_range(self, pupil, first: int, count: int = 1, peak=None, intensity=None, field=None):
         pk = None if peak is None else _dbl(np.broadcast_to(np.asarray(peak, float), (self.batch,)))

@@ -470,6 +470,7 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
             a.out = (C*)field;
             a.tw = tw;
             a.flags = op.row_flags;
+            a.err = ctx->err;
             a.elems = op.elems;
             e = launch_row_pass<C>(n, a, pl);
         } else {

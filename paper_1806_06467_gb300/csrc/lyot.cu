@@ -39,8 +39,16 @@ struct LyotPlan : coro_plan_s {
     std::vector<Buf> bufs;
     TcOperand XA{}, Z1{}, XB{}, Z3{}, Z5{}, W1{}, W2{}, W3{};
     CUtensorMap mXA, mZ1, mXB, mZ3, mZ5, mW1, mW2, mW3;
-    TcItem* dev_items = nullptr;       // [6][batch]
-    std::vector<TcItem> host_items;    // [6][batch]
+    TcItem* dev_items = nullptr;       // [9][batch]: G1-G6, then the adjoint's H1, H2, G4 without stop
+    std::vector<TcItem> host_items;    // [9][batch]
+    int pupil_ld = 0;                  // layout of the pupil argument (elements)
+    long long pupil_bstride = 0;
+    std::vector<std::pair<double, int>> det_bases;   // (du_det, basis index)
+    // adjoint resources, made on the first gradient call
+    bool grad_ready = false;
+    TcOperand XS{}, Z4{}, W4{};
+    CUtensorMap mXS, mZ4, mW4;
+    float2* seed = nullptr;            // [batch][m_det][m_det] dS/dconj(E_det)
     int* keep_lyot = nullptr;          // [batch] Lyot-stop radius^2 (pupil pixels)
     double* dh = nullptr;              // [batch]
     float* peak = nullptr;             // [batch]
@@ -149,7 +157,10 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
     const double pupil_pitch = 1.0 / d->npix;            // pupil coordinates in units of D
     const int lyot_thr = clamp_thr(disk_threshold(0.5 * d->lyot_frac, pupil_pitch, false));
     const int all = 0x7fffffff;
-    p->host_items.resize((size_t)6 * B);
+    p->host_items.resize((size_t)9 * B);
+    p->pupil_ld = n;
+    p->pupil_bstride = (long long)n * n;
+    for (auto& kv : det_id) p->det_bases.push_back({kv.first, kv.second});
     std::vector<int> keep(B, lyot_thr);
     for (int b = 0; b < B; ++b) {
         const coro_lyot_item& it = d->items[b];
@@ -165,6 +176,10 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
         h[3 * B + b] = TcItem{n, n, mo, b, oi[b], 0, lyot_thr, s_occ, 1.0f};
         h[4 * B + b] = TcItem{n, md, n, b, di[b], 0, all, 1.0f, 1.0f};
         h[5 * B + b] = TcItem{md, md, n, b, di[b], dh_lo, dh_hi, s_det, 1.0f};
+        // adjoint: detector IMFT (two GEMMs, Lyot stop on the second), Babinet block without stop
+        h[6 * B + b] = TcItem{md, n, md, b, di[b], 0, all, 1.0f, 1.0f};
+        h[7 * B + b] = TcItem{n, n, md, b, di[b], 0, lyot_thr, s_det, 1.0f};
+        h[8 * B + b] = TcItem{n, n, mo, b, oi[b], 0, all, s_occ, 1.0f};
     }
     p->dev_items = (TcItem*)p->alloc(p->host_items.size() * sizeof(TcItem), &st);
     p->keep_lyot = p->dev_items ? (int*)p->alloc(B * sizeof(int), &st) : nullptr;
@@ -181,8 +196,9 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
 
 namespace {
 
-// G5 + G6 on the operand already in XA planes; intensity epilogue.
-cudaError_t detector_gemms(LyotPlan* p, const double* peak_host, float* intensity, void* field, bool track_peak) {
+// G5 + G6 on the operand already in XA planes; intensity epilogue (seed: write dS/dconj(E_det)).
+cudaError_t detector_gemms(LyotPlan* p, const double* peak_host, float* intensity, void* field, bool track_peak,
+                           float2* seed = nullptr) {
     const int B = p->batch, n = p->n, md = p->m_det;
     cudaStream_t s = p->ctx->stream;
     TcArgs a{};
@@ -213,7 +229,8 @@ cudaError_t detector_gemms(LyotPlan* p, const double* peak_host, float* intensit
     b6.dst_bstride = (long long)md * md;
     b6.dst_rows = md;
     b6.dst_ld = md;
-    b6.c64 = (float2*)field;
+    b6.c64 = seed ? seed : (float2*)field;
+    b6.c64_seed = seed ? 1 : 0;
     b6.c64_bstride = (long long)md * md;
     b6.c64_ld = md;
     b6.dh_acc = p->dh;
@@ -242,7 +259,7 @@ cudaError_t run_stages(LyotPlan* p, const void* pupil, const double* peak, float
         a.dst_ld = dst.ld;
         e = tc_launch(p->bf16, epi, mx, mw, mm, nn, kk, B, a, s);
     };
-    if (first <= 0 && last >= 0) e = tc_split(p->bf16, (const float2*)pupil, (long long)n * n, n, p->XA, s);
+    if (first <= 0 && last >= 0) e = tc_split(p->bf16, (const float2*)pupil, p->pupil_bstride, p->pupil_ld, p->XA, s);
     gemm(0, TC_EPI_SPLITT, p->mXA, p->mW1, p->Z1, n, mo, n);     // G1
     gemm(1, TC_EPI_SPLITT, p->mZ1, p->mW1, p->XB, mo, mo, n);    // G2 (x spot)
     gemm(2, TC_EPI_SPLITT, p->mXB, p->mW2, p->Z3, mo, n, mo);    // G3
@@ -299,7 +316,7 @@ extern "C" coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, do
     DeviceGuard g(p->ctx->device);
     cudaStream_t s = p->ctx->stream;
     // occulter removed: E_D = E_A . Lyot stop, then the detector MFT
-    cudaError_t e = tc_split(p->bf16, (const float2*)pupil, (long long)n * n, n, p->XA, s, p->keep_lyot);
+    cudaError_t e = tc_split(p->bf16, (const float2*)pupil, p->pupil_bstride, p->pupil_ld, p->XA, s, p->keep_lyot);
     if (e == cudaSuccess) e = detector_gemms(p, nullptr, nullptr, nullptr, true);
     std::vector<float> pk(B);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pk.data(), p->peak, B * sizeof(float), cudaMemcpyDeviceToHost, s);
@@ -307,4 +324,87 @@ extern "C" coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, do
     if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_peak");
     for (int b = 0; b < B; ++b) peak_out[b] = pk[b];
     return CORO_OK;
+}
+
+extern "C" coro_status coro_lyot_plan_set_pupil_layout(coro_plan plan, int ld, long long bstride) {
+    clear_error();
+    if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_set_pupil_layout: not a Lyot plan"); return CORO_EINVAL; }
+    auto* p = static_cast<LyotPlan*>(plan);
+    if (ld < p->n || bstride < (long long)ld * (p->n - 1) + p->n) {
+        set_error("coro_lyot_plan_set_pupil_layout: ld %d / bstride %lld too small for n = %d", ld, bstride, p->n);
+        return CORO_EINVAL;
+    }
+    p->pupil_ld = ld;
+    p->pupil_bstride = bstride;
+    return CORO_OK;
+}
+
+namespace {
+
+coro_status prepare_gradient(LyotPlan* p) {
+    if (p->grad_ready) return CORO_OK;
+    coro_status st = CORO_OK;
+    const int B = p->batch, n = p->n, md = p->m_det;
+    const int nd = (int)p->det_bases.size();
+    if (!p->make(p->XS, B, md, md, &st) || !p->make(p->Z4, B, n, md, &st) || !p->make(p->W4, nd, n, md, &st))
+        return st;
+    p->seed = (float2*)p->alloc((size_t)B * md * md * sizeof(float2), &st);
+    if (!p->seed) return st;
+    cudaError_t e = cudaSuccess;
+    // W4[j][u] = exp(+2 pi i j' u' du_det / npix): the detector MFT's conjugate transpose
+    for (auto& db : p->det_bases)
+        if (e == cudaSuccess) e = tc_basis_one(p->bf16, db.first / p->npix, +1, p->W4, db.second, n, md, p->ctx->stream);
+    if (e == cudaSuccess) e = tc_make_operand_map(p->XS, p->bf16, &p->mXS);
+    if (e == cudaSuccess) e = tc_make_operand_map(p->Z4, p->bf16, &p->mZ4);
+    if (e == cudaSuccess) e = tc_make_operand_map(p->W4, p->bf16, &p->mW4);
+    if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_gradient: set-up");
+    p->grad_ready = true;
+    return CORO_OK;
+}
+
+}  // namespace
+
+extern "C" coro_status coro_lyot_plan_gradient(coro_plan plan, const void* pupil, const double* peak, double* dh_out,
+                                               void* grad, int grad_ld, long long grad_bstride) {
+    clear_error();
+    if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_gradient: not a Lyot plan"); return CORO_EINVAL; }
+    auto* p = static_cast<LyotPlan*>(plan);
+    const int B = p->batch, n = p->n, md = p->m_det, mo = p->m_occ_max;
+    if (!pupil || !peak || !grad) { set_error("coro_lyot_plan_gradient: pupil, peak and grad are required"); return CORO_EINVAL; }
+    if (grad_ld < n || grad_bstride < (long long)grad_ld * (n - 1) + n) {
+        set_error("coro_lyot_plan_gradient: grad_ld %d / grad_bstride %lld too small", grad_ld, grad_bstride);
+        return CORO_EINVAL;
+    }
+    for (int b = 0; b < B; ++b)
+        if (!(peak[b] > 0)) { set_error("coro_lyot_plan_gradient: peak[%d] must be > 0", b); return CORO_EINVAL; }
+    DeviceGuard g(p->ctx->device);
+    coro_status st = prepare_gradient(p);
+    if (st != CORO_OK) return st;
+    cudaStream_t s = p->ctx->stream;
+    // forward (stages 0-4), then the detector MFT writing the seed mask . E_det / peak
+    cudaError_t e = run_stages(p, pupil, peak, nullptr, nullptr, 0, 4);
+    if (e == cudaSuccess) e = detector_gemms(p, peak, nullptr, nullptr, false, p->seed);
+    if (e == cudaSuccess && dh_out) e = cudaMemcpyAsync(dh_out, p->dh, B * sizeof(double), cudaMemcpyDeviceToHost, s);
+    // adjoint: G_D = IMFT_det(seed); G_C = Lyot . G_D; G_A = G_C - IMFT_occ(spot . MFT_occ(G_C))
+    if (e == cudaSuccess) e = tc_split(p->bf16, p->seed, (long long)md * md, md, p->XS, s);
+    auto gemm = [&](int gi, int epi, const CUtensorMap& mx, const CUtensorMap& mw, const TcOperand& dst, int mm, int nn, int kk) {
+        if (e != cudaSuccess) return;
+        TcArgs a{};
+        a.err = p->ctx->err;
+        a.items = p->dev_items + gi * B;
+        a.dst = dst.base;
+        a.dst_bstride = (long long)4 * dst.rows * dst.ld;
+        a.dst_rows = dst.rows;
+        a.dst_ld = dst.ld;
+        e = tc_launch(p->bf16, epi, mx, mw, mm, nn, kk, B, a, s);
+    };
+    gemm(6, TC_EPI_SPLITT, p->mXS, p->mW4, p->Z4, md, n, md);    // H1
+    gemm(7, TC_EPI_SPLITT, p->mZ4, p->mW4, p->XA, n, n, md);     // H2 (x Lyot) -> G_C in XA
+    gemm(0, TC_EPI_SPLITT, p->mXA, p->mW1, p->Z1, n, mo, n);     // G1
+    gemm(1, TC_EPI_SPLITT, p->mZ1, p->mW1, p->XB, mo, mo, n);    // G2 (x spot)
+    gemm(2, TC_EPI_SPLITT, p->mXB, p->mW2, p->Z3, mo, n, mo);    // G3
+    gemm(8, TC_EPI_BABINET, p->mZ3, p->mW2, p->XA, n, n, mo);    // G4, no stop -> G_A in XA
+    if (e == cudaSuccess) e = tc_merge(p->bf16, p->XA, (float2*)grad, grad_bstride, grad_ld, s);
+    if (e == cudaSuccess && dh_out) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? CORO_OK : cuda_fail(e, "coro_lyot_plan_gradient");
 }

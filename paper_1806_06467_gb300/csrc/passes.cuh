@@ -8,6 +8,7 @@
 // moved fftshift to the GPU; here it costs no memory pass at all).
 #pragma once
 #include "fft_engine.cuh"
+#include "tc_ptx.cuh"
 
 namespace coro {
 
@@ -51,8 +52,11 @@ struct PassElems {
 
 // Multiply the 16 samples a thread holds (row y of item b, columns x0 + s*XS) by every
 // element of the list. The element loop is outermost and uniform across the block.
+// pre_idx >= 0: element pre_idx is an OPD map whose 16 values this thread already holds in
+// pre (loaded early so that their latency hides behind the inverse FFT).
 template <typename C, int N, int XS>
-__device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, const PassElems& pe) {
+__device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, const PassElems& pe,
+                                            const float (&pre)[16], int pre_idx) {
     using R = typename real_of<C>::type;
     const int ky = y - N / 2;
     for (int i = 0; i < pe.count; ++i) {
@@ -96,7 +100,7 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
                     // phase / pi = (2 / lambda) * OPD
-                    const float ph = k * __ldg(e.map + off + s * XS);
+                    const float ph = k * (i == pre_idx ? pre[s] : __ldg(e.map + off + s * XS));
                     float sn, cs;
                     sincospif(ph, &sn, &cs);
                     R am = 1;
@@ -109,27 +113,36 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                 const int t0 = e.ithr[4 * b];
                 const float k = e.fpar[4 * b], sc = e.fpar[4 * b + 1];
                 const float zy = ky * sc;
-#pragma unroll 4
+                // the polynomial is evaluated in a rolled loop (few registers); only the phase
+                // of each of the 16 samples is kept
+                float ph[16];
+#pragma unroll 1
                 for (int s = 0; s < 16; ++s) {
                     const int kx = x0 + s * XS - N / 2;
-                    if (kx * kx + ky * ky > t0) continue;   // zero OPD outside the disk
-                    const float zx = kx * sc;
-                    const float rho2 = zx * zx + zy * zy;
-                    float pr = 1.f, pim = 0.f, opd = 0.f;
+                    float opd = 0.f;                          // zero OPD outside the disk
+                    if (kx * kx + ky * ky <= t0) {
+                        const float zx = kx * sc;
+                        const float rho2 = zx * zx + zy * zy;
+                        float pr = 1.f, pim = 0.f;
+#pragma unroll 1
+                        for (int m = 0; m < ZM; ++m) {
+                            const float* A = e.zpoly + m * ZD;
+                            const float* Bc = e.zpoly + ZM * ZD + m * ZD;
+                            float a = A[ZD - 1], bb = Bc[ZD - 1];
 #pragma unroll
-                    for (int m = 0; m < ZM; ++m) {
-                        const float* A = e.zpoly + m * ZD;
-                        const float* Bc = e.zpoly + ZM * ZD + m * ZD;
-                        float a = A[ZD - 1], bb = Bc[ZD - 1];
-#pragma unroll
-                        for (int d = ZD - 2; d >= 0; --d) { a = fmaf(a, rho2, A[d]); bb = fmaf(bb, rho2, Bc[d]); }
-                        opd += a * pr + bb * pim;
-                        const float nr = pr * zx - pim * zy;
-                        pim = pr * zy + pim * zx;
-                        pr = nr;
+                            for (int d = ZD - 2; d >= 0; --d) { a = fmaf(a, rho2, A[d]); bb = fmaf(bb, rho2, Bc[d]); }
+                            opd += a * pr + bb * pim;
+                            const float nr = pr * zx - pim * zy;
+                            pim = pr * zy + pim * zx;
+                            pr = nr;
+                        }
                     }
+                    ph[s] = k * opd;
+                }
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
                     float sn, cs;
-                    sincospif(k * opd, &sn, &cs);
+                    sincospif(ph[s], &sn, &cs);
                     v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
                 }
                 break;
@@ -182,8 +195,16 @@ struct RowArgs {
     C* out;
     const C* tw;          // twiddles for N
     int flags;
+    int* err;             // bounded-wait failure flag (persistent kernel)
     PassElems elems;
 };
+
+// First OPD-map element of a pass (its map values get prefetched), or -1.
+__device__ __forceinline__ int first_map(const PassElems& pe) {
+    for (int i = 0; i < pe.count; ++i)
+        if (pe.e[i].kind == DK_OPD_MAP) return i;
+    return -1;
+}
 
 template <int N> struct RowCfg {
     static constexpr int TPL = LineGeom<N>::TPL;
@@ -216,10 +237,108 @@ row_pass_kernel(const __grid_constant__ RowArgs<C> a) {
         for (int s = 0; s < 16; ++s) v[s] = a.in[row_off + t + s * Cfg::TPL];
     }
     if (a.flags & RF_INV_FIRST) line_fft<C, N, true>(v, buf, t, a.tw);
-    if (a.elems.count) apply_elems<C, N, Cfg::TPL>(v, t, y, b, a.elems);
+    if (a.elems.count) {
+        float none[16];
+        apply_elems<C, N, Cfg::TPL>(v, t, y, b, a.elems, none, -1);
+    }
     if (a.flags & RF_FWD_AFTER) line_fft<C, N, false>(v, buf, t, a.tw);
 #pragma unroll
     for (int s = 0; s < 16; ++s) a.out[row_off + t + s * Cfg::TPL] = v[s];
+}
+
+// ------------------------------------------------------------------------------ persistent row pass
+//
+// Same arithmetic as row_pass_kernel, but each block stays resident and streams line groups:
+// the rows of group g+1 arrive by a bulk asynchronous copy into one shared buffer while group
+// g is transformed, and group g's result leaves by a bulk store from the buffer it arrived in,
+// so HBM traffic overlaps the FFT instead of stalling on it.
+
+template <int N> struct PRowCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int L0 = TPL >= 256 ? 1 : 256 / TPL;
+    static constexpr int L = L0 < N ? L0 : N;          // lines per group
+    static constexpr int THREADS = TPL * L;
+    static constexpr int GROUP = L * N;                 // samples per group (contiguous rows)
+    static constexpr int XSTRIDE = LineGeom<N>::STRIDE;
+    template <typename C> static constexpr size_t smem() {
+        return 2 * (size_t)GROUP * sizeof(C) + (size_t)L * XSTRIDE * sizeof(C) + 64;
+    }
+};
+
+template <typename C, int N>
+__global__ void __launch_bounds__(PRowCfg<N>::THREADS)
+row_pass_persistent_kernel(const __grid_constant__ RowArgs<C> a, int groups) {
+    using Cfg = PRowCfg<N>;
+    constexpr uint32_t BYTES = Cfg::GROUP * sizeof(C);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + Cfg::GROUP;
+    C* xbuf = buf1 + Cfg::GROUP;
+    uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + Cfg::L * Cfg::XSTRIDE);
+    const int line = threadIdx.x / Cfg::TPL;
+    const int t = threadIdx.x % Cfg::TPL;
+    const bool load = !(a.flags & RF_INIT_ONE);
+    C* xl = xbuf + line * Cfg::XSTRIDE;
+    const int mi = first_map(a.elems);
+
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&full[0], 1);
+        tc::mbar_init(&full[1], 1);
+        tc::fence_mbar_init();
+        if (load && blockIdx.x < groups) {
+            tc::mbar_arrive_expect_tx(&full[0], BYTES);
+            tc::bulk_load(buf0, a.in + (size_t)blockIdx.x * Cfg::GROUP, BYTES, &full[0]);
+        }
+    }
+    __syncthreads();
+    int it = 0;
+    bool ok = true;
+    for (int g = blockIdx.x; g < groups; g += gridDim.x, ++it) {
+        C* ib = (it & 1) ? buf1 : buf0;
+        C* nb = (it & 1) ? buf0 : buf1;
+        const int row0 = g * Cfg::L;
+        const int b = row0 / N, y = row0 % N + line;
+        C v[16];
+        if (load) {
+            if (ok) ok = tc::mbar_wait(&full[it & 1], (it >> 1) & 1, a.err, 5);
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = ib[line * N + t + s * Cfg::TPL];
+        } else {
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = mk<C>(1, 0);
+        }
+        float pre[16];
+        if (mi >= 0) {
+            const DevElem& e = a.elems.e[mi];
+            const float* mp = e.map + (size_t)b * e.map_bstride + (size_t)y * N + t;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) pre[s] = __ldg(mp + s * Cfg::TPL);
+        }
+        if (threadIdx.x == 0) {
+            if (load) {
+                if (g + (int)gridDim.x < groups) {
+                    tc::bulk_wait_read<0>();            // group g-1's store has left nb
+                    tc::mbar_arrive_expect_tx(&full[(it + 1) & 1], BYTES);
+                    tc::bulk_load(nb, a.in + (size_t)(g + gridDim.x) * Cfg::GROUP, BYTES, &full[(it + 1) & 1]);
+                }
+            } else {
+                tc::bulk_wait_read<1>();                // group g-2's store has left ib
+            }
+        }
+        __syncthreads();
+        if (a.flags & RF_INV_FIRST) line_fft<C, N, true>(v, xl, t, a.tw);
+        if (a.elems.count) apply_elems<C, N, Cfg::TPL>(v, t, y, b, a.elems, pre, mi);
+        if (a.flags & RF_FWD_AFTER) line_fft<C, N, false>(v, xl, t, a.tw);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) ib[line * N + t + s * Cfg::TPL] = v[s];
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::bulk_store(a.out + (size_t)g * Cfg::GROUP, ib, BYTES);
+            tc::bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) tc::bulk_wait<0>();          // shared memory must outlive the stores
 }
 
 // ------------------------------------------------------------------------------ column pass

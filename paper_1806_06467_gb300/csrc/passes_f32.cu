@@ -12,10 +12,10 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
         case 128: return row_launch<float2, 128>(a, l);
         case 256: return row_launch<float2, 256>(a, l);
         case 512: return row_launch<float2, 512>(a, l);
-        case 1024: return row_launch<float2, 1024>(a, l);
-        case 2048: return row_launch<float2, 2048>(a, l);
-        case 4096: return row_launch<float2, 4096>(a, l);
-        case 8192: return row_launch<float2, 8192>(a, l);
+        case 1024: return row_launch_persistent<float2, 1024>(a, l);
+        case 2048: return row_launch_persistent<float2, 2048>(a, l);
+        case 4096: return row_launch_persistent<float2, 4096>(a, l);
+        case 8192: return row_launch_persistent<float2, 8192>(a, l);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -20,6 +20,30 @@ inline cudaError_t ensure_smem(K kernel, size_t bytes, unsigned& done_mask) {
     return e;
 }
 
+// Persistent variant: as many resident blocks as fit, each streaming line groups.
+template <typename C, int N>
+cudaError_t row_launch_persistent(const RowArgs<C>& a, const PassLaunch& l) {
+    using Cfg = PRowCfg<N>;
+    static unsigned done = 0;
+    static int per_sm[32] = {};
+    const size_t smem = Cfg::template smem<C>();
+    cudaError_t e = ensure_smem(row_pass_persistent_kernel<C, N>, smem, done);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int& occ = per_sm[dev & 31];
+    if (occ == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, row_pass_persistent_kernel<C, N>, Cfg::THREADS, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+    }
+    const int groups = l.batch * N / Cfg::L;
+    const int grid = groups < sms * occ ? groups : sms * occ;
+    row_pass_persistent_kernel<C, N><<<grid, Cfg::THREADS, smem, l.stream>>>(a, groups);
+    return cudaGetLastError();
+}
+
 template <typename C, int N>
 cudaError_t row_launch(const RowArgs<C>& a, const PassLaunch& l) {
     using Cfg = RowCfg<N>;

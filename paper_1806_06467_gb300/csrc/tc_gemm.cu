@@ -215,7 +215,13 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
                     } else {
                         const float inten = (re * re + im * im) * it.inv_peak;
                         if (a.dst) reinterpret_cast<float*>(a.dst)[b * a.dst_bstride + (size_t)n * a.dst_ld + m] = inten;
-                        if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(re, im);
+                        if (a.c64) {
+                            // field, or the gradient seed dS/dconj(E) = mask . E / peak
+                            const float2 v = !a.c64_seed ? make_float2(re, im)
+                                             : keep ? make_float2(re * it.inv_peak, im * it.inv_peak)
+                                                    : make_float2(0.f, 0.f);
+                            a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = v;
+                        }
                         if (keep) dh += (double)inten;
                         pk = fmaxf(pk, inten);
                     }
@@ -279,6 +285,15 @@ __global__ void basis_kernel(const double* __restrict__ c, double c_one, int sig
     }
     const size_t plane = (size_t)plane_rows * ld;
     store_split<BF16>(dst, plane, (size_t)b * 4 * plane + (size_t)r * ld + k, re, im);
+}
+
+template <bool BF16>
+__global__ void merge_kernel(const void* src, int rows, int cols, int ld, float2* dst, long long db, int dld) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y, b = blockIdx.z;
+    if (k >= cols) return;
+    const size_t plane = (size_t)rows * ld;
+    dst[b * db + (size_t)r * dld + k] = load_split<BF16>(src, plane, (size_t)b * 4 * plane + (size_t)r * ld + k);
 }
 
 // ---------------------------------------------------------------- driver entry point
@@ -363,6 +378,14 @@ cudaError_t tc_basis(bool bf16, const double* c, int sign, const TcOperand& dst,
     dim3 grid((dst.ld + 127) / 128, dst.rows, dst.batch);
     if (bf16) basis_kernel<true><<<grid, 128, 0, stream>>>(c, 0.0, sign, dst.base, dst.rows, dst.cols, dst.ld, dst.rows, 0);
     else basis_kernel<false><<<grid, 128, 0, stream>>>(c, 0.0, sign, dst.base, dst.rows, dst.cols, dst.ld, dst.rows, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_merge(bool bf16, const TcOperand& src, float2* dst, long long dst_bstride, int dst_ld,
+                     cudaStream_t stream) {
+    dim3 grid((src.cols + 127) / 128, src.rows, src.batch);
+    if (bf16) merge_kernel<true><<<grid, 128, 0, stream>>>(src.base, src.rows, src.cols, src.ld, dst, dst_bstride, dst_ld);
+    else merge_kernel<false><<<grid, 128, 0, stream>>>(src.base, src.rows, src.cols, src.ld, dst, dst_bstride, dst_ld);
     return cudaGetLastError();
 }
 

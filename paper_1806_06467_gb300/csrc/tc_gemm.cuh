@@ -47,6 +47,7 @@ struct TcArgs {
     int c64_ld;
     double* dh_acc;                  // dark-hole sums [b] (intensity epilogue)
     float* peak;                     // running max of the intensity [b] (intensity epilogue), or NULL
+    int c64_seed;                    // intensity epilogue: c64 receives mask . E * inv_peak instead of E
 };
 
 // Host side (tc_gemm.cu).
@@ -69,6 +70,9 @@ cudaError_t tc_basis_one(bool bf16, double c, int sign, const TcOperand& dst, in
                          int cols_valid, cudaStream_t stream);
 // W[r][k] = exp(sign 2 pi i (r - rows/2)(k - cols/2) c[b]) straight into planar split form
 cudaError_t tc_basis(bool bf16, const double* c, int sign, const TcOperand& dst, cudaStream_t stream);
+// planar split operand -> complex64 (hi + lo), dst[b * dst_bstride + r * dst_ld + k]
+cudaError_t tc_merge(bool bf16, const TcOperand& src, float2* dst, long long dst_bstride, int dst_ld,
+                     cudaStream_t stream);
 
 inline size_t tc_elem_size(bool bf16) { return bf16 ? 2 : 4; }
 inline int tc_ld(int cols, bool bf16) {          // 16-byte rows, at least 64 bytes

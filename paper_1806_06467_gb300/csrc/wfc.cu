@@ -1,0 +1,256 @@
+// wfc.cu -- differentiable wavefront control: dark-hole intensity and its gradient with
+// respect to the heights of two deformable mirrors (DM1 at the pupil, DM2 a Fresnel hop z
+// away), summed over wavelengths.
+//
+// Forward, per wavelength (the hop uses the angular-spectrum method of Sec. 1.1):
+//   E0 = A exp(i phi1),  E1 = AS(+z) E0,  E2 = E1 exp(i phi2),  E3 = AS(-z) E2,
+//   E_A = centre n x n of E3 -> Lyot chain -> S = sum over the dark hole of |E_det|^2 / peak
+// with phi = 2 pi OPD / lambda and OPD = 2 x (Gaussian-influence DM surface).
+// Adjoint (G = dL/dconj(E), AS(z)^H = AS(-z), phase elements pass G times exp(-i phi)):
+//   G3 = pad(dS/dconj(E_A)),  G2 = AS(+z) G3,  dL/dphi2 = 2 Im(G2 conj(E2)),
+//   G0 = AS(-z)(exp(-i phi2) G2),  dL/dphi1 = 2 Im(G0 conj(E0)),
+//   dL/dh = sum_lambda (4 pi / lambda) G_infl^T (dL/dphi) G_infl.
+// The wavelength sum is folded into one weighted map per DM before the DM correlation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "capi_common.h"
+
+namespace {
+
+// out[y][x] = sum_b w[b] 2 Im(g_b conj(f_b)),  f_b = e_b exp(i pi k_b opd)  (e, opd optional),
+// k_b = 2 / lambda_b in half-cycles per metre.
+__global__ void phase_grad_kernel(const float2* __restrict__ g, const float2* __restrict__ e,
+                                  const float* __restrict__ opd, const float* __restrict__ k,
+                                  const float* __restrict__ w, int batch, size_t npx, float* __restrict__ out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npx; i += (size_t)gridDim.x * blockDim.x) {
+        const float ph = opd ? opd[i] : 0.f;
+        float acc = 0.f;
+        for (int b = 0; b < batch; ++b) {
+            const float2 gv = g[b * npx + i];
+            float2 f = e ? e[b * npx + i] : make_float2(1.f, 0.f);
+            if (opd) {
+                float sn, cs;
+                sincospif(k[b] * ph, &sn, &cs);
+                f = make_float2(f.x * cs - f.y * sn, f.x * sn + f.y * cs);
+            }
+            // Im(g conj(f)) = g.y f.x - g.x f.y
+            acc = fmaf(w[b] * 2.f, gv.y * f.x - gv.x * f.y, acc);
+        }
+        out[i] = acc;
+    }
+}
+
+struct WfcPlan : coro_plan_s {
+    coro_ctx ctx = nullptr;
+    int device = 0;
+    coro_wfc_desc d{};
+    std::vector<double> lam, ps;
+    std::vector<coro_lyot_item> items;
+    coro_plan lyot = nullptr;
+    std::vector<void*> bufs;
+    float2 *e0 = nullptr, *e1 = nullptr, *w = nullptr, *g = nullptr;
+    float *opd1 = nullptr, *opd2 = nullptr, *opd2n = nullptr, *dphi = nullptr, *zero_h = nullptr;
+    float *k_d = nullptr, *w_d = nullptr;
+    std::vector<double> peak;
+    int kind() const override { return 3; }
+    int launches() const override { return 0; }
+    ~WfcPlan() override {
+        if (lyot) coro_plan_destroy(lyot);
+        coro::DeviceGuard gd(device);
+        cudaDeviceSynchronize();
+        for (void* p : bufs) cudaFree(p);
+    }
+    void* alloc(size_t bytes, coro_status* st) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) { *st = coro::cuda_fail(e, "coro_wfc_plan_create: cudaMalloc"); return nullptr; }
+        bufs.push_back(p);
+        return p;
+    }
+};
+
+coro_wavefront field(WfcPlan* p, float2* data) {
+    return coro_wavefront{data, CORO_C64, p->d.batch, p->d.n_fresnel, p->ps.data(), p->lam.data()};
+}
+
+coro_element opd_elem(const float* map) {
+    coro_element e{};
+    e.kind = CORO_EL_OPD_MAP;
+    e.opd = map;
+    return e;
+}
+
+// Forward through the Fresnel section: fills e0, e1 and leaves E3 in w.
+coro_status fresnel_forward(WfcPlan* p, const float* heights) {
+    const coro_wfc_desc& d = p->d;
+    coro_ctx c = p->ctx;
+    const int nf = d.n_fresnel, na = d.n_act;
+    const double dx = d.diam_m / d.npix;
+    const size_t fbytes = (size_t)d.batch * nf * nf * sizeof(float2);
+    coro_status st;
+    if ((st = coro_dm_opd(c, heights, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, 2.0, p->opd1)) != CORO_OK) return st;
+    if ((st = coro_dm_opd(c, heights + na * na, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, 2.0, p->opd2)) != CORO_OK) return st;
+    if ((st = coro_dm_opd(c, heights + na * na, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, -2.0, p->opd2n)) != CORO_OK) return st;
+    coro_wavefront f0 = field(p, p->e0);
+    if ((st = coro_wavefront_init(c, &f0, 1.0)) != CORO_OK) return st;
+    coro_element ap{};
+    ap.kind = CORO_EL_APERTURE;
+    ap.radius = 0.5 * d.diam_m;
+    if ((st = coro_apply_element(c, &f0, &ap)) != CORO_OK) return st;
+    coro_element o1 = opd_elem(p->opd1);
+    if ((st = coro_apply_element(c, &f0, &o1)) != CORO_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(p->e1, p->e0, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return coro::cuda_fail(e, "wfc: copy");
+    coro_wavefront f1 = field(p, p->e1);
+    if ((st = coro_propagate_fresnel(c, &f1, d.z_m, CORO_FRESNEL_AS)) != CORO_OK) return st;
+    e = cudaMemcpyAsync(p->w, p->e1, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return coro::cuda_fail(e, "wfc: copy");
+    coro_wavefront fw = field(p, p->w);
+    coro_element o2 = opd_elem(p->opd2);
+    if ((st = coro_apply_element(c, &fw, &o2)) != CORO_OK) return st;
+    return coro_propagate_fresnel(c, &fw, -d.z_m, CORO_FRESNEL_AS);
+}
+
+float2* window(WfcPlan* p, float2* base) {
+    const int nf = p->d.n_fresnel, n = p->d.npix;
+    const size_t off = (size_t)(nf / 2 - n / 2) * nf + (nf / 2 - n / 2);
+    return base + off;
+}
+
+}  // namespace
+
+extern "C" coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* d, coro_plan* out) {
+    coro::clear_error();
+    if (!ctx || !d || !out || !d->wavelength || !d->items) { coro::set_error("coro_wfc_plan_create: NULL argument"); return CORO_EINVAL; }
+    *out = nullptr;
+    if (d->batch < 1 || d->batch > 1024) { coro::set_error("coro_wfc_plan_create: batch %d", d->batch); return CORO_ESIZE; }
+    if (!coro::is_pow2(d->n_fresnel) || d->n_fresnel < 32 || d->n_fresnel > 8192 || d->npix < 16 || d->npix > d->n_fresnel ||
+        (d->npix & 1)) {
+        coro::set_error("coro_wfc_plan_create: n_fresnel must be a power of two in [32, 8192], npix even in [16, n_fresnel]");
+        return CORO_ESIZE;
+    }
+    if (!(d->diam_m > 0) || !(d->z_m != 0) || d->n_act < 1 || !(d->act_pitch_m > 0) || !(d->act_fwhm_m > 0)) {
+        coro::set_error("coro_wfc_plan_create: need diam, pitch, fwhm > 0, z != 0, n_act >= 1");
+        return CORO_EINVAL;
+    }
+    coro::DeviceGuard gd(ctx->device);
+    auto p = std::unique_ptr<WfcPlan>(new (std::nothrow) WfcPlan);
+    if (!p) { coro::set_error("out of host memory"); return CORO_ENOMEM; }
+    p->ctx = ctx;
+    p->device = ctx->device;
+    p->d = *d;
+    p->lam.assign(d->wavelength, d->wavelength + d->batch);
+    p->ps.assign(d->batch, d->diam_m / d->npix);
+    p->items.assign(d->items, d->items + d->batch);
+    p->d.wavelength = p->lam.data();
+    p->d.items = p->items.data();
+    coro_lyot_desc ld{d->batch, d->npix, (double)d->npix, d->lyot_frac, d->m_det, p->items.data(), d->precision};
+    coro_status st = coro_lyot_plan_create(ctx, &ld, &p->lyot);
+    if (st != CORO_OK) return st;
+    const int nf = d->n_fresnel;
+    if ((st = coro_lyot_plan_set_pupil_layout(p->lyot, nf, (long long)nf * nf)) != CORO_OK) return st;
+    const size_t fbytes = (size_t)d->batch * nf * nf * sizeof(float2), mbytes = (size_t)nf * nf * sizeof(float);
+    p->e0 = (float2*)p->alloc(fbytes, &st);
+    p->e1 = p->e0 ? (float2*)p->alloc(fbytes, &st) : nullptr;
+    p->w = p->e1 ? (float2*)p->alloc(fbytes, &st) : nullptr;
+    p->g = p->w ? (float2*)p->alloc(fbytes, &st) : nullptr;
+    p->opd1 = p->g ? (float*)p->alloc(mbytes, &st) : nullptr;
+    p->opd2 = p->opd1 ? (float*)p->alloc(mbytes, &st) : nullptr;
+    p->opd2n = p->opd2 ? (float*)p->alloc(mbytes, &st) : nullptr;
+    p->dphi = p->opd2n ? (float*)p->alloc(2 * mbytes, &st) : nullptr;
+    p->zero_h = p->dphi ? (float*)p->alloc((size_t)2 * d->n_act * d->n_act * sizeof(float), &st) : nullptr;
+    p->k_d = p->zero_h ? (float*)p->alloc(d->batch * sizeof(float), &st) : nullptr;
+    p->w_d = p->k_d ? (float*)p->alloc(d->batch * sizeof(float), &st) : nullptr;
+    if (!p->w_d) return st;
+    std::vector<float> k(d->batch), w(d->batch);
+    for (int b = 0; b < d->batch; ++b) {
+        if (!(d->wavelength[b] > 0)) { coro::set_error("coro_wfc_plan_create: wavelength[%d] must be > 0", b); return CORO_EINVAL; }
+        k[b] = (float)(2.0 / d->wavelength[b]);
+        w[b] = (float)(4.0 * M_PI / d->wavelength[b]);     // dphi/dh = 2 (reflection) x 2 pi / lambda
+    }
+    cudaError_t e = cudaMemsetAsync(p->zero_h, 0, (size_t)2 * d->n_act * d->n_act * sizeof(float), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->k_d, k.data(), d->batch * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->w_d, w.data(), d->batch * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return coro::cuda_fail(e, "coro_wfc_plan_create");
+    *out = p.release();
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_wfc_plan_peak(coro_plan plan, double* peak_out) {
+    coro::clear_error();
+    if (!plan || plan->kind() != 3) { coro::set_error("coro_wfc_plan_peak: not a wavefront-control plan"); return CORO_EINVAL; }
+    auto* p = static_cast<WfcPlan*>(plan);
+    coro::DeviceGuard gd(p->device);
+    coro_status st = fresnel_forward(p, p->zero_h);
+    if (st != CORO_OK) return st;
+    p->peak.assign(p->d.batch, 0.0);
+    if ((st = coro_lyot_plan_peak(p->lyot, window(p, p->w), p->peak.data())) != CORO_OK) return st;
+    if (peak_out)
+        for (int b = 0; b < p->d.batch; ++b) peak_out[b] = p->peak[b];
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_wfc_plan_evaluate(coro_plan plan, const float* heights, double* loss, double* per_item,
+                                              float* grad) {
+    coro::clear_error();
+    if (!plan || plan->kind() != 3) { coro::set_error("coro_wfc_plan_evaluate: not a wavefront-control plan"); return CORO_EINVAL; }
+    if (!heights) { coro::set_error("coro_wfc_plan_evaluate: heights is NULL"); return CORO_EINVAL; }
+    auto* p = static_cast<WfcPlan*>(plan);
+    coro::DeviceGuard gd(p->device);
+    coro_status st;
+    if (p->peak.empty() && (st = coro_wfc_plan_peak(plan, nullptr)) != CORO_OK) return st;
+    const coro_wfc_desc& d = p->d;
+    coro_ctx c = p->ctx;
+    const int B = d.batch, nf = d.n_fresnel, na = d.n_act;
+    if ((st = fresnel_forward(p, heights)) != CORO_OK) return st;
+    std::vector<double> dh(B, 0.0);
+    if (!grad) {
+        st = coro_lyot_plan_execute(p->lyot, window(p, p->w), p->peak.data(), nullptr, nullptr, dh.data());
+    } else {
+        const size_t fbytes = (size_t)B * nf * nf * sizeof(float2);
+        cudaError_t e = cudaMemsetAsync(p->g, 0, fbytes, c->stream);     // pad(): zero outside the window
+        if (e != cudaSuccess) return coro::cuda_fail(e, "wfc: memset");
+        st = coro_lyot_plan_gradient(p->lyot, window(p, p->w), p->peak.data(), dh.data(), window(p, p->g), nf,
+                                     (long long)nf * nf);
+        coro_wavefront fg = field(p, p->g);
+        const size_t npx = (size_t)nf * nf;
+        const int blocks = (int)std::min<size_t>((npx + 255) / 256, 152 * 8);
+        // G2 = AS(+z) G3; dL/dphi2 = 2 Im(G2 conj(E1 exp(i phi2)))
+        if (st == CORO_OK) st = coro_propagate_fresnel(c, &fg, d.z_m, CORO_FRESNEL_AS);
+        if (st == CORO_OK) {
+            phase_grad_kernel<<<blocks, 256, 0, c->stream>>>(p->g, p->e1, p->opd2, p->k_d, p->w_d, B, npx, p->dphi + npx);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) st = coro::cuda_fail(e, "phase_grad_kernel");
+        }
+        // G0 = AS(-z)(exp(-i phi2) G2); dL/dphi1 = 2 Im(G0 conj(E0))
+        coro_element o2n = opd_elem(p->opd2n);
+        if (st == CORO_OK) st = coro_apply_element(c, &fg, &o2n);
+        if (st == CORO_OK) st = coro_propagate_fresnel(c, &fg, -d.z_m, CORO_FRESNEL_AS);
+        if (st == CORO_OK) {
+            phase_grad_kernel<<<blocks, 256, 0, c->stream>>>(p->g, p->e0, nullptr, p->k_d, p->w_d, B, npx, p->dphi);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) st = coro::cuda_fail(e, "phase_grad_kernel");
+        }
+        const double dx = d.diam_m / d.npix;
+        if (st == CORO_OK) st = coro_dm_correlate(c, p->dphi, 1, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, grad);
+        if (st == CORO_OK)
+            st = coro_dm_correlate(c, p->dphi + npx, 1, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, grad + na * na);
+        if (st == CORO_OK) {
+            e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) st = coro::cuda_fail(e, "coro_wfc_plan_evaluate");
+        }
+    }
+    if (st != CORO_OK) return st;
+    double total = 0.0;
+    for (int b = 0; b < B; ++b) {
+        total += dh[b];
+        if (per_item) per_item[b] = dh[b];
+    }
+    if (loss) *loss = total;
+    return CORO_OK;
+}
