@@ -5,8 +5,10 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <string>
 
 #include "capi_common.h"
 #include "passes.cuh"
@@ -453,7 +455,8 @@ struct Op {
     PassElems elems{};
     const void* tab_x = nullptr;
     const void* tab_y = nullptr;
-    int lines = 0;
+    int lines = 0;        // column passes: block width (0 default, -1 persistent TMA kernel)
+    int variant = 0;      // row passes: 0 persistent, 1 one block per line group
 };
 
 template <typename C>
@@ -472,6 +475,7 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
             a.flags = op.row_flags;
             a.err = ctx->err;
             a.elems = op.elems;
+            pl.variant = op.variant;
             e = launch_row_pass<C>(n, a, pl);
         } else {
             ColArgs<C> a;
@@ -481,6 +485,7 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
             a.tab_x = (const C*)op.tab_x;
             a.tab_y = (const C*)op.tab_y;
             a.flags = op.col_flags;
+            a.err = ctx->err;
             e = launch_col_pass<C>(n, op.lines, a, pl);
         }
         if (e != cudaSuccess) return cuda_fail(e, op.row ? "row pass" : "column pass");
@@ -654,6 +659,76 @@ extern "C" coro_status coro_fft2(coro_ctx ctx, const coro_wavefront* wf, int dir
 
 namespace {
 
+// Plan-time autotuner: times the candidate row and column kernels on a scratch field of the
+// plan's size and keeps the fastest (CORO_AUTOTUNE=0 keeps the defaults).
+bool autotune_enabled() {
+    const char* v = std::getenv("CORO_AUTOTUNE");
+    return !(v && v[0] == '0');
+}
+
+template <typename C>
+float time_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, void* field, int reps) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return 1e30f;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 1e30f; }
+    float ms = 1e30f;
+    if (run_ops<C>(ctx, n, batch, ops, field) == CORO_OK) {          // warm-up
+        cudaEventRecord(a, ctx->stream);
+        bool ok = true;
+        for (int r = 0; r < reps && ok; ++r) ok = run_ops<C>(ctx, n, batch, ops, field) == CORO_OK;
+        cudaEventRecord(b, ctx->stream);
+        if (ok && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    clear_error();
+    return ms;
+}
+
+coro_status autotune_ops(coro_ctx ctx, int dtype, int n, int batch, std::vector<Op>& ops, std::vector<std::string>* log) {
+    if (dtype != CORO_C64 || !autotune_enabled()) return CORO_OK;
+    int cand[4];
+    const int nc = col_candidates(n, cand), nr = row_variant_count(n);
+    if (nc < 2 && nr < 2) return CORO_OK;
+    coro_status st = CORO_OK;
+    void* scratch = upload_async(ctx, nullptr, (size_t)batch * n * n * sizeof(float2), &st);
+    if (!scratch) { clear_error(); return CORO_OK; }      // no room to tune: keep the defaults
+    cudaMemsetAsync(scratch, 0, (size_t)batch * n * n * sizeof(float2), ctx->stream);
+    const Op* col = nullptr;
+    const Op* row = nullptr;
+    for (const Op& op : ops) {
+        if (!op.row && !col) col = &op;
+        if (op.row && (op.row_flags & (RF_INV_FIRST | RF_FWD_AFTER)) && (!row || (row->row_flags & RF_INIT_ONE))) row = &op;
+    }
+    int best_lines = 0, best_variant = 0;
+    if (col && nc > 1) {
+        float best = 1e30f;
+        for (int i = 0; i < nc; ++i) {
+            Op t = *col;
+            t.lines = cand[i];
+            const float ms = time_ops<float2>(ctx, n, batch, {t}, scratch, 3);
+            if (log) log->push_back("col lines " + std::to_string(cand[i]) + ": " + std::to_string(ms / 3) + " ms");
+            if (ms < best) { best = ms; best_lines = cand[i]; }
+        }
+    }
+    if (row && nr > 1) {
+        float best = 1e30f;
+        for (int v = 0; v < nr; ++v) {
+            Op t = *row;
+            t.variant = v;
+            const float ms = time_ops<float2>(ctx, n, batch, {t}, scratch, 3);
+            if (log) log->push_back("row variant " + std::to_string(v) + ": " + std::to_string(ms / 3) + " ms");
+            if (ms < best) { best = ms; best_variant = v; }
+        }
+    }
+    for (Op& op : ops) {
+        if (op.row) op.variant = best_variant;
+        else op.lines = best_lines;
+    }
+    free_async(ctx, scratch);
+    return CORO_OK;
+}
+
 struct FresnelPlan : coro_plan_s {
     coro_ctx ctx = nullptr;
     int device = 0;                  // kept so that destruction never touches the context
@@ -661,6 +736,7 @@ struct FresnelPlan : coro_plan_s {
     std::vector<Op> ops;
     DevBlocks db;
     std::vector<double> ps_final;
+    std::vector<std::string> tune_log;
     int kind() const override { return 1; }
     int launches() const override { return (int)ops.size(); }
     ~FresnelPlan() override {
@@ -755,6 +831,10 @@ extern "C" coro_status coro_fresnel_plan_create(coro_ctx ctx, const coro_fresnel
     }
     plan->ps_final = ps;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);   // tables ready; plan owns them
+    if (e == cudaSuccess) {
+        autotune_ops(ctx, d->dtype, n, batch, plan->ops, &plan->tune_log);
+        e = cudaStreamSynchronize(ctx->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "coro_fresnel_plan_create");
     *out = plan.release();
     return CORO_OK;

@@ -357,6 +357,7 @@ struct ColArgs {
     const C* tab_x;       // [batch][N]
     const C* tab_y;       // [batch][N]
     int flags;
+    int* err;             // bounded-wait failure flag (persistent kernel)
 };
 
 template <int N, int L> struct ColCfg {
@@ -397,11 +398,97 @@ col_pass_kernel(const __grid_constant__ ColArgs<C> a) {
     for (int s = 0; s < 16; ++s) a.out[base + (size_t)(t + s * Cfg::TPL) * N] = v[s];
 }
 
+// ------------------------------------------------------------------------------ persistent column pass
+//
+// A column group (L adjacent columns x N rows) arrives as N/256 tiled TMA boxes of
+// 256 rows x L samples into one of two shared buffers while the previous group is being
+// transformed, and leaves by TMA tensor stores from the buffer it arrived in. The FFT
+// exchanges use a separate padded buffer. `map` views the field as a 2-D array of 8-byte
+// samples: x = column (N), y = item * N + row.
+
+template <int N, int L> struct PColCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int THREADS = TPL * L;
+    static constexpr int GROUP = L * N;
+    static constexpr int BOXES = N / 256;
+    static constexpr int STRIDE = ColCfg<N, L>::STRIDE;
+    template <typename C> static constexpr size_t smem() {
+        return 2 * (size_t)GROUP * sizeof(C) + (size_t)L * STRIDE * sizeof(C) + 64;
+    }
+};
+
+template <typename C, int N, int L>
+__global__ void __launch_bounds__(PColCfg<N, L>::THREADS)
+col_pass_persistent_kernel(const __grid_constant__ ColArgs<C> a, const __grid_constant__ CUtensorMap map, int groups) {
+    using Cfg = PColCfg<N, L>;
+    constexpr uint32_t BYTES = Cfg::GROUP * sizeof(C);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + Cfg::GROUP;
+    C* xbuf = buf1 + Cfg::GROUP;
+    uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + L * Cfg::STRIDE);
+    const int c = threadIdx.x % L;
+    const int t = threadIdx.x / L;
+    C* xl = xbuf + c * Cfg::STRIDE;
+    constexpr int GPI = N / L;                       // groups per item
+
+    auto issue_load = [&](C* dst, uint64_t* bar, int g) {
+        const int x = (g % GPI) * L, y = (g / GPI) * N;
+        tc::mbar_arrive_expect_tx(bar, BYTES);
+#pragma unroll 1
+        for (int k = 0; k < Cfg::BOXES; ++k) tc::tma_load_2d(dst + k * 256 * L, &map, bar, x, y + k * 256);
+    };
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&full[0], 1);
+        tc::mbar_init(&full[1], 1);
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&map);
+        if (blockIdx.x < groups) issue_load(buf0, &full[0], blockIdx.x);
+    }
+    __syncthreads();
+    int it = 0;
+    bool ok = true;
+    for (int g = blockIdx.x; g < groups; g += gridDim.x, ++it) {
+        C* ib = (it & 1) ? buf1 : buf0;
+        C* nb = (it & 1) ? buf0 : buf1;
+        const int b = g / GPI, col = (g % GPI) * L + c;
+        if (ok) ok = tc::mbar_wait(&full[it & 1], (it >> 1) & 1, a.err, 6);
+        C v[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) v[s] = ib[(t + s * Cfg::TPL) * L + c];
+        if (threadIdx.x == 0 && g + (int)gridDim.x < groups) {
+            tc::bulk_wait_read<0>();                    // group g-1's stores have left nb
+            issue_load(nb, &full[(it + 1) & 1], g + gridDim.x);
+        }
+        if (a.flags & CF_FWD) line_fft<C, N, false>(v, xl, t, a.tw);
+        if (a.flags & CF_TABLE) {
+            const C hx = a.tab_x[(size_t)b * N + col];
+            const C* ty = a.tab_y + (size_t)b * N;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], cmul(hx, ty[t + s * Cfg::TPL]));
+        }
+        if (a.flags & CF_INV) line_fft<C, N, true>(v, xl, t, a.tw);
+        __syncthreads();                                 // every thread has read ib before it is rewritten
+#pragma unroll
+        for (int s = 0; s < 16; ++s) ib[(t + s * Cfg::TPL) * L + c] = v[s];
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int x = (g % GPI) * L, y = b * N;
+#pragma unroll 1
+            for (int k = 0; k < Cfg::BOXES; ++k) tc::tma_store_2d(&map, ib + k * 256 * L, x, y + k * 256);
+            tc::bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) tc::bulk_wait<0>();
+}
+
 // ------------------------------------------------------------------------------ launchers
 
 struct PassLaunch {
     cudaStream_t stream;
     int batch;
+    int variant = 0;      // row passes: 0 persistent (where built), 1 one block per line group
 };
 
 // Implemented per precision in passes_f32.cu / passes_f64.cu.
@@ -409,7 +496,10 @@ template <typename C>
 cudaError_t launch_row_pass(int n, const RowArgs<C>& a, const PassLaunch& l);
 template <typename C>
 cudaError_t launch_col_pass(int n, int lines, const ColArgs<C>& a, const PassLaunch& l);
-// Supported column widths for a given n (first = default).
+// Column widths per block for n (0 picks the default); -1 selects the persistent TMA kernel.
 int col_lines_default(int n, bool dbl);
+// Candidate column variants and row variants the plan autotuner times for n (complex64).
+int col_candidates(int n, int* out);
+int row_variant_count(int n);
 
 }  // namespace coro

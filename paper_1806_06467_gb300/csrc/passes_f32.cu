@@ -12,10 +12,10 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
         case 128: return row_launch<float2, 128>(a, l);
         case 256: return row_launch<float2, 256>(a, l);
         case 512: return row_launch<float2, 512>(a, l);
-        case 1024: return row_launch_persistent<float2, 1024>(a, l);
-        case 2048: return row_launch_persistent<float2, 2048>(a, l);
-        case 4096: return row_launch_persistent<float2, 4096>(a, l);
-        case 8192: return row_launch_persistent<float2, 8192>(a, l);
+        case 1024: return l.variant == 1 ? row_launch<float2, 1024>(a, l) : row_launch_persistent<float2, 1024>(a, l);
+        case 2048: return l.variant == 1 ? row_launch<float2, 2048>(a, l) : row_launch_persistent<float2, 2048>(a, l);
+        case 4096: return l.variant == 1 ? row_launch<float2, 4096>(a, l) : row_launch_persistent<float2, 4096>(a, l);
+        case 8192: return l.variant == 1 ? row_launch<float2, 8192>(a, l) : row_launch_persistent<float2, 8192>(a, l);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -32,9 +32,15 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
         case 128: return col_launch<float2, 128, 16>(a, l);
         case 256: return col_launch<float2, 256, 16>(a, l);
         case 512: return col_launch<float2, 512, 16>(a, l);
-        case 1024: return lines == 8 ? col_launch<float2, 1024, 8>(a, l) : col_launch<float2, 1024, 16>(a, l);
-        case 2048: return lines == 4 ? col_launch<float2, 2048, 4>(a, l) : col_launch<float2, 2048, 8>(a, l);
-        case 4096: return lines == 2 ? col_launch<float2, 4096, 2>(a, l) : col_launch<float2, 4096, 4>(a, l);
+        case 1024:
+            if (lines == -1) return col_launch_persistent<float2, 1024, 4>(a, l);
+            return lines == 8 ? col_launch<float2, 1024, 8>(a, l) : col_launch<float2, 1024, 16>(a, l);
+        case 2048:
+            if (lines == -1) return col_launch_persistent<float2, 2048, 2>(a, l);
+            return lines == 4 ? col_launch<float2, 2048, 4>(a, l) : col_launch<float2, 2048, 8>(a, l);
+        case 4096:
+            if (lines == -1) return col_launch_persistent<float2, 4096, 2>(a, l);
+            return lines == 2 ? col_launch<float2, 4096, 2>(a, l) : col_launch<float2, 4096, 4>(a, l);
         case 8192: return lines == 1 ? col_launch<float2, 8192, 1>(a, l) : col_launch<float2, 8192, 2>(a, l);
         default: return cudaErrorInvalidValue;
     }
@@ -57,5 +63,17 @@ int col_lines_default(int n, bool dbl) {
         default: return 16;
     }
 }
+
+int col_candidates(int n, int* out) {
+    switch (n) {
+        case 8192: out[0] = 2; out[1] = 1; return 2;
+        case 4096: out[0] = 4; out[1] = 2; out[2] = -1; return 3;
+        case 2048: out[0] = 8; out[1] = 4; out[2] = -1; return 3;
+        case 1024: out[0] = 16; out[1] = 8; out[2] = -1; return 3;
+        default: out[0] = 0; return 1;
+    }
+}
+
+int row_variant_count(int n) { return n >= 1024 ? 2 : 1; }
 
 }  // namespace coro

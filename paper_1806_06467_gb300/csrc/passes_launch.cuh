@@ -2,6 +2,7 @@
 // complex type. Included once per precision (passes_f32.cu, passes_f64.cu).
 #pragma once
 #include "passes.cuh"
+#include "tc_gemm.cuh"
 
 namespace coro {
 namespace detail {
@@ -55,6 +56,33 @@ cudaError_t row_launch(const RowArgs<C>& a, const PassLaunch& l) {
     if (e != cudaSuccess) return e;
     dim3 grid(N / Cfg::L, l.batch);
     row_pass_kernel<C, N><<<grid, Cfg::THREADS, smem, l.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename C, int N, int L>
+cudaError_t col_launch_persistent(const ColArgs<C>& a, const PassLaunch& l) {
+    using Cfg = PColCfg<N, L>;
+    static unsigned done = 0;
+    static int per_sm[32] = {};
+    const size_t smem = Cfg::template smem<C>();
+    cudaError_t e = ensure_smem(col_pass_persistent_kernel<C, N, L>, smem, done);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int& occ = per_sm[dev & 31];
+    if (occ == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, col_pass_persistent_kernel<C, N, L>, Cfg::THREADS, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+    }
+    // in place: the same map serves the loads and the stores
+    if (a.in != a.out) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    if ((e = tc_make_field_map(a.in, N, (long long)l.batch * N, L, &map)) != cudaSuccess) return e;
+    const int groups = l.batch * N / L;
+    const int grid = groups < sms * occ ? groups : sms * occ;
+    col_pass_persistent_kernel<C, N, L><<<grid, Cfg::THREADS, smem, l.stream>>>(a, map, groups);
     return cudaGetLastError();
 }
 
