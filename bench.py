@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-coronagraph", action="store_true")
     ap.add_argument("--bf16", action="store_true", help="also time the 3xBF16 coronagraph plan")
+    ap.add_argument("--psf-lambdas", type=int, default=21, help="wavelengths in the coronagraph batch")
+    ap.add_argument("--psf-probes", type=int, default=8, help="DM probe states in the coronagraph batch")
     return ap.parse_args()
 
 
@@ -133,8 +135,9 @@ def pass_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kind: str) -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels."""
+def recorded_traffic(kernel: str) -> float | None:
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if taken on the
+    current pass sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
@@ -142,7 +145,7 @@ def recorded_traffic(kind: str) -> float | None:
         return None
     if t.get("source_hash") != pass_source_hash():
         return None
-    return t.get(kind, {}).get("dram_bytes_per_launch")
+    return t.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch")
 
 
 def relay_setup(n: int, seed: int, device):
@@ -309,14 +312,14 @@ def tensor_peak(precision_bf16: bool) -> tuple[float, str]:
     return bf16 * 1.1 / 2.25, src + " x 1.1/2.25 (tf32)"
 
 
-def broadband_pupils(ctx, device):
+def broadband_pupils(ctx, device, n_lambda: int = 21, n_probe: int = 8):
     """168 pupil fields (21 wavelengths x 8 DM sinc probes): clear aperture, Zernike 4-21 at 5 nm
     RMS and the probe's DM surface (Gaussian influence, FWHM 1 pitch), built by the library."""
     import numpy as np
     import torch
 
     from paper_1806_06467_gb300 import coro, inputs
-    bw = inputs.BroadbandWorkload()
+    bw = inputs.BroadbandWorkload(n_lambda=n_lambda, n_probe=n_probe)
     lw = bw.lyot
     lams = bw.wavelengths()
     lam_b = np.repeat(lams, bw.n_probe)
@@ -340,12 +343,13 @@ def broadband_pupils(ctx, device):
     return field, items, lw
 
 
-def coronagraph_bench(ctx, device, steps: int, warmup: int, precision: int) -> dict:
+def coronagraph_bench(ctx, device, steps: int, warmup: int, precision: int, n_lambda: int = 21,
+                      n_probe: int = 8) -> dict:
     import numpy as np
     import torch
 
     from paper_1806_06467_gb300 import coro
-    pupils, items, lw = broadband_pupils(ctx, device)
+    pupils, items, lw = broadband_pupils(ctx, device, n_lambda, n_probe)
     B, n, md = len(items), lw.n, lw.m_det
     plan = coro.LyotPlan(ctx, n=n, npix=lw.npix, lyot_frac=lw.lyot_frac, m_det=md, items=items, precision=precision)
     peak = plan.peak(pupils)                          # normalisation, computed once
@@ -468,6 +472,7 @@ def main():
                             distances=list(w.distances()), elements=els, init_uniform=True)
     n_pass = plan.launch_count
     info = [plan.pass_info(i) for i in range(n_pass)]
+    kernels = [plan.pass_kernel(i) for i in range(n_pass)]
     field = torch.empty((1, n, n), dtype=torch.complex64, device=device)
 
     for _ in range(args.warmup):
@@ -504,24 +509,27 @@ def main():
     value = HOPS * args.steps * world / (t_max / 1e3)
 
     # -------- roofline of the dominant pass kind
-    kinds = {"row": [0.0, 0.0, 0], "col": [0.0, 0.0, 0]}
+    kinds = {"row": [0.0, 0.0, 0, set()], "col": [0.0, 0.0, 0, set()]}
     for i, (is_row, nbytes) in enumerate(info):
         kk = "row" if is_row else "col"
         kinds[kk][0] += per_pass[:, i].sum()
         kinds[kk][1] += nbytes * args.steps
         kinds[kk][2] += args.steps
+        kinds[kk][3].add(kernels[i])
     dom = max(kinds, key=lambda k: kinds[k][0])
-    t_dom, b_dom, l_dom = kinds[dom]
+    t_dom, b_dom, l_dom, k_dom = kinds[dom]
+    k_name = ", ".join(sorted(k_dom))
     peak, peak_src = measured_peaks()
     achieved = b_dom / (t_dom / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(dom), "kernel": f"{dom}_pass_kernel",
+                "traffic": recorded_traffic(k_name) if len(k_dom) == 1 else None, "kernel": k_name,
                 "bytes_per_launch": b_dom / l_dom, "us_per_launch": 1e3 * t_dom / l_dom,
                 "time_share": t_dom / per_pass.sum(), "peak_source": f"{peak_src} hbm_gbs (copy)"}
     other = "col" if dom == "row" else "row"
     if kinds[other][2]:
-        t_o, b_o, l_o = kinds[other]
-        roofline["other_kernel"] = {"kernel": f"{other}_pass_kernel", "achieved": b_o / (t_o / 1e3) / 1e9,
+        t_o, b_o, l_o, k_o = kinds[other]
+        roofline["other_kernel"] = {"kernel": ", ".join(sorted(k_o)), "achieved": b_o / (t_o / 1e3) / 1e9,
+                                    "traffic": recorded_traffic(next(iter(k_o))) if len(k_o) == 1 else None,
                                     "frac": b_o / (t_o / 1e3) / 1e9 / peak, "us_per_launch": 1e3 * t_o / l_o,
                                     "time_share": t_o / per_pass.sum()}
 
@@ -550,10 +558,12 @@ def main():
     extras = {}
     if not args.no_coronagraph:
         k_psf = max(3, args.steps // 2)
-        extras["coronagraph"] = coronagraph_bench(ctx, device, k_psf, max(1, min(3, args.warmup)), coro.MFT_3XTF32)
+        extras["coronagraph"] = coronagraph_bench(ctx, device, k_psf, max(1, min(3, args.warmup)), coro.MFT_3XTF32,
+                                                  args.psf_lambdas, args.psf_probes)
         extras["coronagraph"]["value"] *= world
         if args.bf16:
-            extras["coronagraph_3xbf16"] = coronagraph_bench(ctx, device, k_psf, 1, coro.MFT_3XBF16)
+            extras["coronagraph_3xbf16"] = coronagraph_bench(ctx, device, k_psf, 1, coro.MFT_3XBF16,
+                                                             args.psf_lambdas, args.psf_probes)
         if rank == 0 and not args.no_plain:
             extras["coronagraph"]["plain_gpu"] = coronagraph_plain(device, max(2, k_psf // 3))
             extras["coronagraph"]["plain_gpu"]["speedup_of_coro"] = (

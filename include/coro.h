@@ -193,6 +193,14 @@ coro_status coro_fresnel_plan_execute_range(coro_plan plan, void* field, int fir
 /* Describe pass i: *is_row (1 = row pass, 0 = column pass) and *bytes, the algorithmic HBM
  * traffic of the launch (field read unless generated, field write, OPD/amplitude maps read). */
 coro_status coro_fresnel_plan_pass_info(coro_plan plan, int i, int* is_row, double* bytes);
+/* Kernel that pass i launches, as chosen when the plan was built (the complex64 plan times
+ * its candidates then unless the environment sets CORO_AUTOTUNE=0):
+ * *persistent = 1 for the persistent kernel (one block per SM slot, lines staged through
+ * shared memory by bulk or TMA copies while the previous lines are transformed), 0 for one
+ * block per group of lines; *lines = lines one block holds (columns for a column pass) for a
+ * non-persistent column pass, columns per staged group for a persistent one, 0 for a row pass.
+ * Either output pointer may be NULL. Plain host query; no device work. */
+coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent, int* lines);
 coro_status coro_plan_destroy(coro_plan plan);
 
 /* ------------------------------------------------------------------------------------------

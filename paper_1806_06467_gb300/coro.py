@@ -101,6 +101,7 @@ _SIGS = {
     "coro_plan_launch_count": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "coro_fresnel_plan_execute_range": (ct.c_int, [_P, _P, ct.c_int, ct.c_int]),
     "coro_fresnel_plan_pass_info": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]),
+    "coro_fresnel_plan_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "coro_plan_destroy": (ct.c_int, [_P]),
     "coro_propagate_mft": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_double, ct.c_int, ct.c_int,
                                       ct.POINTER(ct.c_double), ct.c_int, ct.POINTER(Wavefront)]),
@@ -409,6 +410,7 @@ class FresnelPlan:
                  elements: Sequence[Element], methods=None, dtype: int = C64, init_uniform: bool = False):
         self.ctx = ctx
         self.batch = batch
+        self.n = n
         d = FresnelDesc()
         d.dtype, d.batch, d.n = dtype, batch, n
         self._ps = _dbl(np.broadcast_to(np.asarray(pixelscale, float), (batch,)))
@@ -444,6 +446,15 @@ class FresnelPlan:
         r, b = ct.c_int(), ct.c_double()
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_info(self.handle, i, ct.byref(r), ct.byref(b)))
         return bool(r.value), b.value
+
+    def pass_kernel(self, i: int) -> str:
+        """Name of the kernel pass i launches, e.g. 'col_pass_persistent<4096,2>'."""
+        p, w = ct.c_int(), ct.c_int()
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_kernel(self.handle, i, ct.byref(p), ct.byref(w)))
+        row, _ = self.pass_info(i)
+        kind = "row_pass" if row else "col_pass"
+        name = kind + ("_persistent" if p.value else "_kernel")
+        return f"{name}<{self.n}>" if row else f"{name}<{self.n},{w.value}>"
 
     @property
     def launch_count(self) -> int:

@@ -888,6 +888,16 @@ extern "C" coro_status coro_fresnel_plan_pass_info(coro_plan plan, int i, int* i
     return CORO_OK;
 }
 
+extern "C" coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent, int* lines) {
+    clear_error();
+    if (!plan || plan->kind() != 1) { set_error("coro_fresnel_plan_pass_kernel: not a Fresnel plan"); return CORO_EINVAL; }
+    auto* p = static_cast<FresnelPlan*>(plan);
+    if (i < 0 || i >= (int)p->ops.size()) { set_error("coro_fresnel_plan_pass_kernel: pass %d of %d", i, (int)p->ops.size()); return CORO_EINVAL; }
+    const Op& op = p->ops[i];
+    describe_pass(p->n, p->dtype == CORO_C128, op.row, op.variant, op.lines, persistent, lines);
+    return CORO_OK;
+}
+
 extern "C" coro_status coro_plan_launch_count(coro_plan plan, int* out) {
     clear_error();
     if (!plan || !out) { set_error("coro_plan_launch_count: NULL argument"); return CORO_EINVAL; }

@@ -366,12 +366,14 @@ template <int N, int L> struct ColCfg {
     // column c's region starts at c * STRIDE; STRIDE = 16/L (mod 16) spreads the L columns a
     // half-warp touches over distinct banks.
     static constexpr int STRIDE = LineGeom<N>::STRIDE + ((16 / L) & 15);
+    // blocks of at most 512 threads are held to 64 registers so that two fit on an SM
+    static constexpr int MINB = THREADS <= 512 ? 2 : 1;
 };
 
 // grid: (N / L, batch); one block = L adjacent columns of one item. Thread (t, c) = t*L + c,
 // so a warp reads 32/L rows x L contiguous columns.
 template <typename C, int N, int L>
-__global__ void __launch_bounds__(ColCfg<N, L>::THREADS)
+__global__ void __launch_bounds__(ColCfg<N, L>::THREADS, ColCfg<N, L>::MINB)
 col_pass_kernel(const __grid_constant__ ColArgs<C> a) {
     using Cfg = ColCfg<N, L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -501,5 +503,7 @@ int col_lines_default(int n, bool dbl);
 // Candidate column variants and row variants the plan autotuner times for n (complex64).
 int col_candidates(int n, int* out);
 int row_variant_count(int n);
+// The kernel a pass with these settings launches: persistent (1) or not, and its lines.
+void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persistent, int* out_lines);
 
 }  // namespace coro

@@ -76,4 +76,24 @@ int col_candidates(int n, int* out) {
 
 int row_variant_count(int n) { return n >= 1024 ? 2 : 1; }
 
+void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persistent, int* out_lines) {
+    int p = 0, w = 0;
+    if (row) {
+        p = (!dbl && n >= 1024 && variant != 1) ? 1 : 0;     // mirrors launch_row_pass
+    } else if (dbl) {
+        w = col_lines_default(n, true);                     // the double launcher ignores `lines`
+    } else {                                                // mirrors launch_col_pass<float2>
+        if (lines == 0) lines = col_lines_default(n, false);
+        switch (n) {
+            case 1024: p = lines == -1; w = p ? 4 : (lines == 8 ? 8 : 16); break;
+            case 2048: p = lines == -1; w = p ? 2 : (lines == 4 ? 4 : 8); break;
+            case 4096: p = lines == -1; w = p ? 2 : (lines == 2 ? 2 : 4); break;
+            case 8192: w = lines == 1 ? 1 : 2; break;
+            default: w = 16; break;
+        }
+    }
+    if (persistent) *persistent = p;
+    if (out_lines) *out_lines = w;
+}
+
 }  // namespace coro
