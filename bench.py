@@ -533,6 +533,9 @@ def main():
                                     "frac": b_o / (t_o / 1e3) / 1e9 / peak, "us_per_launch": 1e3 * t_o / l_o,
                                     "time_share": t_o / per_pass.sum()}
 
+    passes = [{"kernel": kernels[i], "us": round(1e3 * float(np.median(per_pass[:, i])), 2),
+               "bytes": info[i][1]} for i in range(n_pass)]
+
     # -------- end to end through host buffers
     e2e = None
     if not args.no_e2e:
@@ -585,7 +588,7 @@ def main():
                "config": {"workload": f"relay6_{n}", "n": n, "npix": n // 4, "planes_per_step": HOPS,
                           "batch": 1, "parallelism": f"replicas{world}",
                           "l2": f"inputs larger than L2 ({n * n * 8 / 1e6:.0f} MB field + 2 x {n * n * 4 / 1e6:.0f} MB maps)"},
-               "gpu_launches": n_pass * args.steps, "roofline": roofline, "cpu_baseline": cpu,
+               "gpu_launches": n_pass * args.steps, "roofline": roofline, "passes": passes, "cpu_baseline": cpu,
                "e2e": e2e, "clocks": clk}
         out.update(extras)
         print(json.dumps(out), flush=True)

@@ -102,6 +102,7 @@ _SIGS = {
     "coro_fresnel_plan_execute_range": (ct.c_int, [_P, _P, ct.c_int, ct.c_int]),
     "coro_fresnel_plan_pass_info": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]),
     "coro_fresnel_plan_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "coro_fresnel_plan_set_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.c_int]),
     "coro_plan_destroy": (ct.c_int, [_P]),
     "coro_propagate_mft": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_double, ct.c_int, ct.c_int,
                                       ct.POINTER(ct.c_double), ct.c_int, ct.POINTER(Wavefront)]),
@@ -453,8 +454,13 @@ class FresnelPlan:
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_kernel(self.handle, i, ct.byref(p), ct.byref(w)))
         row, _ = self.pass_info(i)
         kind = "row_pass" if row else "col_pass"
-        name = kind + ("_persistent" if p.value else "_kernel")
+        name = kind + ("_kernel", "_persistent", "_units")[p.value]
         return f"{name}<{self.n}>" if row else f"{name}<{self.n},{w.value}>"
+
+    def set_pass_kernel(self, row_variant: int, col_lines: int) -> None:
+        """Override the tuned kernels (row: 0 persistent, 1 per-group, 2 units; column:
+        lines per block, -1 persistent TMA, -2 units, 0 default)."""
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_set_pass_kernel(self.handle, row_variant, col_lines))
 
     @property
     def launch_count(self) -> int:

@@ -898,6 +898,30 @@ extern "C" coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int*
     return CORO_OK;
 }
 
+extern "C" coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, int col_lines) {
+    clear_error();
+    if (!plan || plan->kind() != 1) { set_error("coro_fresnel_plan_set_pass_kernel: not a Fresnel plan"); return CORO_EINVAL; }
+    auto* p = static_cast<FresnelPlan*>(plan);
+    if (p->dtype != CORO_C64) { set_error("coro_fresnel_plan_set_pass_kernel: complex64 plans only"); return CORO_EINVAL; }
+    if (row_variant < 0 || row_variant >= row_variant_count(p->n)) {
+        set_error("coro_fresnel_plan_set_pass_kernel: row variant %d not offered at n=%d", row_variant, p->n);
+        return CORO_EINVAL;
+    }
+    bool col_ok = col_lines == 0;
+    int cand[4];
+    const int nc = col_candidates(p->n, cand);
+    for (int i = 0; i < nc; ++i) col_ok = col_ok || cand[i] == col_lines;
+    if (!col_ok) {
+        set_error("coro_fresnel_plan_set_pass_kernel: column kernel %d not offered at n=%d", col_lines, p->n);
+        return CORO_EINVAL;
+    }
+    for (Op& op : p->ops) {
+        if (op.row) op.variant = row_variant;
+        else op.lines = col_lines;
+    }
+    return CORO_OK;
+}
+
 extern "C" coro_status coro_plan_launch_count(coro_plan plan, int* out) {
     clear_error();
     if (!plan || !out) { set_error("coro_plan_launch_count: NULL argument"); return CORO_EINVAL; }

@@ -149,10 +149,22 @@ template <bool INV, typename C> __device__ __forceinline__ C twiddle(const C* __
     return w;
 }
 
+// Barrier policies for the exchanges: the whole block, or one named barrier shared by the
+// threads of an independent unit inside the block (ids 1..15; count a multiple of 32).
+struct SyncBlock {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct SyncNamed {
+    int id, count;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+    }
+};
+
 // One Stockham pass with span NS; recursion continues until NS * R == N.
 // buf: this line's shared-memory region, indexed through pad16().
-template <typename C, int N, bool INV, int NS>
-__device__ __forceinline__ void line_fft_pass(C (&v)[16], C* buf, int t, const C* __restrict__ tw) {
+template <typename C, int N, bool INV, int NS, typename Sync>
+__device__ __forceinline__ void line_fft_pass(C (&v)[16], C* buf, int t, const C* __restrict__ tw, const Sync& sync) {
     constexpr int TPL = N / 16;
     constexpr int REM = N / NS;
     constexpr int R = REM >= 16 ? 16 : REM;
@@ -190,7 +202,7 @@ __device__ __forceinline__ void line_fft_pass(C (&v)[16], C* buf, int t, const C
         }
     }
     if constexpr (!LAST) {
-        __syncthreads();
+        sync();
         if constexpr (TPL % 16 == 0) {
             const C* p = buf + pad16(t);
 #pragma unroll
@@ -199,16 +211,16 @@ __device__ __forceinline__ void line_fft_pass(C (&v)[16], C* buf, int t, const C
 #pragma unroll
             for (int s = 0; s < 16; ++s) v[s] = buf[pad16(t + s * TPL)];
         }
-        __syncthreads();
-        line_fft_pass<C, N, INV, NS * R>(v, buf, t, tw);
+        sync();
+        line_fft_pass<C, N, INV, NS * R>(v, buf, t, tw, sync);
     }
 }
 
-// Full N-point DFT of the line held by the calling threads (all threads of the block must
-// call it together: it contains block-wide barriers).
-template <typename C, int N, bool INV>
-__device__ __forceinline__ void line_fft(C (&v)[16], C* buf, int t, const C* __restrict__ tw) {
-    line_fft_pass<C, N, INV, 1>(v, buf, t, tw);
+// Full N-point DFT of the line held by the calling threads (all threads that share the
+// barrier must call it together). Without a policy the barrier is the whole block.
+template <typename C, int N, bool INV, typename Sync = SyncBlock>
+__device__ __forceinline__ void line_fft(C (&v)[16], C* buf, int t, const C* __restrict__ tw, const Sync& sync = Sync{}) {
+    line_fft_pass<C, N, INV, 1>(v, buf, t, tw, sync);
 }
 
 template <int N> struct LineGeom {

@@ -485,6 +485,181 @@ col_pass_persistent_kernel(const __grid_constant__ ColArgs<C> a, const __grid_co
     if (threadIdx.x == 0) tc::bulk_wait<0>();
 }
 
+// ------------------------------------------------------------------------------ unit-pipelined passes
+//
+// One resident block per SM is split into U independent units. A unit transforms one line
+// group (L adjacent columns, or one row) with its own named barrier and its own shared region,
+// which serves as the FFT exchange buffer and then holds the finished group while its
+// asynchronous store drains. Line groups arrive by asynchronous copy into S staging slots
+// (S <= U): the k-th group of the block lands in slot k % S and is taken by unit k % U, which
+// copies it into registers and then issues the copy of group k + S into the slot it just
+// emptied (S divides U). Loads, FFTs and stores of different groups therefore overlap while every thread
+// of the block keeps its 16 samples in registers. Unit u's j-th group completes phase j of
+// mbarrier full[u]. The copy of group k + U is issued only after group k + U - S has been
+// taken, which (stepping back by S, S dividing U) needs group k taken first: so phase j + 1
+// of full[u] cannot complete before unit u has passed phase j, and a parity wait is exact.
+
+template <int N, int L, int U, int S> struct UColCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int UT = TPL * L;                 // threads per unit
+    static constexpr int THREADS = UT * U;
+    static constexpr int GROUP = L * N;                // samples per column group
+    static constexpr int BOXES = N / 256;
+    static constexpr int STRIDE = ColCfg<N, L>::STRIDE;
+    static constexpr int REGION = L * STRIDE;          // exchange buffer; >= GROUP
+    static_assert(S >= 1 && U % S == 0 && U <= 15, "unit layout");
+    template <typename C> static constexpr size_t smem() {
+        return ((size_t)S * GROUP + (size_t)U * REGION) * sizeof(C) + 8 * U;
+    }
+};
+
+template <typename C, int N, int L, int U, int S>
+__global__ void __launch_bounds__(UColCfg<N, L, U, S>::THREADS, 1)
+col_pass_units_kernel(const __grid_constant__ ColArgs<C> a, const __grid_constant__ CUtensorMap map, int groups) {
+    using Cfg = UColCfg<N, L, U, S>;
+    constexpr uint32_t BYTES = Cfg::GROUP * sizeof(C);
+    constexpr int GPI = N / L;                         // groups per item
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    C* stage = reinterpret_cast<C*>(smem_raw);
+    const int u = threadIdx.x / Cfg::UT;
+    const int ut = threadIdx.x % Cfg::UT;
+    const int c = ut % L;
+    const int t = ut / L;
+    C* region = stage + S * Cfg::GROUP + u * Cfg::REGION;
+    uint64_t* full = reinterpret_cast<uint64_t*>(stage + S * Cfg::GROUP + U * Cfg::REGION);
+    C* xl = region + c * Cfg::STRIDE;
+    const SyncNamed sync{1 + u, Cfg::UT};
+    const bool leader = ut == 0;
+
+    // group index k of this block -> slot k % S, consumer unit k % U
+    auto issue_load = [&](int k) {
+        const int g = blockIdx.x + k * gridDim.x;
+        const int x = (g % GPI) * L, y = (g / GPI) * N;
+        C* dst = stage + (k % S) * Cfg::GROUP;
+        uint64_t* bar = &full[k % U];
+        tc::mbar_arrive_expect_tx(bar, BYTES);
+#pragma unroll 1
+        for (int q = 0; q < Cfg::BOXES; ++q) tc::tma_load_2d(dst + q * 256 * L, &map, bar, x, y + q * 256);
+    };
+    const int mine = groups > (int)blockIdx.x ? (groups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < U; ++i) tc::mbar_init(&full[i], 1);
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&map);
+        for (int k = 0; k < S && k < mine; ++k) issue_load(k);
+    }
+    __syncthreads();
+    bool ok = true;
+    int j = 0;
+    for (int k = u; k < mine; k += U, ++j) {
+        const int g = blockIdx.x + k * gridDim.x;
+        const int b = g / GPI, col = (g % GPI) * L + c;
+        const C* src = stage + (k % S) * Cfg::GROUP;
+        if (ok) ok = tc::mbar_wait(&full[u], j & 1, a.err, 7);
+        C v[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) v[s] = src[(t + s * Cfg::TPL) * L + c];
+        if (leader) tc::bulk_wait_read<0>();           // this unit's previous store has left its region
+        sync();                                        // slot emptied by the whole unit; region free
+        if (leader && k + S < mine) issue_load(k + S);
+        if (a.flags & CF_FWD) line_fft<C, N, false>(v, xl, t, a.tw, sync);
+        if (a.flags & CF_TABLE) {
+            const C hx = a.tab_x[(size_t)b * N + col];
+            const C* ty = a.tab_y + (size_t)b * N;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], cmul(hx, ty[t + s * Cfg::TPL]));
+        }
+        if (a.flags & CF_INV) line_fft<C, N, true>(v, xl, t, a.tw, sync);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) region[(t + s * Cfg::TPL) * L + c] = v[s];
+        tc::fence_proxy_async();
+        sync();
+        if (leader) {
+            const int x = (g % GPI) * L, y = b * N;
+#pragma unroll 1
+            for (int q = 0; q < Cfg::BOXES; ++q) tc::tma_store_2d(&map, region + q * 256 * L, x, y + q * 256);
+            tc::bulk_commit();
+        }
+    }
+    if (leader) tc::bulk_wait<0>();
+}
+
+template <int N, int U, int S> struct URowCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int UT = TPL;                     // one row per unit
+    static constexpr int THREADS = UT * U;
+    static constexpr int STRIDE = LineGeom<N>::STRIDE; // exchange buffer; >= N
+    static_assert(S >= 1 && U % S == 0 && U <= 15, "unit layout");
+    template <typename C> static constexpr size_t smem() {
+        return ((size_t)S * N + (size_t)U * STRIDE) * sizeof(C) + 8 * U;
+    }
+};
+
+template <typename C, int N, int U, int S>
+__global__ void __launch_bounds__(URowCfg<N, U, S>::THREADS, 1)
+row_pass_units_kernel(const __grid_constant__ RowArgs<C> a, int rows) {
+    using Cfg = URowCfg<N, U, S>;
+    constexpr uint32_t BYTES = N * sizeof(C);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    C* stage = reinterpret_cast<C*>(smem_raw);
+    const int u = threadIdx.x / Cfg::UT;
+    const int t = threadIdx.x % Cfg::UT;
+    C* region = stage + S * N + u * Cfg::STRIDE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(stage + S * N + U * Cfg::STRIDE);
+    const SyncNamed sync{1 + u, Cfg::UT};
+    const bool leader = t == 0;
+    const bool load = !(a.flags & RF_INIT_ONE);
+
+    auto issue_load = [&](int k) {
+        const int g = blockIdx.x + k * gridDim.x;
+        uint64_t* bar = &full[k % U];
+        tc::mbar_arrive_expect_tx(bar, BYTES);
+        tc::bulk_load(stage + (k % S) * N, a.in + (size_t)g * N, BYTES, bar);
+    };
+    const int mine = rows > (int)blockIdx.x ? (rows - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < U; ++i) tc::mbar_init(&full[i], 1);
+        tc::fence_mbar_init();
+        if (load)
+            for (int k = 0; k < S && k < mine; ++k) issue_load(k);
+    }
+    __syncthreads();
+    bool ok = true;
+    int j = 0;
+    for (int k = u; k < mine; k += U, ++j) {
+        const int g = blockIdx.x + k * gridDim.x;      // global row index over the batch
+        const int b = g / N, y = g % N;
+        C v[16];
+        if (load) {
+            const C* src = stage + (k % S) * N;
+            if (ok) ok = tc::mbar_wait(&full[u], j & 1, a.err, 8);
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = src[t + s * Cfg::TPL];
+        } else {
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = mk<C>(1, 0);
+        }
+        if (leader) tc::bulk_wait_read<0>();           // this unit's previous store has left its region
+        sync();
+        if (load && leader && k + S < mine) issue_load(k + S);
+        if (a.flags & RF_INV_FIRST) line_fft<C, N, true>(v, region, t, a.tw, sync);
+        if (a.elems.count) {
+            float none[16];
+            apply_elems<C, N, Cfg::TPL>(v, t, y, b, a.elems, none, -1);
+        }
+        if (a.flags & RF_FWD_AFTER) line_fft<C, N, false>(v, region, t, a.tw, sync);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) region[t + s * Cfg::TPL] = v[s];
+        tc::fence_proxy_async();
+        sync();
+        if (leader) {
+            tc::bulk_store(a.out + (size_t)g * N, region, BYTES);
+            tc::bulk_commit();
+        }
+    }
+    if (leader) tc::bulk_wait<0>();
+}
+
 // ------------------------------------------------------------------------------ launchers
 
 struct PassLaunch {

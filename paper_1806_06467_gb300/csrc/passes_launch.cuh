@@ -98,5 +98,46 @@ cudaError_t col_launch(const ColArgs<C>& a, const PassLaunch& l) {
     return cudaGetLastError();
 }
 
+// Unit-pipelined passes: one block per SM (as many SMs as there are groups).
+inline cudaError_t sm_count(int* sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+    return e;
+}
+
+template <typename C, int N, int L, int U, int S>
+cudaError_t col_launch_units(const ColArgs<C>& a, const PassLaunch& l) {
+    using Cfg = UColCfg<N, L, U, S>;
+    static unsigned done = 0;
+    const size_t smem = Cfg::template smem<C>();
+    cudaError_t e = ensure_smem(col_pass_units_kernel<C, N, L, U, S>, smem, done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = sm_count(&sms)) != cudaSuccess) return e;
+    if (a.in != a.out) return cudaErrorInvalidValue;   // one tensor map serves loads and stores
+    CUtensorMap map;
+    if ((e = tc_make_field_map(a.in, N, (long long)l.batch * N, L, &map)) != cudaSuccess) return e;
+    const int groups = l.batch * N / L;
+    const int grid = groups < sms ? groups : sms;
+    col_pass_units_kernel<C, N, L, U, S><<<grid, Cfg::THREADS, smem, l.stream>>>(a, map, groups);
+    return cudaGetLastError();
+}
+
+template <typename C, int N, int U, int S>
+cudaError_t row_launch_units(const RowArgs<C>& a, const PassLaunch& l) {
+    using Cfg = URowCfg<N, U, S>;
+    static unsigned done = 0;
+    const size_t smem = Cfg::template smem<C>();
+    cudaError_t e = ensure_smem(row_pass_units_kernel<C, N, U, S>, smem, done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = sm_count(&sms)) != cudaSuccess) return e;
+    const int rows = l.batch * N;
+    const int grid = rows < sms ? rows : sms;
+    row_pass_units_kernel<C, N, U, S><<<grid, Cfg::THREADS, smem, l.stream>>>(a, rows);
+    return cudaGetLastError();
+}
+
 }  // namespace detail
 }  // namespace coro
