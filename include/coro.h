@@ -194,19 +194,27 @@ coro_status coro_fresnel_plan_execute_range(coro_plan plan, void* field, int fir
  * traffic of the launch (field read unless generated, field write, OPD/amplitude maps read). */
 coro_status coro_fresnel_plan_pass_info(coro_plan plan, int i, int* is_row, double* bytes);
 /* Kernel that pass i launches, as chosen when the plan was built (the complex64 plan times
- * its candidates then unless the environment sets CORO_AUTOTUNE=0). *persistent: 0 = one
- * block per group of lines; 1 = persistent kernel (one block per SM slot, line groups staged
- * through shared memory by bulk or TMA copies while the previous group is transformed);
- * 2 = unit-pipelined persistent kernel (one block per SM split into independent units with
- * their own barriers, sharing staged line groups). *lines = columns per group for a column
- * pass, 0 for a row pass. Either output pointer may be NULL. Plain host query; no device work. */
+ * its candidates then unless the environment sets CORO_AUTOTUNE=0). *persistent:
+ *   0  one block per group of lines;
+ *   1  persistent kernel: one block per SM slot, line groups staged through shared memory
+ *      by bulk or TMA copies while the previous group is transformed;
+ *   2  unit-pipelined persistent kernel: one block per SM split into independent units
+ *      with their own barriers, sharing staged line groups;
+ *   3  as 2, each unit transforming two lines (columns, or rows) at once in packed FP32x2
+ *      arithmetic;
+ *   4  wide kernel: four-column groups (32-byte row segments) staged by TMA, packed FP32x2
+ *      arithmetic, half-size exchange buffers, results stored from registers.
+ * *lines = columns per group for a column pass, 0 for a row pass. Either output pointer may
+ * be NULL. Plain host query; no device work. */
 coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent, int* lines);
-/* Override the tuned kernel choice of every pass of a complex64 plan: row_variant 0 =
- * persistent, 1 = one block per line group, 2 = unit-pipelined (N = 2048, 4096); col_lines
- * = columns per block (a width the plan's N supports), -1 = persistent TMA kernel, -2 =
- * unit-pipelined (N = 1024 ... 4096), 0 = default. Values the plan's N does not offer are
- * rejected with CORO_EINVAL and nothing changes. Results are identical up to FP32 rounding
- * order for every choice (used to test each kernel). */
+/* Override the tuned kernel choice of every pass of a complex64 plan.
+ *   row_variant: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row
+ *                pairs (2 and 3: N = 1024 ... 4096).
+ *   col_lines:   columns per block (a width the plan's N supports), -1 persistent TMA,
+ *                -2 unit-pipelined, -3 packed column pairs, -4 wide (-2 to -4: N = 1024 ...
+ *                4096), 0 default.
+ * Values the plan's N does not offer are rejected with CORO_EINVAL and nothing changes.
+ * Every choice gives the same result up to FP32 rounding order (used to test each kernel). */
 coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, int col_lines);
 coro_status coro_plan_destroy(coro_plan plan);
 

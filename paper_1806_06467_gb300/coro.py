@@ -454,12 +454,14 @@ class FresnelPlan:
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_kernel(self.handle, i, ct.byref(p), ct.byref(w)))
         row, _ = self.pass_info(i)
         kind = "row_pass" if row else "col_pass"
-        name = kind + ("_kernel", "_persistent", "_units")[p.value]
+        name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide")[p.value]
         return f"{name}<{self.n}>" if row else f"{name}<{self.n},{w.value}>"
 
     def set_pass_kernel(self, row_variant: int, col_lines: int) -> None:
-        """Override the tuned kernels (row: 0 persistent, 1 per-group, 2 units; column:
-        lines per block, -1 persistent TMA, -2 units, 0 default)."""
+        """Override the tuned kernels (row: 0 persistent, 1 per-group, 2 units, 3 packed row
+        pairs; column:
+        lines per block, -1 persistent TMA, -2 units, -3 packed column pairs, -4 wide
+        four-column groups, 0 default)."""
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_set_pass_kernel(self.handle, row_variant, col_lines))
 
     @property

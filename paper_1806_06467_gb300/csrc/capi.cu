@@ -687,7 +687,7 @@ float time_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, void*
 
 coro_status autotune_ops(coro_ctx ctx, int dtype, int n, int batch, std::vector<Op>& ops, std::vector<std::string>* log) {
     if (dtype != CORO_C64 || !autotune_enabled()) return CORO_OK;
-    int cand[4];
+    int cand[8];
     const int nc = col_candidates(n, cand), nr = row_variant_count(n);
     if (nc < 2 && nr < 2) return CORO_OK;
     coro_status st = CORO_OK;
@@ -908,7 +908,7 @@ extern "C" coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row
         return CORO_EINVAL;
     }
     bool col_ok = col_lines == 0;
-    int cand[4];
+    int cand[8];
     const int nc = col_candidates(p->n, cand);
     for (int i = 0; i < nc; ++i) col_ok = col_ok || cand[i] == col_lines;
     if (!col_ok) {

@@ -50,6 +50,7 @@ struct DeviceGuard {
 // Twiddle table for n (built lazily on the context's stream).
 const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st);
 
+
 // Stream-ordered copy of a host array into a fresh device block (freed with free_async).
 void* upload_async(coro_ctx ctx, const void* host, size_t bytes, coro_status* st);
 void free_async(coro_ctx ctx, void* p);

@@ -7,7 +7,9 @@
 // The fftshift of the centred DFT is folded in as a (-1)^(x+y) sign flip (Sec. 2.4: the paper
 // moved fftshift to the GPU; here it costs no memory pass at all).
 #pragma once
+#include <type_traits>
 #include "fft_engine.cuh"
+#include "fft_pair.cuh"
 #include "tc_ptx.cuh"
 
 namespace coro {
@@ -49,6 +51,20 @@ struct PassElems {
     int count;
     DevElem e[kMaxPassElems];
 };
+
+// exp(i pi ph) for a phase ph in half-cycles. Complex64 passes reduce ph exactly to
+// r = ph - 2 rint(ph / 2) in [-1, 1] (Sterbenz: ph and the even integer are within 1) and
+// take the hardware sine and cosine of pi r, whose absolute error on [-pi, pi] is below
+// 2^-21.4 -- far inside the FP32 field tolerance, at a fraction of the cost of sincospif.
+// Complex128 passes keep sincospif.
+template <typename C> __device__ __forceinline__ void phasor_hc(float ph, float& sn, float& cs) {
+    if constexpr (std::is_same<C, float2>::value) {
+        const float r = ph - 2.f * rintf(0.5f * ph);
+        __sincosf(3.14159265358979323846f * r, &sn, &cs);
+    } else {
+        sincospif(ph, &sn, &cs);
+    }
+}
 
 // Multiply the 16 samples a thread holds (row y of item b, columns x0 + s*XS) by every
 // element of the list. The element loop is outermost and uniform across the block.
@@ -102,7 +118,7 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                     // phase / pi = (2 / lambda) * OPD
                     const float ph = k * (i == pre_idx ? pre[s] : __ldg(e.map + off + s * XS));
                     float sn, cs;
-                    sincospif(ph, &sn, &cs);
+                    phasor_hc<C>(ph, sn, cs);
                     R am = 1;
                     if (e.amp) am = (R)__ldg(e.amp + off + s * XS);
                     v[s] = cmul(v[s], mk<C>(am * (R)cs, am * (R)sn));
@@ -142,7 +158,7 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
                     float sn, cs;
-                    sincospif(ph[s], &sn, &cs);
+                    phasor_hc<C>(ph[s], sn, cs);
                     v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
                 }
                 break;
@@ -158,7 +174,7 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                     a -= rintf(a);
                     a += (float)kk * p[2];
                     float sn, cs;
-                    sincospif(p[0] * sinpif(2.f * a), &sn, &cs);
+                    phasor_hc<C>(p[0] * sinpif(2.f * a), sn, cs);
                     v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
                 }
                 break;
@@ -173,6 +189,163 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
 #pragma unroll
                 for (int s = 0; s < 16; ++s)
                     if ((x0 + s * XS + y) & 1) v[s] = mk<C>(-v[s].x, -v[s].y);
+                break;
+            }
+            default:
+                break;
+        }
+    }
+}
+
+// Elements on a packed row pair: the samples a thread holds for rows ya (lane 0) and ya + 1
+// (lane 1) of item b, columns x0 + s*XS, as packed pairs (complex64 only). Per element and
+// sample, the two rows' factors are evaluated as in apply_elems and applied with packed
+// arithmetic, which keeps the register footprint of one sample pair.
+template <int N, int XS>
+__device__ __forceinline__ void apply_elems_pair(pk::CP (&v)[16], int x0, int ya, int b, const PassElems& pe) {
+    using pk::CP;
+    using pk::u64;
+    const int kya = ya - N / 2, kyb = kya + 1;
+    auto mask = [&](int s, bool pa, bool pb) {
+        const u64 m = pk::pack(pa ? 1.f : 0.f, pb ? 1.f : 0.f);
+        v[s] = CP{pk::mul2(v[s].re, m), pk::mul2(v[s].im, m)};
+    };
+    // v[s] *= (fr_a + i fi_a, fr_b + i fi_b)
+    auto mulf = [&](int s, u64 fr, u64 fi) {
+        v[s] = CP{pk::sub2(pk::mul2(v[s].re, fr), pk::mul2(v[s].im, fi)), pk::fma2(v[s].re, fi, pk::mul2(v[s].im, fr))};
+    };
+    for (int i = 0; i < pe.count; ++i) {
+        const DevElem& e = pe.e[i];
+        switch (e.kind) {
+            case DK_APERTURE: {
+                const int* th = e.ithr + 4 * b;
+                const int t0 = th[0], t1 = th[1], t2 = th[2];
+                auto pass = [&](int kx, int ky) {
+                    const int r2 = kx * kx + ky * ky;
+                    bool p = r2 <= t0;
+                    if (t1 >= 0 && r2 <= t1) p = false;
+                    if (t2 >= 0 && (abs(kx) <= t2 || abs(ky) <= t2)) p = false;
+                    return p;
+                };
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int kx = x0 + s * XS - N / 2;
+                    mask(s, pass(kx, kya), pass(kx, kyb));
+                }
+                break;
+            }
+            case DK_CIRCLE: {
+                const int t0 = e.ithr[4 * b];
+                const bool opaque_inside = e.flags & 1;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int kx = x0 + s * XS - N / 2;
+                    mask(s, (kx * kx + kya * kya <= t0) != opaque_inside, (kx * kx + kyb * kyb <= t0) != opaque_inside);
+                }
+                break;
+            }
+            case DK_TABLE: {
+                const float2* t = reinterpret_cast<const float2*>(e.tab) + (size_t)b * N;
+                const float2 ta = t[ya], tb = t[ya + 1];
+                const u64 tyr = pk::pack(ta.x, tb.x), tyi = pk::pack(ta.y, tb.y), ntyi = pk::pack(-ta.y, -tb.y);
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const float2 tx = __ldg(t + x0 + s * XS);
+                    const u64 txr = pk::pack(tx.x, tx.x), txi = pk::pack(tx.y, tx.y);
+                    mulf(s, pk::fma2(txr, tyr, pk::mul2(txi, ntyi)), pk::fma2(txr, tyi, pk::mul2(txi, tyr)));
+                }
+                break;
+            }
+            case DK_OPD_MAP: {
+                const float k = e.fpar[4 * b];
+                const size_t off = (size_t)b * e.map_bstride + (size_t)ya * N + x0;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    float sa, ca, sb, cb;
+                    phasor_hc<float2>(k * __ldg(e.map + off + s * XS), sa, ca);
+                    phasor_hc<float2>(k * __ldg(e.map + off + N + s * XS), sb, cb);
+                    if (e.amp) {
+                        const float aa = __ldg(e.amp + off + s * XS), ab = __ldg(e.amp + off + N + s * XS);
+                        sa *= aa; ca *= aa; sb *= ab; cb *= ab;
+                    }
+                    mulf(s, pk::pack(ca, cb), pk::pack(sa, sb));
+                }
+                break;
+            }
+            case DK_ZERNIKE: {
+                const int t0 = e.ithr[4 * b];
+                const float k = e.fpar[4 * b], sc = e.fpar[4 * b + 1];
+                // one row at a time, through the one-line evaluator's rolled polynomial loop
+#pragma unroll 1
+                for (int lane = 0; lane < 2; ++lane) {
+                    const int ky = lane ? kyb : kya;
+                    const float zy = ky * sc;
+                    float ph[16];
+#pragma unroll 1
+                    for (int s = 0; s < 16; ++s) {
+                        const int kx = x0 + s * XS - N / 2;
+                        float opd = 0.f;
+                        if (kx * kx + ky * ky <= t0) {
+                            const float zx = kx * sc;
+                            const float rho2 = zx * zx + zy * zy;
+                            float pr = 1.f, pim = 0.f;
+#pragma unroll 1
+                            for (int m = 0; m < ZM; ++m) {
+                                const float* A = e.zpoly + m * ZD;
+                                const float* Bc = e.zpoly + ZM * ZD + m * ZD;
+                                float a = A[ZD - 1], bb = Bc[ZD - 1];
+#pragma unroll
+                                for (int d = ZD - 2; d >= 0; --d) { a = fmaf(a, rho2, A[d]); bb = fmaf(bb, rho2, Bc[d]); }
+                                opd += a * pr + bb * pim;
+                                const float nr = pr * zx - pim * zy;
+                                pim = pr * zy + pim * zx;
+                                pr = nr;
+                            }
+                        }
+                        ph[s] = k * opd;
+                    }
+#pragma unroll
+                    for (int s = 0; s < 16; ++s) {
+                        float sn, cs;
+                        phasor_hc<float2>(ph[s], sn, cs);
+                        mulf(s, lane ? pk::pack(1.f, cs) : pk::pack(cs, 1.f), lane ? pk::pack(0.f, sn) : pk::pack(sn, 0.f));
+                    }
+                }
+                break;
+            }
+            case DK_SINE: {
+                const float* p = e.fpar + 4 * b;
+                const bool along_y = e.flags & 1;
+                auto phase = [&](int kk) {
+                    float a = (float)kk * p[1];
+                    a -= rintf(a);
+                    a += (float)kk * p[2];
+                    return p[0] * sinpif(2.f * a);
+                };
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int kx = x0 + s * XS - N / 2;
+                    float sa, ca, sb, cb;
+                    phasor_hc<float2>(phase(along_y ? kya : kx), sa, ca);
+                    if (along_y) phasor_hc<float2>(phase(kyb), sb, cb);
+                    else { sb = sa; cb = ca; }
+                    mulf(s, pk::pack(ca, cb), pk::pack(sa, sb));
+                }
+                break;
+            }
+            case DK_SCALAR: {
+                const u64 sc = pk::pack(e.fpar[4 * b], e.fpar[4 * b]);
+#pragma unroll
+                for (int s = 0; s < 16; ++s) v[s] = CP{pk::mul2(v[s].re, sc), pk::mul2(v[s].im, sc)};
+                break;
+            }
+            case DK_CHECKER: {
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const float sa = ((x0 + s * XS + ya) & 1) ? -1.f : 1.f;
+                    const u64 m = pk::pack(sa, -sa);        // rows ya and ya + 1 have opposite parity
+                    v[s] = CP{pk::mul2(v[s].re, m), pk::mul2(v[s].im, m)};
+                }
                 break;
             }
             default:
@@ -584,6 +757,206 @@ col_pass_units_kernel(const __grid_constant__ ColArgs<C> a, const __grid_constan
     if (leader) tc::bulk_wait<0>();
 }
 
+// Column pass on packed line pairs: a unit of N/16 threads transforms two adjacent columns
+// at once, lane 0 / lane 1 of every FP32x2 register holding column A / B (fft_pair.cuh);
+// otherwise the unit pipeline of col_pass_units_kernel with L = 2. hx (per column) commutes with the column transforms and is applied after the
+// inverse FFT; hy (per row) sits between the two FFTs.
+template <int N, int U, int S> struct PColPairCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int UT = TPL;                     // threads per unit (one column pair)
+    static constexpr int THREADS = UT * U;
+    static constexpr int GROUP = 2 * N;                // float2 samples per pair
+    static constexpr int BOXES = N / 256;
+    static constexpr int REGION = 2 * LineGeom<N>::STRIDE;   // float2 units; 16-byte pair entries
+    static_assert(S >= 1 && U % S == 0 && U <= 15, "unit layout");
+    template <typename C> static constexpr size_t smem() {
+        return ((size_t)S * GROUP + (size_t)U * REGION) * sizeof(C) + 8 * U;
+    }
+};
+
+template <int N, int U, int S>
+__global__ void __launch_bounds__(PColPairCfg<N, U, S>::THREADS, 1)
+col_pass_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_constant__ CUtensorMap map, int groups) {
+    using Cfg = PColPairCfg<N, U, S>;
+    using pk::CP;
+    constexpr uint32_t BYTES = Cfg::GROUP * sizeof(float2);
+    constexpr int GPI = N / 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    const int u = threadIdx.x / Cfg::UT;
+    const int t = threadIdx.x % Cfg::UT;
+    float2* region = stage + S * Cfg::GROUP + u * Cfg::REGION;
+    CP* xl = reinterpret_cast<CP*>(region);
+    uint64_t* full = reinterpret_cast<uint64_t*>(stage + S * Cfg::GROUP + U * Cfg::REGION);
+    const SyncNamed sync{1 + u, Cfg::UT};
+    const bool leader = t == 0;
+    const float2* tw = a.tw;
+
+    auto issue_load = [&](int k) {
+        const int g = blockIdx.x + k * gridDim.x;
+        const int x = (g % GPI) * 2, y = (g / GPI) * N;
+        float2* dst = stage + (k % S) * Cfg::GROUP;
+        uint64_t* bar = &full[k % U];
+        tc::mbar_arrive_expect_tx(bar, BYTES);
+#pragma unroll 1
+        for (int q = 0; q < Cfg::BOXES; ++q) tc::tma_load_2d(dst + q * 512, &map, bar, x, y + q * 256);
+    };
+    const int mine = groups > (int)blockIdx.x ? (groups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < U; ++i) tc::mbar_init(&full[i], 1);
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&map);
+        for (int k = 0; k < S && k < mine; ++k) issue_load(k);
+    }
+    __syncthreads();
+    bool ok = true;
+    int j = 0;
+    for (int k = u; k < mine; k += U, ++j) {
+        const int g = blockIdx.x + k * gridDim.x;
+        const int b = g / GPI, col = (g % GPI) * 2;
+        const float4* src = reinterpret_cast<const float4*>(stage + (k % S) * Cfg::GROUP);
+        if (ok) ok = tc::mbar_wait(&full[u], j & 1, a.err, 9);
+        CP v[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const float4 q = src[t + s * Cfg::TPL];       // row t + s*TPL: (re_A, im_A, re_B, im_B)
+            v[s] = CP{pk::pack(q.x, q.z), pk::pack(q.y, q.w)};
+        }
+        if (leader) tc::bulk_wait_read<0>();
+        sync();
+        if (leader && k + S < mine) issue_load(k + S);
+        if (a.flags & CF_FWD) pk::line_fft2<N, false>(v, xl, t, tw, sync);
+        if (a.flags & CF_TABLE) {
+            const float2* ty = a.tab_y + (size_t)b * N;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const float2 h = ty[t + s * Cfg::TPL];
+                v[s] = pk::cmul_b<false>(v[s], pk::pack(h.x, h.x), pk::pack(h.y, h.y));
+            }
+        }
+        if (a.flags & CF_INV) pk::line_fft2<N, true>(v, xl, t, tw, sync);
+        if (a.flags & CF_TABLE) {
+            const float2 ha = a.tab_x[(size_t)b * N + col], hb = a.tab_x[(size_t)b * N + col + 1];
+            const pk::u64 hr = pk::pack(ha.x, hb.x), hi = pk::pack(ha.y, hb.y);
+#pragma unroll
+            for (int s = 0; s < 16; ++s)
+                v[s] = CP{pk::sub2(pk::mul2(v[s].re, hr), pk::mul2(v[s].im, hi)),
+                          pk::fma2(v[s].re, hi, pk::mul2(v[s].im, hr))};
+        }
+        float4* out = reinterpret_cast<float4*>(region);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            float4 q;
+            pk::unpack(v[s].re, q.x, q.z);
+            pk::unpack(v[s].im, q.y, q.w);
+            out[t + s * Cfg::TPL] = q;
+        }
+        tc::fence_proxy_async();
+        sync();
+        if (leader) {
+            const int x = col, y = b * N;
+#pragma unroll 1
+            for (int q = 0; q < Cfg::BOXES; ++q) tc::tma_store_2d(&map, region + q * 512, x, y + q * 256);
+            tc::bulk_commit();
+        }
+    }
+    if (leader) tc::bulk_wait<0>();
+}
+
+// Wide column pass: four adjacent columns per group, so that every row segment read or
+// written is one full 32-byte sector (two-column strips reach about half the copy bandwidth
+// of four-column ones). One resident block per SM of two pair-units (N/16 threads each,
+// packed FP32x2, fft_pair.cuh); thread (t, p) = 2t + p holds column pair p of the group, so
+// a warp covers 16 rows x 4 columns. The next group arrives by TMA (boxes of 4 x 256) in a
+// 128-KB staging buffer while the current one is transformed in registers; the FFT
+// exchanges use half-size buffers (two rounds), which is what leaves room for the staging
+// buffer; results leave straight from registers (16-byte stores, 32 bytes per row per warp).
+template <int N> struct WColCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int THREADS = 2 * TPL;
+    static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;   // 512 threads/SM at <= 128 regs
+    static constexpr int GROUP = 4 * N;                 // float2 samples per group
+    static constexpr int BOXES = N / 256;
+    // CP entries per pair (half buffer); XHALF = 4 (mod 8) puts pair 1's buffer 64 bytes
+    // of bank space away from pair 0's, as lanes 2t and 2t + 1 touch the same position of each
+    static constexpr int XHALF = N / 2 + N / 32 + 4;
+    static constexpr size_t smem() { return (size_t)GROUP * 8 + 2 * (size_t)XHALF * 16 + 16; }
+};
+
+template <int N>
+__global__ void __launch_bounds__(WColCfg<N>::THREADS, WColCfg<N>::MINB)
+col_pass_wide_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_constant__ CUtensorMap map, int groups) {
+    using Cfg = WColCfg<N>;
+    using pk::CP;
+    constexpr uint32_t BYTES = Cfg::GROUP * sizeof(float2);
+    constexpr int GPI = N / 4;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    const int p = threadIdx.x & 1;
+    const int t = threadIdx.x >> 1;
+    CP* xl = reinterpret_cast<CP*>(stage + Cfg::GROUP) + p * Cfg::XHALF;
+    uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<CP*>(stage + Cfg::GROUP) + 2 * Cfg::XHALF);
+    const float2* tw = a.tw;
+    const SyncBlock sync{};
+
+    auto issue_load = [&](int k) {
+        const int g = blockIdx.x + k * gridDim.x;
+        const int x = (g % GPI) * 4, y = (g / GPI) * N;
+        tc::mbar_arrive_expect_tx(full, BYTES);
+#pragma unroll 1
+        for (int q = 0; q < Cfg::BOXES; ++q) tc::tma_load_2d(stage + q * 1024, &map, full, x, y + q * 256);
+    };
+    const int mine = groups > (int)blockIdx.x ? (groups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(full, 1);
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&map);
+        if (mine > 0) issue_load(0);
+    }
+    __syncthreads();
+    bool ok = true;
+    for (int k = 0; k < mine; ++k) {
+        const int g = blockIdx.x + k * gridDim.x;
+        const int b = g / GPI, col = (g % GPI) * 4 + 2 * p;
+        if (ok) ok = tc::mbar_wait(full, k & 1, a.err, 10);
+        const float4* src = reinterpret_cast<const float4*>(stage);
+        CP v[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const float4 q = src[(t + s * Cfg::TPL) * 2 + p];   // (re_A, im_A, re_B, im_B)
+            v[s] = CP{pk::pack(q.x, q.z), pk::pack(q.y, q.w)};
+        }
+        __syncthreads();                                    // staging emptied by every thread
+        if (threadIdx.x == 0 && k + 1 < mine) issue_load(k + 1);
+        if (a.flags & CF_FWD) pk::line_fft2<N, false, true>(v, xl, t, tw, sync);
+        if (a.flags & CF_TABLE) {
+            const float2* ty = a.tab_y + (size_t)b * N;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const float2 h = ty[t + s * Cfg::TPL];
+                v[s] = pk::cmul_b<false>(v[s], pk::pack(h.x, h.x), pk::pack(h.y, h.y));
+            }
+        }
+        if (a.flags & CF_INV) pk::line_fft2<N, true, true>(v, xl, t, tw, sync);
+        if (a.flags & CF_TABLE) {
+            const float2 ha = a.tab_x[(size_t)b * N + col], hb = a.tab_x[(size_t)b * N + col + 1];
+            const pk::u64 hr = pk::pack(ha.x, hb.x), hi = pk::pack(ha.y, hb.y);
+#pragma unroll
+            for (int s = 0; s < 16; ++s)
+                v[s] = CP{pk::sub2(pk::mul2(v[s].re, hr), pk::mul2(v[s].im, hi)),
+                          pk::fma2(v[s].re, hi, pk::mul2(v[s].im, hr))};
+        }
+        float2* out = a.out + (size_t)b * N * N + col;
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            float4 q;
+            pk::unpack(v[s].re, q.x, q.z);
+            pk::unpack(v[s].im, q.y, q.w);
+            *reinterpret_cast<float4*>(out + (size_t)(t + s * Cfg::TPL) * N) = q;
+        }
+    }
+}
+
 template <int N, int U, int S> struct URowCfg {
     static constexpr int TPL = LineGeom<N>::TPL;
     static constexpr int UT = TPL;                     // one row per unit
@@ -660,6 +1033,96 @@ row_pass_units_kernel(const __grid_constant__ RowArgs<C> a, int rows) {
     if (leader) tc::bulk_wait<0>();
 }
 
+// Row pass on packed row pairs: a unit of N/16 threads transforms rows 2m and 2m + 1 (one
+// contiguous bulk copy) at once, lane 0 / lane 1 of every FP32x2 register holding row A / B
+// (fft_pair.cuh). Elements are applied per row on the unpacked lanes. Otherwise the unit
+// pipeline of row_pass_units_kernel: S staging slots of two rows, U units, each with its own
+// named barrier and a shared region that is the exchange buffer and then holds the finished
+// pair while its bulk store drains.
+template <int N, int U, int S> struct PRowPairCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int UT = TPL;
+    static constexpr int THREADS = UT * U;
+    static constexpr int GROUP = 2 * N;                // float2 samples per row pair
+    static constexpr int REGION = 2 * LineGeom<N>::STRIDE;   // float2 units (16-byte pair entries)
+    static_assert(S >= 1 && U % S == 0 && U <= 15, "unit layout");
+    static constexpr size_t smem() { return ((size_t)S * GROUP + (size_t)U * REGION) * 8 + 8 * U; }
+};
+
+template <int N, int U, int S>
+__global__ void __launch_bounds__(PRowPairCfg<N, U, S>::THREADS, 1)
+row_pass_pair_kernel(const __grid_constant__ RowArgs<float2> a, int pairs) {
+    using Cfg = PRowPairCfg<N, U, S>;
+    using pk::CP;
+    constexpr uint32_t BYTES = Cfg::GROUP * sizeof(float2);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    const int u = threadIdx.x / Cfg::UT;
+    const int t = threadIdx.x % Cfg::UT;
+    float2* region = stage + S * Cfg::GROUP + u * Cfg::REGION;
+    CP* xl = reinterpret_cast<CP*>(region);
+    uint64_t* full = reinterpret_cast<uint64_t*>(stage + S * Cfg::GROUP + U * Cfg::REGION);
+    const SyncNamed sync{1 + u, Cfg::UT};
+    const bool leader = t == 0;
+    const bool load = !(a.flags & RF_INIT_ONE);
+
+    auto issue_load = [&](int k) {
+        const int g = blockIdx.x + k * gridDim.x;
+        uint64_t* bar = &full[k % U];
+        tc::mbar_arrive_expect_tx(bar, BYTES);
+        tc::bulk_load(stage + (k % S) * Cfg::GROUP, a.in + (size_t)g * Cfg::GROUP, BYTES, bar);
+    };
+    const int mine = pairs > (int)blockIdx.x ? (pairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < U; ++i) tc::mbar_init(&full[i], 1);
+        tc::fence_mbar_init();
+        if (load)
+            for (int k = 0; k < S && k < mine; ++k) issue_load(k);
+    }
+    __syncthreads();
+    bool ok = true;
+    int j = 0;
+    for (int k = u; k < mine; k += U, ++j) {
+        const int g = blockIdx.x + k * gridDim.x;       // row pair index over the batch
+        const int b = (2 * g) / N, ya = (2 * g) % N;
+        CP v[16];
+        if (load) {
+            const float2* src = stage + (k % S) * Cfg::GROUP;
+            if (ok) ok = tc::mbar_wait(&full[u], j & 1, a.err, 11);
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const float2 qa = src[t + s * Cfg::TPL], qb = src[N + t + s * Cfg::TPL];
+                v[s] = CP{pk::pack(qa.x, qb.x), pk::pack(qa.y, qb.y)};
+            }
+        } else {
+            const pk::u64 one = pk::pack(1.f, 1.f);
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = CP{one, 0ull};
+        }
+        if (leader) tc::bulk_wait_read<0>();            // this unit's previous store has left its region
+        sync();
+        if (load && leader && k + S < mine) issue_load(k + S);
+        if (a.flags & RF_INV_FIRST) pk::line_fft2<N, true>(v, xl, t, a.tw, sync);
+        if (a.elems.count) apply_elems_pair<N, Cfg::TPL>(v, t, ya, b, a.elems);
+        if (a.flags & RF_FWD_AFTER) pk::line_fft2<N, false>(v, xl, t, a.tw, sync);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            float2 qa, qb;
+            pk::unpack(v[s].re, qa.x, qb.x);
+            pk::unpack(v[s].im, qa.y, qb.y);
+            region[t + s * Cfg::TPL] = qa;
+            region[N + t + s * Cfg::TPL] = qb;
+        }
+        tc::fence_proxy_async();
+        sync();
+        if (leader) {
+            tc::bulk_store(a.out + (size_t)g * Cfg::GROUP, region, BYTES);
+            tc::bulk_commit();
+        }
+    }
+    if (leader) tc::bulk_wait<0>();
+}
+
 // ------------------------------------------------------------------------------ launchers
 
 struct PassLaunch {
@@ -675,7 +1138,8 @@ template <typename C>
 cudaError_t launch_col_pass(int n, int lines, const ColArgs<C>& a, const PassLaunch& l);
 // Column widths per block for n (0 picks the default); -1 selects the persistent TMA kernel.
 int col_lines_default(int n, bool dbl);
-// Candidate column variants and row variants the plan autotuner times for n (complex64).
+// Candidate column variants (at most 8) and row variants the plan autotuner times for n
+// (complex64).
 int col_candidates(int n, int* out);
 int row_variant_count(int n);
 // The kernel a pass with these settings launches: persistent (1) or not, and its lines.

@@ -12,11 +12,16 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
         case 128: return row_launch<float2, 128>(a, l);
         case 256: return row_launch<float2, 256>(a, l);
         case 512: return row_launch<float2, 512>(a, l);
-        case 1024: return l.variant == 1 ? row_launch<float2, 1024>(a, l) : row_launch_persistent<float2, 1024>(a, l);
+        case 1024:
+            if (l.variant == 3) return row_launch_pair<1024, 8, 4>(a, l);
+            if (l.variant == 2) return row_launch_units<float2, 1024, 8, 4>(a, l);
+            return l.variant == 1 ? row_launch<float2, 1024>(a, l) : row_launch_persistent<float2, 1024>(a, l);
         case 2048:
+            if (l.variant == 3) return row_launch_pair<2048, 4, 2>(a, l);
             if (l.variant == 2) return row_launch_units<float2, 2048, 8, 4>(a, l);
             return l.variant == 1 ? row_launch<float2, 2048>(a, l) : row_launch_persistent<float2, 2048>(a, l);
         case 4096:
+            if (l.variant == 3) return row_launch_pair<4096, 2, 1>(a, l);
             if (l.variant == 2) return row_launch_units<float2, 4096, 4, 2>(a, l);
             return l.variant == 1 ? row_launch<float2, 4096>(a, l) : row_launch_persistent<float2, 4096>(a, l);
         case 8192: return l.variant == 1 ? row_launch<float2, 8192>(a, l) : row_launch_persistent<float2, 8192>(a, l);
@@ -26,7 +31,8 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
 
 // lines = columns per block; 0 = default. Wider blocks give longer contiguous segments per
 // row (L * 8 bytes), narrower ones more resident blocks per SM. -1 = persistent TMA kernel,
-// -2 = unit-pipelined kernel (two columns per unit).
+// -2 = unit-pipelined kernel (two columns per unit), -3 = unit-pipelined kernel on packed
+// FP32x2 column pairs, -4 = wide kernel (four columns, packed pairs, staged by TMA).
 template <>
 cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, const PassLaunch& l) {
     using namespace detail;
@@ -38,14 +44,20 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
         case 256: return col_launch<float2, 256, 16>(a, l);
         case 512: return col_launch<float2, 512, 16>(a, l);
         case 1024:
+            if (lines == -4) return col_launch_wide<1024>(a, l);
+            if (lines == -3) return col_launch_pair<1024, 8, 4>(a, l);
             if (lines == -2) return col_launch_units<float2, 1024, 2, 8, 4>(a, l);
             if (lines == -1) return col_launch_persistent<float2, 1024, 4>(a, l);
             return lines == 8 ? col_launch<float2, 1024, 8>(a, l) : col_launch<float2, 1024, 16>(a, l);
         case 2048:
+            if (lines == -4) return col_launch_wide<2048>(a, l);
+            if (lines == -3) return col_launch_pair<2048, 4, 2>(a, l);
             if (lines == -2) return col_launch_units<float2, 2048, 2, 4, 2>(a, l);
             if (lines == -1) return col_launch_persistent<float2, 2048, 2>(a, l);
             return lines == 4 ? col_launch<float2, 2048, 4>(a, l) : col_launch<float2, 2048, 8>(a, l);
         case 4096:
+            if (lines == -4) return col_launch_wide<4096>(a, l);
+            if (lines == -3) return col_launch_pair<4096, 2, 1>(a, l);
             if (lines == -2) return col_launch_units<float2, 4096, 2, 2, 1>(a, l);
             if (lines == -1) return col_launch_persistent<float2, 4096, 2>(a, l);
             return lines == 2 ? col_launch<float2, 4096, 2>(a, l) : col_launch<float2, 4096, 4>(a, l);
@@ -75,27 +87,28 @@ int col_lines_default(int n, bool dbl) {
 int col_candidates(int n, int* out) {
     switch (n) {
         case 8192: out[0] = 2; out[1] = 1; return 2;
-        case 4096: out[0] = 4; out[1] = 2; out[2] = -1; out[3] = -2; return 4;
-        case 2048: out[0] = 8; out[1] = 4; out[2] = -1; out[3] = -2; return 4;
-        case 1024: out[0] = 16; out[1] = 8; out[2] = -1; out[3] = -2; return 4;
+        case 4096: out[5] = -4; out[0] = 4; out[1] = 2; out[2] = -1; out[3] = -2; out[4] = -3; return 6;
+        case 2048: out[5] = -4; out[0] = 8; out[1] = 4; out[2] = -1; out[3] = -2; out[4] = -3; return 6;
+        case 1024: out[5] = -4; out[0] = 16; out[1] = 8; out[2] = -1; out[3] = -2; out[4] = -3; return 6;
         default: out[0] = 0; return 1;
     }
 }
 
-int row_variant_count(int n) { return (n == 2048 || n == 4096) ? 3 : n >= 1024 ? 2 : 1; }
+// row variants: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row pairs
+int row_variant_count(int n) { return (n >= 1024 && n <= 4096) ? 4 : n == 8192 ? 2 : 1; }
 
 void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persistent, int* out_lines) {
     int p = 0, w = 0;
     if (row) {                                              // mirrors launch_row_pass
-        p = (!dbl && n >= 1024) ? (variant == 1 ? 0 : variant == 2 && (n == 2048 || n == 4096) ? 2 : 1) : 0;
+        p = (!dbl && n >= 1024) ? (variant == 1 ? 0 : (variant == 2 || variant == 3) && n <= 4096 ? variant : 1) : 0;
     } else if (dbl) {
         w = col_lines_default(n, true);                     // the double launcher ignores `lines`
     } else {                                                // mirrors launch_col_pass<float2>
         if (lines == 0) lines = col_lines_default(n, false);
         switch (n) {
-            case 1024: p = lines == -1 ? 1 : lines == -2 ? 2 : 0; w = p == 1 ? 4 : p == 2 ? 2 : (lines == 8 ? 8 : 16); break;
-            case 2048: p = lines == -1 ? 1 : lines == -2 ? 2 : 0; w = p ? 2 : (lines == 4 ? 4 : 8); break;
-            case 4096: p = lines == -1 ? 1 : lines == -2 ? 2 : 0; w = p ? 2 : (lines == 2 ? 2 : 4); break;
+            case 1024: p = lines < 0 ? -lines : 0; w = p == 1 || p == 4 ? 4 : p ? 2 : (lines == 8 ? 8 : 16); break;
+            case 2048: p = lines < 0 ? -lines : 0; w = p == 4 ? 4 : p ? 2 : (lines == 4 ? 4 : 8); break;
+            case 4096: p = lines < 0 ? -lines : 0; w = p == 4 ? 4 : p ? 2 : (lines == 2 ? 2 : 4); break;
             case 8192: w = lines == 1 ? 1 : 2; break;
             default: w = 16; break;
         }

@@ -124,6 +124,50 @@ cudaError_t col_launch_units(const ColArgs<C>& a, const PassLaunch& l) {
     return cudaGetLastError();
 }
 
+template <int N, int U, int S>
+cudaError_t col_launch_pair(const ColArgs<float2>& a, const PassLaunch& l) {
+    using Cfg = PColPairCfg<N, U, S>;
+    static unsigned done = 0;
+    const size_t smem = Cfg::template smem<float2>();
+    cudaError_t e = ensure_smem(col_pass_pair_kernel<N, U, S>, smem, done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = sm_count(&sms)) != cudaSuccess) return e;
+    if (a.in != a.out) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    if ((e = tc_make_field_map(a.in, N, (long long)l.batch * N, 2, &map)) != cudaSuccess) return e;
+    const int groups = l.batch * N / 2;
+    const int grid = groups < sms ? groups : sms;
+    col_pass_pair_kernel<N, U, S><<<grid, Cfg::THREADS, smem, l.stream>>>(a, map, groups);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t col_launch_wide(const ColArgs<float2>& a, const PassLaunch& l) {
+    using Cfg = WColCfg<N>;
+    static unsigned done = 0;
+    const size_t smem = Cfg::smem();
+    cudaError_t e = ensure_smem(col_pass_wide_kernel<N>, smem, done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = sm_count(&sms)) != cudaSuccess) return e;
+    // every group is loaded before any of its results is stored, so the pass may run in
+    // place; a separate output is fine too
+    if ((uintptr_t)a.out & 15) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    if ((e = tc_make_field_map(a.in, N, (long long)l.batch * N, 4, &map)) != cudaSuccess) return e;
+    static int occ = 0;
+    if (occ == 0) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, col_pass_wide_kernel<N>, Cfg::THREADS, smem)) != cudaSuccess)
+            return e;
+        if (occ < 1) occ = 1;
+    }
+    const int groups = l.batch * N / 4;
+    const int grid = groups < sms * occ ? groups : sms * occ;
+    col_pass_wide_kernel<N><<<grid, Cfg::THREADS, smem, l.stream>>>(a, map, groups);
+    return cudaGetLastError();
+}
+
 template <typename C, int N, int U, int S>
 cudaError_t row_launch_units(const RowArgs<C>& a, const PassLaunch& l) {
     using Cfg = URowCfg<N, U, S>;
@@ -136,6 +180,21 @@ cudaError_t row_launch_units(const RowArgs<C>& a, const PassLaunch& l) {
     const int rows = l.batch * N;
     const int grid = rows < sms ? rows : sms;
     row_pass_units_kernel<C, N, U, S><<<grid, Cfg::THREADS, smem, l.stream>>>(a, rows);
+    return cudaGetLastError();
+}
+
+template <int N, int U, int S>
+cudaError_t row_launch_pair(const RowArgs<float2>& a, const PassLaunch& l) {
+    using Cfg = PRowPairCfg<N, U, S>;
+    static unsigned done = 0;
+    const size_t smem = Cfg::smem();
+    cudaError_t e = ensure_smem(row_pass_pair_kernel<N, U, S>, smem, done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = sm_count(&sms)) != cudaSuccess) return e;
+    const int pairs = l.batch * N / 2;
+    const int grid = pairs < sms ? pairs : sms;
+    row_pass_pair_kernel<N, U, S><<<grid, Cfg::THREADS, smem, l.stream>>>(a, pairs);
     return cudaGetLastError();
 }
 

@@ -240,9 +240,9 @@ def test_relay_chain_plan_4096(ctx):
 
 KERNEL_CHOICES = {
     # n: (row variants, column kernels) the complex64 plan offers
-    1024: ([0, 1], [16, 8, -1, -2]),
-    2048: ([0, 1, 2], [8, 4, -1, -2]),
-    4096: ([0, 1, 2], [4, 2, -1, -2]),
+    1024: ([0, 1, 2, 3], [16, 8, -1, -2, -3, -4]),
+    2048: ([0, 1, 2, 3], [8, 4, -1, -2, -3, -4]),
+    4096: ([0, 1, 2, 3], [4, 2, -1, -2, -3, -4]),
 }
 
 
@@ -257,15 +257,16 @@ def _relay_all_kernels(ctx, n, npix, seed):
     rows, cols = KERNEL_CHOICES[n]
     x = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
     seen = set()
-    for rv in rows:
-        for cl in cols:
-            plan.set_pass_kernel(rv, cl)
-            names = {plan.pass_kernel(i) for i in range(plan.launch_count)}
-            seen |= names
-            x.fill_(float("nan"))
-            plan.execute(x)
-            err = rel_l2(x.cpu().numpy()[0], ref)
-            assert err < 1e-5, (rv, cl, sorted(names), err)
+    # every row kernel with one column kernel, every column kernel with one row kernel
+    combos = [(rv, cols[0]) for rv in rows] + [(rows[0], cl) for cl in cols[1:]]
+    for rv, cl in combos:
+        plan.set_pass_kernel(rv, cl)
+        names = {plan.pass_kernel(i) for i in range(plan.launch_count)}
+        seen |= names
+        x.fill_(float("nan"))
+        plan.execute(x)
+        err = rel_l2(x.cpu().numpy()[0], ref)
+        assert err < 1e-5, (rv, cl, sorted(names), err)
     with pytest.raises(RuntimeError):
         plan.set_pass_kernel(len(rows), 0)
     with pytest.raises(RuntimeError):
@@ -275,17 +276,18 @@ def _relay_all_kernels(ctx, n, npix, seed):
 
 @pytest.mark.parametrize("n", [1024, 2048])
 def test_relay_every_pass_kernel(ctx, n):
-    """Every row and column kernel the plan can pick (per-group, persistent, unit-pipelined)
-    gives the oracle's relay to 1e-5 relative L2."""
+    """Every row and column kernel the plan can pick (per-group, persistent, unit-pipelined,
+    packed pairs, wide) gives the oracle's relay to 1e-5 relative L2."""
     seen = _relay_all_kernels(ctx, n, n // 2, seed=2)
     assert any("_units" in k for k in seen) and any("_persistent" in k for k in seen)
 
 
 @pytest.mark.slow
 def test_relay_every_pass_kernel_4096(ctx):
-    """The same at 4096^2, the benchmarked size (one oracle run, twelve kernel pairs)."""
+    """The same at 4096^2, the benchmarked size (one oracle run, nine kernel pairs)."""
     seen = _relay_all_kernels(ctx, 4096, 1024, seed=0)
-    assert "row_pass_units<4096>" in seen and "col_pass_units<4096,2>" in seen
+    assert "row_pass_units<4096>" in seen and "col_pass_units<4096,2>" in seen and "col_pass_pair<4096,2>" in seen
+    assert "col_pass_wide<4096,4>" in seen and "row_pass_pair<4096>" in seen
 
 
 def test_mixed_plan_direct_then_as(ctx):
