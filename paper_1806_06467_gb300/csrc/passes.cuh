@@ -870,7 +870,7 @@ col_pass_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_con
 // a warp covers 16 rows x 4 columns. The next group arrives by TMA (boxes of 4 x 256) in a
 // 128-KB staging buffer while the current one is transformed in registers; the FFT
 // exchanges use half-size buffers (two rounds), which is what leaves room for the staging
-// buffer; results leave straight from registers (16-byte stores, 32 bytes per row per warp).
+// buffer; results leave by TMA stores through the exchange region, half a group at a time.
 template <int N> struct WColCfg {
     static constexpr int TPL = LineGeom<N>::TPL;
     static constexpr int THREADS = 2 * TPL;
@@ -926,7 +926,8 @@ col_pass_wide_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_con
             const float4 q = src[(t + s * Cfg::TPL) * 2 + p];   // (re_A, im_A, re_B, im_B)
             v[s] = CP{pk::pack(q.x, q.z), pk::pack(q.y, q.w)};
         }
-        __syncthreads();                                    // staging emptied by every thread
+        if (threadIdx.x == 0) tc::bulk_wait_read<0>();      // previous group's second half stored
+        __syncthreads();                                    // staging emptied; exchange region free
         if (threadIdx.x == 0 && k + 1 < mine) issue_load(k + 1);
         if (a.flags & CF_FWD) pk::line_fft2<N, false, true>(v, xl, t, tw, sync);
         if (a.flags & CF_TABLE) {
@@ -946,15 +947,32 @@ col_pass_wide_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_con
                 v[s] = CP{pk::sub2(pk::mul2(v[s].re, hr), pk::mul2(v[s].im, hi)),
                           pk::fma2(v[s].re, hi, pk::mul2(v[s].im, hr))};
         }
-        float2* out = a.out + (size_t)b * N * N + col;
+        // results leave by TMA in two halves of N/2 rows through the exchange region (slots
+        // 0..7 are rows 0..N/2-1), so that no warp waits on global stores
+        float4* obuf = reinterpret_cast<float4*>(stage + Cfg::GROUP);
+        const int x = (g % GPI) * 4, y = b * N;
 #pragma unroll
-        for (int s = 0; s < 16; ++s) {
-            float4 q;
-            pk::unpack(v[s].re, q.x, q.z);
-            pk::unpack(v[s].im, q.y, q.w);
-            *reinterpret_cast<float4*>(out + (size_t)(t + s * Cfg::TPL) * N) = q;
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                float4 q;
+                pk::unpack(v[8 * h + s].re, q.x, q.z);
+                pk::unpack(v[8 * h + s].im, q.y, q.w);
+                obuf[(t + s * Cfg::TPL) * 2 + p] = q;
+            }
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+#pragma unroll 1
+                for (int q = 0; q < Cfg::BOXES / 2; ++q)
+                    tc::tma_store_2d(&map, obuf + q * 512, x, y + h * (N / 2) + q * 256);
+                tc::bulk_commit();
+                if (h == 0) tc::bulk_wait_read<0>();     // first half read out before the second is written
+            }
+            if (h == 0) __syncthreads();
         }
     }
+    if (threadIdx.x == 0) tc::bulk_wait<0>();
 }
 
 template <int N, int U, int S> struct URowCfg {

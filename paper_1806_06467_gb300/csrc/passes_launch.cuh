@@ -151,9 +151,7 @@ cudaError_t col_launch_wide(const ColArgs<float2>& a, const PassLaunch& l) {
     if (e != cudaSuccess) return e;
     int sms = 0;
     if ((e = sm_count(&sms)) != cudaSuccess) return e;
-    // every group is loaded before any of its results is stored, so the pass may run in
-    // place; a separate output is fine too
-    if ((uintptr_t)a.out & 15) return cudaErrorInvalidValue;
+    if (a.in != a.out) return cudaErrorInvalidValue;   // one tensor map serves loads and stores
     CUtensorMap map;
     if ((e = tc_make_field_map(a.in, N, (long long)l.batch * N, 4, &map)) != cudaSuccess) return e;
     static int occ = 0;
