@@ -367,15 +367,15 @@ def coronagraph_bench(ctx, device, steps: int, warmup: int, precision: int, n_la
     torch.cuda.synchronize()
     per = np.array([[evs[k][s].elapsed_time(evs[k][s + 1]) for s in range(n_stage)] for k in range(steps)])
     total_ms = float(per.sum())
-    # algorithmic tensor work: 8 real flops per complex MAC, three split products
-    cmac = {1: 0.0, 2: 0.0, 3: 0.0, 4: 0.0, 5: 0.0}
+    # dense tensor work: 8 real flops per complex MAC, three split products, every K element
+    cmac = 0.0
     for it in items:
         mo = it["m_occ"]
-        cmac[1] += n * mo * n + mo * mo * n
-        cmac[2] += 0.0
-        cmac[3] += mo * n * mo + n * n * mo
-        cmac[5] += n * md * n + md * md * n
-    flops_per_step = 24.0 * sum(cmac.values())
+        cmac += n * mo * n + mo * mo * n + mo * n * mo + n * n * mo + n * md * n + md * md * n
+    dense_flops = 24.0 * cmac
+    # what the support-aware plan computes: only K ranges / tiles inside the spot and stop
+    useful_flops, issued_flops = plan.flops()
+    flops_per_step = useful_flops
     gemm_ms = float(per[:, 1:].sum())                 # stages 1-5 are tensor-core GEMM launches
     achieved = flops_per_step * steps / (gemm_ms / 1e3) / 1e12
     pk, src = tensor_peak(precision == coro.MFT_3XBF16)
@@ -387,7 +387,9 @@ def coronagraph_bench(ctx, device, steps: int, warmup: int, precision: int, n_la
            "roofline": {"bound": "tensor", "kernel": "tc_cgemm_kernel", "achieved": achieved, "peak": pk,
                         "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
                         "flops_per_step": flops_per_step, "time_share": gemm_ms / total_ms,
-                        "peak_source": src}}
+                        "issued_flops_per_step": issued_flops, "issued_frac": issued_flops * steps / (gemm_ms / 1e3) / 1e12 / pk,
+                        "dense_flops_per_step": dense_flops, "peak_source": src},
+           "stage_ms": [round(float(x), 4) for x in per.mean(axis=0)]}
     plan.close()
     return out
 

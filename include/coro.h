@@ -303,6 +303,11 @@ coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, double* peak_
  * Running 0-5 in order equals coro_lyot_plan_execute without the host copy of dh. */
 coro_status coro_lyot_plan_execute_range(coro_plan plan, const void* pupil, const double* peak, float* intensity,
                                          void* field, int first, int count);
+/* Tensor work of one execute (the six GEMMs), in flops: *useful = 24 per valid output per
+ * complex product inside the operands' known support (the spot, the Lyot stop: the plan runs
+ * only the K ranges and tiles those leave non-zero); *issued = the same over every 128 x 128
+ * tile and K slice the kernels run (padding included). Either pointer may be NULL. Host only. */
+coro_status coro_lyot_plan_flops(coro_plan plan, double* useful, double* issued);
 
 /* Pupil argument layout for execute / peak / gradient: item b, row i, column j of E_A at
  * pupil[b * bstride + i * ld + j] (default ld = n, bstride = n * n), so the pupil can be the

@@ -86,6 +86,7 @@ _SIGS = {
     "coro_lyot_plan_execute": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), _P, _P, ct.POINTER(ct.c_double)]),
     "coro_lyot_plan_peak": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double)]),
     "coro_lyot_plan_execute_range": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), _P, _P, ct.c_int, ct.c_int]),
+    "coro_lyot_plan_flops": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
     "coro_version": (ct.c_int, []),
     "coro_last_error": (ct.c_char_p, []),
     "coro_ctx_create": (ct.c_int, [ct.c_int, _P, ct.POINTER(_P)]),
@@ -391,6 +392,12 @@ class LyotPlan:
             self.handle, ct.c_void_p(pupil.data_ptr()), pk,
             None if intensity is None else ct.c_void_p(intensity.data_ptr()),
             None if field is None else ct.c_void_p(field.data_ptr()), first, count))
+
+    def flops(self) -> tuple[float, float]:
+        """(useful, issued) tensor flops of one execute (coro_lyot_plan_flops)."""
+        u, i = ct.c_double(), ct.c_double()
+        self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_flops(self.handle, ct.byref(u), ct.byref(i)))
+        return u.value, i.value
 
     def close(self):
         if getattr(self, "handle", None):

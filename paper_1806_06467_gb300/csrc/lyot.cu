@@ -180,6 +180,25 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
         h[6 * B + b] = TcItem{md, n, md, b, di[b], 0, all, 1.0f, 1.0f};
         h[7 * B + b] = TcItem{n, n, md, b, di[b], 0, lyot_thr, s_det, 1.0f};
         h[8 * B + b] = TcItem{n, n, mo, b, oi[b], 0, all, s_occ, 1.0f};
+        // known zeros of the X operands (tc_gemm skips the K slices and tiles they cover):
+        // X_B is the spot disk; Z3's columns are X_B's rows, so a band of the spot's width;
+        // E_D is the Lyot-stop disk; Z5's columns are E_D's rows, a band of the stop's width
+        h[2 * B + b].kr2 = spot;
+        h[2 * B + b].kdy = 1;
+        h[3 * B + b].kr2 = spot;
+        h[3 * B + b].kdy = 0;
+        h[4 * B + b].kr2 = lyot_thr;
+        h[4 * B + b].kdy = 1;
+        h[5 * B + b].kr2 = lyot_thr;
+        h[5 * B + b].kdy = 0;
+        // adjoint: the seed is zero outside the dark-hole's outer circle, Z4 a band of its
+        // width; the stop-less Babinet block reads Z3 as G4 does
+        h[6 * B + b].kr2 = dh_hi;
+        h[6 * B + b].kdy = 1;
+        h[7 * B + b].kr2 = dh_hi;
+        h[7 * B + b].kdy = 0;
+        h[8 * B + b].kr2 = spot;
+        h[8 * B + b].kdy = 0;
     }
     p->dev_items = (TcItem*)p->alloc(p->host_items.size() * sizeof(TcItem), &st);
     p->keep_lyot = p->dev_items ? (int*)p->alloc(B * sizeof(int), &st) : nullptr;
@@ -305,6 +324,21 @@ extern "C" coro_status coro_lyot_plan_execute(coro_plan plan, const void* pupil,
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_execute");
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_lyot_plan_flops(coro_plan plan, double* useful, double* issued) {
+    clear_error();
+    if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_flops: not a Lyot plan"); return CORO_EINVAL; }
+    auto* p = static_cast<LyotPlan*>(plan);
+    const int B = p->batch, n = p->n, md = p->m_det, mo = p->m_occ_max;
+    const int epi[6] = {TC_EPI_SPLITT, TC_EPI_SPLITT, TC_EPI_SPLITT, TC_EPI_BABINET, TC_EPI_SPLITT, TC_EPI_INTENSITY};
+    const int mm[6] = {n, mo, mo, n, n, md}, nn[6] = {mo, mo, n, n, md, md};
+    double u = 0, is = 0;
+    for (int g = 0; g < 6; ++g)
+        tc_count_flops(p->bf16, epi[g], p->host_items.data() + (size_t)g * B, B, mm[g], nn[g], &u, &is);
+    if (useful) *useful = u;
+    if (issued) *issued = is;
     return CORO_OK;
 }
 

@@ -20,8 +20,9 @@ constexpr int PLANE_BYTES = 128 * 64;    // 128 rows x 64-byte K slice
 constexpr int OPER_BYTES = 4 * PLANE_BYTES;
 constexpr int STAGE_BYTES = 2 * OPER_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int EPI_WARPS = 8;             // two per TMEM lane quarter, 64 output columns each
-constexpr int THREADS = 64 + 32 * EPI_WARPS;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int EPI_WARPS = 16;            // four per TMEM lane quarter, 32 output columns each
+constexpr int EPI_COLS = 128 * 4 / EPI_WARPS;  // output columns per epilogue warp
+constexpr int THREADS = 64 + 32 * EPI_WARPS;   // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr uint32_t TMEM_COLS = 512;      // two accumulator buffers of (128 re + 128 im) columns
 constexpr int kChunk = 1;                // K slices summed inside one tensor-core accumulator
 
@@ -63,6 +64,41 @@ __device__ __forceinline__ float2 load_split(const void* base, size_t plane, siz
     }
 }
 
+__host__ __device__ inline int isqrt_floor(long long v) {
+    long long w = (long long)sqrt((double)v);
+    while (w * w > v) --w;
+    while ((w + 1) * (w + 1) <= v) ++w;
+    return (int)w;
+}
+
+// Distance from c to the nearest of the integers lo..hi (0 if c lies inside).
+__host__ __device__ inline int dist_to_range(int c, int lo, int hi) { return c < lo ? lo - c : c > hi ? c - hi : 0; }
+
+// K slices [kb0, kb0 + kblocks) a tile (rows m0.., columns n0..) has to run: those that can
+// hold non-zeros of X's known support, none when a masking epilogue zeroes every output of
+// the tile. Shared by the kernel and the host-side flop count.
+__host__ __device__ inline void tile_k_range(const TcItem& it, int m0, int n0, int KE, bool masked, int& kb0,
+                                             int& kblocks) {
+    const int mhi = (m0 + BM < it.M ? m0 + BM : it.M) - 1, nhi = (n0 + BN < it.N ? n0 + BN : it.N) - 1;
+    if (masked && (it.mask_lo > 0 || it.mask_hi < 0x7fffffff)) {
+        const long long dx0 = dist_to_range(it.M / 2, m0, mhi), dy0 = dist_to_range(it.N / 2, n0, nhi);
+        const long long dx1 = (it.M / 2 - m0 > mhi - it.M / 2) ? it.M / 2 - m0 : mhi - it.M / 2;
+        const long long dy1 = (it.N / 2 - n0 > nhi - it.N / 2) ? it.N / 2 - n0 : nhi - it.N / 2;
+        const long long r2min = dx0 * dx0 + dy0 * dy0, r2max = dx1 * dx1 + dy1 * dy1;
+        if (r2min > it.mask_hi || r2max < it.mask_lo) { kb0 = 0; kblocks = 0; return; }
+    }
+    if (it.kr2 < 0) return;
+    const long long dm = dist_to_range(it.M / 2, m0, mhi);
+    const long long rem = (long long)it.kr2 - (long long)it.kdy * dm * dm;
+    if (rem < 0) { kb0 = 0; kblocks = 0; return; }
+    const int w = isqrt_floor(rem);
+    const int klo = it.K / 2 - w < 0 ? 0 : it.K / 2 - w;
+    const int khi = it.K / 2 + w > it.K - 1 ? it.K - 1 : it.K / 2 + w;
+    if (khi < klo) { kb0 = 0; kblocks = 0; return; }
+    kb0 = klo / KE;
+    kblocks = khi / KE - kb0 + 1;
+}
+
 template <bool BF16, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw, const TcArgs a) {
@@ -81,7 +117,8 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int KE = BF16 ? 32 : 16;               // real elements per 64-byte K slice
-    const int kblocks = (it.K + KE - 1) / KE;
+    int kb0 = 0, kblocks = (it.K + KE - 1) / KE;
+    tile_k_range(it, m0, n0, KE, EPI == TC_EPI_SPLITT || EPI == TC_EPI_BABINET, kb0, kblocks);
     const int nchunks = (kblocks + kChunk - 1) / kChunk;
 
     if (threadIdx.x == 0) {
@@ -108,8 +145,8 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
                 if (!tc::mbar_wait(&empty[s], ph ^ 1, a.err, 1)) break;
                 unsigned char* st = smem + s * STAGE_BYTES;
                 tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                tc::tma_load_4d(st, &mx, &full[s], k * KE, m0, 0, it.x_idx);
-                tc::tma_load_4d(st + OPER_BYTES, &mw, &full[s], k * KE, n0, 0, it.w_idx);
+                tc::tma_load_4d(st, &mx, &full[s], (kb0 + k) * KE, m0, 0, it.x_idx);
+                tc::tma_load_4d(st + OPER_BYTES, &mw, &full[s], (kb0 + k) * KE, n0, 0, it.w_idx);
             }
         }
     } else if (warp == 1) {
@@ -156,13 +193,13 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..9)
         const int q = warp & 3;                          // TMEM lane quarter this warp may read
-        const int half = (warp - 2) >> 2;                // which 64 of the 128 output columns
+        const int half = (warp - 2) >> 2;                // which EPI_COLS-wide group of the 128 output columns
         const int row = q * 32 + lane;
         const int m = m0 + row;
-        const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16) + half * 64;
-        float acc_re[64], acc_im[64];
+        const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16) + half * EPI_COLS;
+        float acc_re[EPI_COLS], acc_im[EPI_COLS];
 #pragma unroll
-        for (int j = 0; j < 64; ++j) { acc_re[j] = 0.f; acc_im[j] = 0.f; }
+        for (int j = 0; j < EPI_COLS; ++j) { acc_re[j] = 0.f; acc_im[j] = 0.f; }
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
             const int buf = c & 1;
@@ -170,16 +207,16 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
             __syncwarp();
             tc::tc_fence_after();
 #pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                uint32_t r[32];
-                tc::tmem_ld32(lane_base + buf * 256 + part * 32, r);
+            for (int part = 0; part < EPI_COLS / 16; ++part) {
+                uint32_t r[16];
+                tc::tmem_ld16(lane_base + buf * 256 + part * 16, r);
                 tc::tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc_re[part * 32 + j] += __uint_as_float(r[j]);
-                tc::tmem_ld32(lane_base + buf * 256 + 128 + part * 32, r);
+                for (int j = 0; j < 16; ++j) acc_re[part * 16 + j] += __uint_as_float(r[j]);
+                tc::tmem_ld16(lane_base + buf * 256 + 128 + part * 16, r);
                 tc::tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc_im[part * 32 + j] += __uint_as_float(r[j]);
+                for (int j = 0; j < 16; ++j) acc_im[part * 16 + j] += __uint_as_float(r[j]);
             }
             tc::tc_fence_before();
             __syncwarp();
@@ -187,11 +224,44 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
         }
         double dh = 0.0;
         float pk = 0.f;
-        if (ok && m < it.M) {
+        if constexpr (EPI == TC_EPI_BABINET) {
+            // read-modify-write of E_A: the reads of four columns are issued before any of
+            // their arithmetic, so each thread keeps 16 loads in flight
+            if (ok && m < it.M) {
+                const int kx = m - it.M / 2;
+                const size_t plane = (size_t)a.dst_rows * a.dst_ld;
+                constexpr int G = 4;
+#pragma unroll
+                for (int j0 = 0; j0 < EPI_COLS; j0 += G) {
+                    float2 e[G];
+                    bool keep[G];
+#pragma unroll
+                    for (int jj = 0; jj < G; ++jj) {
+                        const int n = n0 + half * EPI_COLS + j0 + jj;
+                        const int ky = n - it.N / 2;
+                        const int r2 = kx * kx + ky * ky;
+                        keep[jj] = n < it.N && r2 >= it.mask_lo && r2 <= it.mask_hi;
+                        e[jj] = keep[jj] ? load_split<BF16>(a.dst, plane, b * a.dst_bstride + (size_t)n * a.dst_ld + m)
+                                         : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < G; ++jj) {
+                        const int n = n0 + half * EPI_COLS + j0 + jj;
+                        if (n < it.N) {
+                            const float re = keep[jj] ? e[jj].x - acc_re[j0 + jj] * it.scale : 0.f;
+                            const float im = keep[jj] ? e[jj].y - acc_im[j0 + jj] * it.scale : 0.f;
+                            const size_t off = b * a.dst_bstride + (size_t)n * a.dst_ld + m;
+                            store_split<BF16>(a.dst, plane, off, re, im);
+                            if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(re, im);
+                        }
+                    }
+                }
+            }
+        } else if (ok && m < it.M) {
             const int kx = m - it.M / 2;
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const int n = n0 + half * 64 + j;
+            for (int j = 0; j < EPI_COLS; ++j) {
+                const int n = n0 + half * EPI_COLS + j;
                 if (n < it.N) {
                     float re = acc_re[j] * it.scale, im = acc_im[j] * it.scale;
                     const int ky = n - it.N / 2;
@@ -204,14 +274,6 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
                         if (!keep) { re = 0.f; im = 0.f; }
                         const size_t plane = (size_t)a.dst_rows * a.dst_ld;
                         store_split<BF16>(a.dst, plane, b * a.dst_bstride + (size_t)n * a.dst_ld + m, re, im);
-                    } else if constexpr (EPI == TC_EPI_BABINET) {
-                        const size_t plane = (size_t)a.dst_rows * a.dst_ld;
-                        const size_t off = b * a.dst_bstride + (size_t)n * a.dst_ld + m;
-                        const float2 e = load_split<BF16>(a.dst, plane, off);
-                        re = keep ? e.x - re : 0.f;
-                        im = keep ? e.y - im : 0.f;
-                        store_split<BF16>(a.dst, plane, off, re, im);
-                        if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(re, im);
                     } else {
                         const float inten = (re * re + im * im) * it.inv_peak;
                         if (a.dst) reinterpret_cast<float*>(a.dst)[b * a.dst_bstride + (size_t)n * a.dst_ld + m] = inten;
@@ -329,6 +391,31 @@ cudaError_t launch_t(const CUtensorMap& mx, const CUtensorMap& mw, int max_m, in
 }
 
 }  // namespace
+
+void tc_count_flops(bool bf16, int epi, const TcItem* items, int batch, int max_m, int max_n, double* useful,
+                    double* issued) {
+    const int KE = bf16 ? 32 : 16;
+    const bool masked = epi == TC_EPI_SPLITT || epi == TC_EPI_BABINET;
+    for (int b = 0; b < batch; ++b) {
+        const TcItem& it = items[b];
+        for (int m0 = 0; m0 < max_m && m0 < it.M; m0 += BM)
+            for (int n0 = 0; n0 < max_n && n0 < it.N; n0 += BN) {
+                int kb0 = 0, kblocks = (it.K + KE - 1) / KE;
+                tile_k_range(it, m0, n0, KE, masked, kb0, kblocks);
+                if (kblocks <= 0) continue;
+                const int rows = (m0 + BM < it.M ? BM : it.M - m0), cols = (n0 + BN < it.N ? BN : it.N - n0);
+                int klo = 0, khi = it.K - 1;                  // elements inside the support
+                if (it.kr2 >= 0) {
+                    const long long dm = dist_to_range(it.M / 2, m0, m0 + rows - 1);
+                    const int w = isqrt_floor((long long)it.kr2 - (long long)it.kdy * dm * dm);
+                    klo = it.K / 2 - w < 0 ? 0 : it.K / 2 - w;
+                    khi = it.K / 2 + w > it.K - 1 ? it.K - 1 : it.K / 2 + w;
+                }
+                *useful += 24.0 * rows * cols * (double)(khi - klo + 1);
+                *issued += 24.0 * BM * BN * (double)kblocks * KE;
+            }
+    }
+}
 
 cudaError_t tc_make_operand_map(const TcOperand& op, bool bf16, CUtensorMap* map) {
     auto fn = encode_fn();

@@ -10,7 +10,7 @@
 // One CTA owns a 128 x 128 complex output tile: two 128x128 FP32 accumulators in TMEM
 // (real at columns 0-127, imaginary at 128-255). Warp 0 streams 64-byte-wide K slices of all
 // four planes of X and W through a 3-stage shared-memory ring with one 4-D TMA per operand;
-// warp 1 issues tcgen05.mma (24 per slice); warps 2-5 drain TMEM and run the epilogue, which
+// warp 1 issues tcgen05.mma (24 per slice); warps 2-17 drain TMEM and run the epilogue, which
 // always writes the TRANSPOSED tile (Y^T), so that chained GEMMs X.W^T then (X.W^T)^T.W^T
 // realise A . E . A^T without any separate transpose.
 #pragma once
@@ -34,6 +34,10 @@ struct TcItem {
     int mask_lo, mask_hi;  // epilogue keeps samples with mask_lo <= r^2 <= mask_hi (integer px^2)
     float scale;           // multiplies Y
     float inv_peak;        // intensity normalisation
+    // Known support of X: X[m][k] = 0 unless (k - K/2)^2 + kdy (m - M/2)^2 <= kr2 (kdy = 1:
+    // a disk, 0: a band of columns); kr2 < 0: no known zeros. Each tile then runs only the K
+    // slices that can hold non-zeros (none if its rows hold none); the result is unchanged.
+    int kr2 = -1, kdy = 0;
 };
 
 struct TcArgs {
@@ -57,6 +61,11 @@ struct TcOperand {                   // a planar split operand in global memory
 };
 
 cudaError_t tc_make_operand_map(const TcOperand& op, bool bf16, CUtensorMap* map);
+// Tensor work of one tc_launch over host copies of its items: *useful = 24 flops (three split
+// products of a complex multiply-add) per valid output per K element inside the known support,
+// *issued = the same for every 128 x 128 tile and K slice the kernel runs. Added to the outputs.
+void tc_count_flops(bool bf16, int epi, const TcItem* items, int batch, int max_m, int max_n, double* useful,
+                    double* issued);
 // A field of 8-byte samples [rows_total][n] as a 2-D tensor map with boxes of box_cols x 256.
 cudaError_t tc_make_field_map(const void* base, int n, long long rows_total, int box_cols, CUtensorMap* map);
 cudaError_t tc_launch(bool bf16, int epi, const CUtensorMap& mx, const CUtensorMap& mw, int max_m, int max_n,
