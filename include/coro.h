@@ -185,6 +185,9 @@ coro_status coro_fresnel_plan_create(coro_ctx ctx, const coro_fresnel_desc* desc
 /* Run the plan in place on `field` (device, [batch][n][n]). pixelscale_out (host [batch], may
  * be NULL) receives the final pixel scale. */
 coro_status coro_fresnel_plan_execute(coro_plan plan, void* field, double* pixelscale_out);
+/* `times` executes back to back on the same field (one graph when graphs are on): the
+ * repeated-system throughput measurement, with per-pass timing when enabled. */
+coro_status coro_fresnel_plan_execute_n(coro_plan plan, void* field, int times);
 /* Number of kernels one execute launches (for launch accounting). */
 coro_status coro_plan_launch_count(coro_plan plan, int* out);
 /* Run passes [first, first + count) of the plan only (for per-launch timing); running every
@@ -216,6 +219,24 @@ coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent
  * Values the plan's N does not offer are rejected with CORO_EINVAL and nothing changes.
  * Every choice gives the same result up to FP32 rounding order (used to test each kernel). */
 coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, int col_lines);
+/* a10: replay plan execution as one CUDA graph (enable = 1) or launch kernel by kernel (0,
+ * the default). With graphs on, the first execute with a given set of device pointers
+ * (field; or pupil, intensity and field) runs eagerly and captures its launch sequence on a
+ * private stream; later executes with the same pointers replay it on the context's stream,
+ * and new pointers trigger a new capture. Host-side arguments (the Lyot peak normalisation)
+ * are copied to the device before each replay, outside the graph. Results are identical to
+ * the eager path. execute_range and the gradient never use the graph. */
+coro_status coro_plan_set_graph(coro_plan plan, int enable);
+/* Per-unit timing (units: the passes of a Fresnel plan; the six stages of execute_range for a
+ * Lyot plan). steps > 0 creates steps x (units + 1) CUDA events: the k-th execute of an
+ * execute_n call (execute counts as k = 0) records set k before its first unit and after
+ * every unit, on the stream the kernels run on and inside the graph when one is replayed.
+ * steps = 0 releases them. Synchronises the device; drops a captured graph. */
+coro_status coro_plan_set_timing(coro_plan plan, int steps);
+/* ms (host, [steps][units]): unit durations of executes 0..steps-1 of the last timed call
+ * (steps <= the count given to coro_plan_set_timing; every one of them must have run).
+ * Waits for the last of those events. */
+coro_status coro_plan_unit_times(coro_plan plan, int steps, float* ms);
 coro_status coro_plan_destroy(coro_plan plan);
 
 /* ------------------------------------------------------------------------------------------
@@ -294,6 +315,10 @@ coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc* desc, coro
  * (when given, the stream is synchronised). */
 coro_status coro_lyot_plan_execute(coro_plan plan, const void* pupil, const double* peak, float* intensity,
                                    void* field, double* dh);
+/* `times` executes back to back (one graph when graphs are on), without the host copy of dh;
+ * per-stage timing when enabled. */
+coro_status coro_lyot_plan_execute_n(coro_plan plan, const void* pupil, const double* peak, float* intensity,
+                                     void* field, int times);
 /* Normalisation: peak_out[b] = max |E_det|^2 of the same chain with the occulter removed
  * (E_D = E_A . Lyot stop). Synchronises the stream. */
 coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, double* peak_out);

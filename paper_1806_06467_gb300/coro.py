@@ -104,6 +104,11 @@ _SIGS = {
     "coro_fresnel_plan_pass_info": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]),
     "coro_fresnel_plan_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "coro_fresnel_plan_set_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.c_int]),
+    "coro_plan_set_timing": (ct.c_int, [_P, ct.c_int]),
+    "coro_plan_unit_times": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_float)]),
+    "coro_fresnel_plan_execute_n": (ct.c_int, [_P, _P, ct.c_int]),
+    "coro_lyot_plan_execute_n": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), _P, _P, ct.c_int]),
+    "coro_plan_set_graph": (ct.c_int, [_P, ct.c_int]),
     "coro_plan_destroy": (ct.c_int, [_P]),
     "coro_propagate_mft": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_double, ct.c_int, ct.c_int,
                                       ct.POINTER(ct.c_double), ct.c_int, ct.POINTER(Wavefront)]),
@@ -370,6 +375,16 @@ class LyotPlan:
             None if field is None else ct.c_void_p(field.data_ptr()), dh))
         return np.array(dh[:]) if want_dh else None
 
+    timing_units = 6
+
+    def execute_n(self, pupil, times: int, peak=None, intensity=None, field=None):
+        """`times` executes back to back (coro_lyot_plan_execute_n)."""
+        pk = None if peak is None else _dbl(np.broadcast_to(np.asarray(peak, float), (self.batch,)))
+        self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_execute_n(
+            self.handle, ct.c_void_p(pupil.data_ptr()), pk,
+            None if intensity is None else ct.c_void_p(intensity.data_ptr()),
+            None if field is None else ct.c_void_p(field.data_ptr()), times))
+
     def set_pupil_layout(self, ld: int, bstride: int):
         self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_set_pupil_layout(self.handle, ld, bstride))
 
@@ -398,6 +413,21 @@ class LyotPlan:
         u, i = ct.c_double(), ct.c_double()
         self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_flops(self.handle, ct.byref(u), ct.byref(i)))
         return u.value, i.value
+
+    def use_graph(self, enable: bool = True) -> None:
+        """Replay execute as a CUDA graph (coro_plan_set_graph)."""
+        self.ctx.lib.check(self.ctx.lib.coro_plan_set_graph(self.handle, 1 if enable else 0))
+
+    def set_timing(self, steps: int) -> None:
+        """Per-unit CUDA-event timing of the next `steps` executes (coro_plan_set_timing)."""
+        self.ctx.lib.check(self.ctx.lib.coro_plan_set_timing(self.handle, steps))
+
+    def unit_times(self, steps: int) -> np.ndarray:
+        """[steps][units] durations in ms (coro_plan_unit_times)."""
+        units = self.timing_units
+        buf = (ct.c_float * (steps * units))()
+        self.ctx.lib.check(self.ctx.lib.coro_plan_unit_times(self.handle, steps, buf))
+        return np.array(buf[:], dtype=np.float64).reshape(steps, units)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -440,10 +470,33 @@ class FresnelPlan:
         self.handle = h
         ctx._track(self)
 
+    def use_graph(self, enable: bool = True) -> None:
+        """Replay execute as a CUDA graph (coro_plan_set_graph)."""
+        self.ctx.lib.check(self.ctx.lib.coro_plan_set_graph(self.handle, 1 if enable else 0))
+
+    def set_timing(self, steps: int) -> None:
+        """Per-unit CUDA-event timing of the next `steps` executes (coro_plan_set_timing)."""
+        self.ctx.lib.check(self.ctx.lib.coro_plan_set_timing(self.handle, steps))
+
+    def unit_times(self, steps: int) -> np.ndarray:
+        """[steps][units] durations in ms (coro_plan_unit_times)."""
+        units = self.timing_units
+        buf = (ct.c_float * (steps * units))()
+        self.ctx.lib.check(self.ctx.lib.coro_plan_unit_times(self.handle, steps, buf))
+        return np.array(buf[:], dtype=np.float64).reshape(steps, units)
+
     def execute(self, field) -> np.ndarray:
         ps = (ct.c_double * self.batch)()
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_execute(self.handle, ct.c_void_p(field.data_ptr()), ps))
         return np.array(ps[:])
+
+    @property
+    def timing_units(self) -> int:
+        return self.launch_count
+
+    def execute_n(self, field, times: int):
+        """`times` executes back to back (coro_fresnel_plan_execute_n)."""
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_execute_n(self.handle, ct.c_void_p(field.data_ptr()), times))
 
     def execute_range(self, field, first: int, count: int = 1):
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_execute_range(

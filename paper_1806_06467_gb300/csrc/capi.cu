@@ -459,12 +459,19 @@ struct Op {
     int variant = 0;      // row passes: 0 persistent, 1 one block per line group
 };
 
+// ev (optional, ops.size() + 1 events): recorded before the first pass and after each.
 template <typename C>
-coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, void* field) {
+coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, void* field,
+                    const cudaEvent_t* ev = nullptr) {
     coro_status st = CORO_OK;
     const C* tw = (const C*)get_twiddles(ctx, n, sizeof(C) == sizeof(double2), &st);
     if (!tw) return st;
     PassLaunch pl{ctx->stream, batch};
+    if (ev) {
+        const cudaError_t e0 = record_timing_event(ev[0], ctx->stream);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "cudaEventRecord");
+    }
+    int i = 0;
     for (const Op& op : ops) {
         cudaError_t e;
         if (op.row) {
@@ -489,13 +496,16 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
             e = launch_col_pass<C>(n, op.lines, a, pl);
         }
         if (e != cudaSuccess) return cuda_fail(e, op.row ? "row pass" : "column pass");
+        ++i;
+        if (ev && (e = record_timing_event(ev[i], ctx->stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     }
     return CORO_OK;
 }
 
-coro_status run_ops_any(coro_ctx ctx, int dtype, int n, int batch, const std::vector<Op>& ops, void* field) {
-    return dtype == CORO_C64 ? run_ops<float2>(ctx, n, batch, ops, field)
-                             : run_ops<double2>(ctx, n, batch, ops, field);
+coro_status run_ops_any(coro_ctx ctx, int dtype, int n, int batch, const std::vector<Op>& ops, void* field,
+                        const cudaEvent_t* ev = nullptr) {
+    return dtype == CORO_C64 ? run_ops<float2>(ctx, n, batch, ops, field, ev)
+                             : run_ops<double2>(ctx, n, batch, ops, field, ev);
 }
 
 // ------------------------------------------------------------------------------ hop tables
@@ -739,9 +749,12 @@ struct FresnelPlan : coro_plan_s {
     std::vector<std::string> tune_log;
     int kind() const override { return 1; }
     int launches() const override { return (int)ops.size(); }
+    int timing_units() const override { return (int)ops.size(); }
     ~FresnelPlan() override {
         DeviceGuard g(device);
         cudaDeviceSynchronize();
+        timing.release();
+        graph.reset();
         db.release();
     }
 };
@@ -846,10 +859,26 @@ extern "C" coro_status coro_fresnel_plan_execute(coro_plan plan, void* field, do
     if (!field) { set_error("coro_fresnel_plan_execute: field is NULL"); return CORO_EINVAL; }
     auto* p = static_cast<FresnelPlan*>(plan);
     DeviceGuard g(p->ctx->device);
-    coro_status st = run_ops_any(p->ctx, p->dtype, p->n, p->batch, p->ops, field);
+    coro_status st = run_graphed(p->ctx, p->graph, {field, (const void*)1}, [&]() {
+        return run_ops_any(p->ctx, p->dtype, p->n, p->batch, p->ops, field, p->timing.set(0));
+    });
     if (st == CORO_OK && pixelscale_out)
         for (int b = 0; b < p->batch; ++b) pixelscale_out[b] = p->ps_final[b];
     return st;
+}
+
+extern "C" coro_status coro_fresnel_plan_execute_n(coro_plan plan, void* field, int times) {
+    clear_error();
+    if (!plan || plan->kind() != 1) { set_error("coro_fresnel_plan_execute_n: not a Fresnel plan"); return CORO_EINVAL; }
+    if (!field || times < 1) { set_error("coro_fresnel_plan_execute_n: field NULL or times < 1"); return CORO_EINVAL; }
+    auto* p = static_cast<FresnelPlan*>(plan);
+    DeviceGuard g(p->ctx->device);
+    return run_graphed(p->ctx, p->graph, {field, (const void*)(intptr_t)times}, [&]() {
+        coro_status st = CORO_OK;
+        for (int k = 0; k < times && st == CORO_OK; ++k)
+            st = run_ops_any(p->ctx, p->dtype, p->n, p->batch, p->ops, field, p->timing.set(k));
+        return st;
+    });
 }
 
 extern "C" coro_status coro_fresnel_plan_execute_range(coro_plan plan, void* field, int first, int count) {
@@ -919,6 +948,7 @@ extern "C" coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row
         if (op.row) op.variant = row_variant;
         else op.lines = col_lines;
     }
+    p->graph.reset();                                   // a captured graph holds the old kernels
     return CORO_OK;
 }
 
@@ -926,6 +956,52 @@ extern "C" coro_status coro_plan_launch_count(coro_plan plan, int* out) {
     clear_error();
     if (!plan || !out) { set_error("coro_plan_launch_count: NULL argument"); return CORO_EINVAL; }
     *out = plan->launches();
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_plan_set_timing(coro_plan plan, int steps) {
+    clear_error();
+    if (!plan || steps < 0) { set_error("coro_plan_set_timing: NULL plan or steps < 0"); return CORO_EINVAL; }
+    PlanTiming& t = plan->timing;
+    cudaDeviceSynchronize();                             // no recorded event may be in flight
+    t.release();
+    plan->graph.reset();                                 // a captured graph holds the old events
+    if (steps == 0) return CORO_OK;
+    t.units = plan->timing_units();
+    t.ev.resize((size_t)steps * (t.units + 1));
+    for (auto& e : t.ev) {
+        const cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) {
+            e = nullptr;
+            for (auto& x : t.ev) if (x) cudaEventDestroy(x);
+            t.ev.clear();
+            return cuda_fail(r, "coro_plan_set_timing: cudaEventCreate");
+        }
+    }
+    t.steps = steps;
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_plan_unit_times(coro_plan plan, int steps, float* ms) {
+    clear_error();
+    if (!plan || !ms || steps < 1 || steps > plan->timing.steps) {
+        set_error("coro_plan_unit_times: bad argument (timing holds %d steps)", plan ? plan->timing.steps : 0);
+        return CORO_EINVAL;
+    }
+    const PlanTiming& t = plan->timing;
+    cudaError_t e = cudaEventSynchronize(t.ev[(size_t)(steps - 1) * (t.units + 1) + t.units]);
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+        const cudaEvent_t* s = t.set(k);
+        for (int i = 0; i < t.units && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[k * t.units + i], s[i], s[i + 1]);
+    }
+    return e == cudaSuccess ? CORO_OK : cuda_fail(e, "coro_plan_unit_times");
+}
+
+extern "C" coro_status coro_plan_set_graph(coro_plan plan, int enable) {
+    clear_error();
+    if (!plan) { set_error("coro_plan_set_graph: NULL plan"); return CORO_EINVAL; }
+    plan->graph.enabled = enable != 0;
+    plan->graph.reset();
     return CORO_OK;
 }
 

@@ -20,11 +20,48 @@ struct coro_ctx_s {
     int* err = nullptr;          // device flag set by kernels whose bounded waits expired
 };
 
+// Replay of a plan's launch sequence as one CUDA graph. The graph is captured on a private
+// stream the first time execute runs with a given set of device pointers (after one eager
+// run of the same sequence, which makes every lazily built table exist and produces that
+// call's result), and re-captured when the pointers change.
+struct PlanGraph {
+    bool enabled = false;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
+    }
+    ~PlanGraph() {
+        reset();
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+// Per-unit timing of consecutive executes: `steps` sets of (units + 1) events; execute k of
+// an execute_n call records set k before its first unit and after each unit (inside the
+// graph when one is used), so unit durations are measured on the stream the kernels run on.
+struct PlanTiming {
+    int steps = 0, units = 0;
+    std::vector<cudaEvent_t> ev;
+    void release() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        ev.clear();
+        steps = 0;
+    }
+    const cudaEvent_t* set(int k) const { return k < steps ? ev.data() + (size_t)k * (units + 1) : nullptr; }
+};
+
 // Base of every plan handle (Fresnel systems: kind 1, Lyot coronagraphs: kind 2).
 struct coro_plan_s {
+    PlanGraph graph;
+    PlanTiming timing;
     virtual ~coro_plan_s() {}
     virtual int kind() const = 0;
     virtual int launches() const = 0;
+    virtual int timing_units() const = 0;
 };
 
 namespace coro {
@@ -46,6 +83,49 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
+
+// Run `body` (which launches on ctx->stream) directly, or through the plan's graph: captured
+// on first use with `key`, replayed on ctx->stream afterwards. body returns a coro_status.
+template <typename F>
+coro_status run_graphed(coro_ctx ctx, PlanGraph& g, const std::vector<const void*>& key, F body) {
+    if (!g.enabled) return body();
+    if (g.exec && key == g.key) {
+        const cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
+        return e == cudaSuccess ? CORO_OK : cuda_fail(e, "cudaGraphLaunch");
+    }
+    coro_status st = body();                              // eager run: this call's result
+    if (st != CORO_OK) return st;
+    g.reset();
+    cudaError_t e = cudaSuccess;
+    if (!g.cap) e = cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate (graph capture)");
+    cudaStream_t user = ctx->stream;
+    ctx->stream = g.cap;
+    e = cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = body();
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(g.cap, &graph);
+        if (st == CORO_OK && e2 == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        else if (e2 != cudaSuccess) e = e2;
+        if (graph) cudaGraphDestroy(graph);
+    }
+    ctx->stream = user;
+    if (st != CORO_OK) { g.reset(); return st; }
+    if (e != cudaSuccess) { g.reset(); return cuda_fail(e, "graph capture"); }
+    g.key = key;
+    return CORO_OK;
+}
+
+// Record a timing event: a plain record, or an event-record node of the graph while the
+// stream is being captured (the external flag is only valid during capture).
+inline cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, s);
+}
 
 // Twiddle table for n (built lazily on the context's stream).
 const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st);

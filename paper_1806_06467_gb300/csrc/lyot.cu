@@ -55,9 +55,12 @@ struct LyotPlan : coro_plan_s {
     int device = 0;                    // kept so that destruction never touches the context
     int kind() const override { return 2; }
     int launches() const override { return 7; }
+    int timing_units() const override { return 6; }     // the stages of execute_range
     ~LyotPlan() override {
         DeviceGuard g(device);
         cudaDeviceSynchronize();
+        timing.release();
+        graph.reset();
         for (auto& b : bufs) cudaFree(b.p);
     }
     void* alloc(size_t bytes, coro_status* st) {
@@ -215,9 +218,21 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
 
 namespace {
 
+// The G6 item table with the intensity normalisation 1/peak (peak NULL: 1), stream-ordered.
+cudaError_t upload_det_items(LyotPlan* p, const double* peak_host) {
+    const int B = p->batch;
+    cudaStream_t s = p->ctx->stream;
+    if (peak_host) {
+        std::vector<TcItem> g6(p->host_items.begin() + 5 * B, p->host_items.begin() + 6 * B);
+        for (int b = 0; b < B; ++b) g6[b].inv_peak = (float)(1.0 / peak_host[b]);
+        return cudaMemcpyAsync(p->dev_items + 5 * B, g6.data(), B * sizeof(TcItem), cudaMemcpyHostToDevice, s);
+    }
+    return cudaMemcpyAsync(p->dev_items + 5 * B, p->host_items.data() + 5 * B, B * sizeof(TcItem), cudaMemcpyHostToDevice, s);
+}
+
 // G5 + G6 on the operand already in XA planes; intensity epilogue (seed: write dS/dconj(E_det)).
-cudaError_t detector_gemms(LyotPlan* p, const double* peak_host, float* intensity, void* field, bool track_peak,
-                           float2* seed = nullptr) {
+// The G6 items must have been uploaded (upload_det_items) before.
+cudaError_t detector_gemms(LyotPlan* p, float* intensity, void* field, bool track_peak, float2* seed = nullptr) {
     const int B = p->batch, n = p->n, md = p->m_det;
     cudaStream_t s = p->ctx->stream;
     TcArgs a{};
@@ -229,15 +244,6 @@ cudaError_t detector_gemms(LyotPlan* p, const double* peak_host, float* intensit
     a.dst_ld = p->Z5.ld;
     cudaError_t e = tc_launch(p->bf16, TC_EPI_SPLITT, p->mXA, p->mW3, n, md, n, B, a, s);
     if (e != cudaSuccess) return e;
-    if (peak_host) {                                  // normalisation goes into the item table
-        std::vector<TcItem> g6(p->host_items.begin() + 5 * B, p->host_items.begin() + 6 * B);
-        for (int b = 0; b < B; ++b) g6[b].inv_peak = (float)(1.0 / peak_host[b]);
-        e = cudaMemcpyAsync(p->dev_items + 5 * B, g6.data(), B * sizeof(TcItem), cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return e;
-    } else {
-        e = cudaMemcpyAsync(p->dev_items + 5 * B, p->host_items.data() + 5 * B, B * sizeof(TcItem), cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return e;
-    }
     e = cudaMemsetAsync(p->dh, 0, B * sizeof(double), s);
     if (e == cudaSuccess && track_peak) e = cudaMemsetAsync(p->peak, 0, B * sizeof(float), s);
     if (e != cudaSuccess) return e;
@@ -261,12 +267,18 @@ cudaError_t detector_gemms(LyotPlan* p, const double* peak_host, float* intensit
 
 namespace {
 
-// Stages 0 (split of the pupil), 1-4 (G1-G4), 5 (G5 + G6 with the intensity epilogue).
-cudaError_t run_stages(LyotPlan* p, const void* pupil, const double* peak, float* intensity, void* field, int first,
-                       int last) {
+// Stages 0 (split of the pupil), 1-4 (G1-G4), 5 (G5 + G6 with the intensity epilogue; its
+// item table must be current, see upload_det_items).
+// ev (optional, 7 events): recorded before stage 0 and after each of stages 0-5 (all six run).
+cudaError_t run_stages(LyotPlan* p, const void* pupil, float* intensity, void* field, int first, int last,
+                       const cudaEvent_t* ev = nullptr) {
     const int B = p->batch, n = p->n, mo = p->m_occ_max;
     cudaStream_t s = p->ctx->stream;
     cudaError_t e = cudaSuccess;
+    auto mark = [&](int i) {
+        if (ev && e == cudaSuccess) e = record_timing_event(ev[i], s);
+    };
+    mark(0);
     auto gemm = [&](int gi, int epi, const CUtensorMap& mx, const CUtensorMap& mw, const TcOperand& dst, int mm, int nn, int kk) {
         if (e != cudaSuccess || gi + 1 < first || gi + 1 > last) return;
         TcArgs a{};
@@ -277,13 +289,16 @@ cudaError_t run_stages(LyotPlan* p, const void* pupil, const double* peak, float
         a.dst_rows = dst.rows;
         a.dst_ld = dst.ld;
         e = tc_launch(p->bf16, epi, mx, mw, mm, nn, kk, B, a, s);
+        mark(gi + 2);
     };
     if (first <= 0 && last >= 0) e = tc_split(p->bf16, (const float2*)pupil, p->pupil_bstride, p->pupil_ld, p->XA, s);
+    mark(1);
     gemm(0, TC_EPI_SPLITT, p->mXA, p->mW1, p->Z1, n, mo, n);     // G1
     gemm(1, TC_EPI_SPLITT, p->mZ1, p->mW1, p->XB, mo, mo, n);    // G2 (x spot)
     gemm(2, TC_EPI_SPLITT, p->mXB, p->mW2, p->Z3, mo, n, mo);    // G3
     gemm(3, TC_EPI_BABINET, p->mZ3, p->mW2, p->XA, n, n, mo);    // G4 (Babinet, x Lyot)
-    if (e == cudaSuccess && first <= 5 && last >= 5) e = detector_gemms(p, peak, intensity, field, false);
+    if (e == cudaSuccess && first <= 5 && last >= 5) e = detector_gemms(p, intensity, field, false);
+    mark(6);
     return e;
 }
 
@@ -302,7 +317,9 @@ extern "C" coro_status coro_lyot_plan_execute_range(coro_plan plan, const void* 
         for (int b = 0; b < p->batch; ++b)
             if (!(peak[b] > 0)) { set_error("coro_lyot_plan_execute_range: peak[%d] must be > 0", b); return CORO_EINVAL; }
     DeviceGuard g(p->ctx->device);
-    cudaError_t e = run_stages(p, pupil, peak, intensity, field, first, first + count - 1);
+    const int last = first + count - 1;
+    cudaError_t e = (first <= 5 && last >= 5) ? upload_det_items(p, peak) : cudaSuccess;
+    if (e == cudaSuccess) e = run_stages(p, pupil, intensity, field, first, last);
     return e == cudaSuccess ? CORO_OK : cuda_fail(e, "coro_lyot_plan_execute_range");
 }
 
@@ -318,13 +335,40 @@ extern "C" coro_status coro_lyot_plan_execute(coro_plan plan, const void* pupil,
             if (!(peak[b] > 0)) { set_error("coro_lyot_plan_execute: peak[%d] must be > 0", b); return CORO_EINVAL; }
     DeviceGuard g(p->ctx->device);
     cudaStream_t s = p->ctx->stream;
-    cudaError_t e = run_stages(p, pupil, peak, intensity, field, 0, 5);
+    cudaError_t e = upload_det_items(p, peak);           // outside any graph: plain stream copy
+    if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_execute");
+    const coro_status st = run_graphed(p->ctx, p->graph, {pupil, intensity, field, (const void*)1}, [&]() -> coro_status {
+        const cudaError_t e1 = run_stages(p, pupil, intensity, field, 0, 5, p->timing.set(0));
+        return e1 == cudaSuccess ? CORO_OK : cuda_fail(e1, "coro_lyot_plan_execute");
+    });
+    if (st != CORO_OK) return st;
+    s = p->ctx->stream;
     if (e == cudaSuccess && dh) {
         e = cudaMemcpyAsync(dh, p->dh, B * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_execute");
     return CORO_OK;
+}
+
+extern "C" coro_status coro_lyot_plan_execute_n(coro_plan plan, const void* pupil, const double* peak, float* intensity,
+                                                void* field, int times) {
+    clear_error();
+    if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_execute_n: not a Lyot plan"); return CORO_EINVAL; }
+    if (!pupil || times < 1) { set_error("coro_lyot_plan_execute_n: pupil NULL or times < 1"); return CORO_EINVAL; }
+    auto* p = static_cast<LyotPlan*>(plan);
+    if (peak)
+        for (int b = 0; b < p->batch; ++b)
+            if (!(peak[b] > 0)) { set_error("coro_lyot_plan_execute_n: peak[%d] must be > 0", b); return CORO_EINVAL; }
+    DeviceGuard g(p->ctx->device);
+    cudaError_t e = upload_det_items(p, peak);
+    if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_execute_n");
+    return run_graphed(p->ctx, p->graph, {pupil, intensity, field, (const void*)(intptr_t)times}, [&]() -> coro_status {
+        cudaError_t e1 = cudaSuccess;
+        for (int k = 0; k < times && e1 == cudaSuccess; ++k)
+            e1 = run_stages(p, pupil, intensity, field, 0, 5, p->timing.set(k));
+        return e1 == cudaSuccess ? CORO_OK : cuda_fail(e1, "coro_lyot_plan_execute_n");
+    });
 }
 
 extern "C" coro_status coro_lyot_plan_flops(coro_plan plan, double* useful, double* issued) {
@@ -351,7 +395,8 @@ extern "C" coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, do
     cudaStream_t s = p->ctx->stream;
     // occulter removed: E_D = E_A . Lyot stop, then the detector MFT
     cudaError_t e = tc_split(p->bf16, (const float2*)pupil, p->pupil_bstride, p->pupil_ld, p->XA, s, p->keep_lyot);
-    if (e == cudaSuccess) e = detector_gemms(p, nullptr, nullptr, nullptr, true);
+    if (e == cudaSuccess) e = upload_det_items(p, nullptr);
+    if (e == cudaSuccess) e = detector_gemms(p, nullptr, nullptr, true);
     std::vector<float> pk(B);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pk.data(), p->peak, B * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -416,8 +461,9 @@ extern "C" coro_status coro_lyot_plan_gradient(coro_plan plan, const void* pupil
     if (st != CORO_OK) return st;
     cudaStream_t s = p->ctx->stream;
     // forward (stages 0-4), then the detector MFT writing the seed mask . E_det / peak
-    cudaError_t e = run_stages(p, pupil, peak, nullptr, nullptr, 0, 4);
-    if (e == cudaSuccess) e = detector_gemms(p, peak, nullptr, nullptr, false, p->seed);
+    cudaError_t e = run_stages(p, pupil, nullptr, nullptr, 0, 4);
+    if (e == cudaSuccess) e = upload_det_items(p, peak);
+    if (e == cudaSuccess) e = detector_gemms(p, nullptr, nullptr, false, p->seed);
     if (e == cudaSuccess && dh_out) e = cudaMemcpyAsync(dh_out, p->dh, B * sizeof(double), cudaMemcpyDeviceToHost, s);
     // adjoint: G_D = IMFT_det(seed); G_C = Lyot . G_D; G_A = G_C - IMFT_occ(spot . MFT_occ(G_C))
     if (e == cudaSuccess) e = tc_split(p->bf16, p->seed, (long long)md * md, md, p->XS, s);

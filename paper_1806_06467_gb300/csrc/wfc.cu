@@ -58,6 +58,7 @@ struct WfcPlan : coro_plan_s {
     std::vector<double> peak;
     int kind() const override { return 3; }
     int launches() const override { return 0; }
+    int timing_units() const override { return 0; }
     ~WfcPlan() override {
         if (lyot) coro_plan_destroy(lyot);
         coro::DeviceGuard gd(device);

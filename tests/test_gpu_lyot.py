@@ -109,3 +109,39 @@ def test_lyot_full_size(ctx, prec):
                           "3.3e-11 on this dark hole", strict=False)
 def test_lyot_full_size_north_star_bar(ctx):
     assert full_size_error(ctx, coro.MFT_3XTF32) <= NORTH_STAR_DH
+
+
+def test_lyot_graph_replay_matches_eager(ctx):
+    """a10: the graph-replayed execute gives bitwise the eager result, follows new peak values
+    (copied outside the graph) and re-captures when the output buffer changes."""
+    n, npix, m_det = 128, 120, 96
+    items = [dict(m_occ=40, du_occ=0.25, spot_radius=3.0, du_det=0.5, dh_in=4.0, dh_out=16.0),
+             dict(m_occ=37, du_occ=0.27, spot_radius=3.0, du_det=0.45, dh_in=4.0, dh_out=16.0)]
+    pupils = np.stack([zernike_pupil(n, npix, 550e-9, s, rms=20e-9) for s in range(2)]).astype(np.complex64)
+    x = torch.from_numpy(pupils).cuda()
+    plan = coro.LyotPlan(ctx, n=n, npix=npix, lyot_frac=0.8, m_det=m_det, items=items, precision=coro.MFT_3XTF32)
+    peak = plan.peak(x)
+    eager = torch.empty((2, m_det, m_det), dtype=torch.float32, device="cuda")
+    dh_eager = plan.execute(x, peak=peak, intensity=eager)
+    plan.use_graph(True)
+    out = torch.full((2, m_det, m_det), float("nan"), device="cuda")
+    for _ in range(3):                                  # capture, then two replays
+        out.fill_(float("nan"))
+        dh = plan.execute(x, peak=peak, intensity=out)
+        assert torch.equal(out, eager)
+        assert np.array_equal(dh, dh_eager)
+    dh2 = plan.execute(x, peak=2 * np.asarray(peak), intensity=out)     # new normalisation, same graph
+    assert torch.allclose(out, eager / 2, rtol=1e-6, atol=0)
+    assert np.allclose(dh2, dh_eager / 2, rtol=1e-12)
+    other = torch.empty_like(out)
+    plan.execute(x, peak=peak, intensity=other)        # new pointer: re-captured
+    assert torch.equal(other, eager)
+    plan.set_timing(2)
+    for _ in range(2):
+        other.fill_(float("nan"))
+        plan.execute_n(x, 2, peak=peak, intensity=other)
+        assert torch.equal(other, eager)
+    t = plan.unit_times(2)
+    assert t.shape == (2, 6) and np.all(t > 0)
+    plan.set_timing(0)
+    plan.use_graph(False)
