@@ -129,7 +129,7 @@ def measured_peaks() -> tuple[float, str]:
 
 def pass_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("fft_engine.cuh", "passes.cuh", "passes_launch.cuh", "passes_f32.cu"):
+    for f in ("fft_engine.cuh", "fft_pair.cuh", "passes.cuh", "passes_launch.cuh", "passes_f32.cu"):
         with open(os.path.join(ROOT, "paper_1806_06467_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

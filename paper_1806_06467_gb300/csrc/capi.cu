@@ -455,8 +455,8 @@ struct Op {
     PassElems elems{};
     const void* tab_x = nullptr;
     const void* tab_y = nullptr;
-    int lines = 0;        // column passes: block width (0 default, -1 persistent TMA kernel)
-    int variant = 0;      // row passes: 0 persistent, 1 one block per line group
+    int lines = 0;        // column passes: 0 default, > 0 block width, < 0 staged kernels (passes_f32.cu)
+    int variant = -1;     // row passes: -1 default, 0 persistent, 1 per group, 2 units, 3 pairs
 };
 
 // ev (optional, ops.size() + 1 events): recorded before the first pass and after each.

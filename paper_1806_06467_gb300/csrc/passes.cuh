@@ -1146,7 +1146,7 @@ row_pass_pair_kernel(const __grid_constant__ RowArgs<float2> a, int pairs) {
 struct PassLaunch {
     cudaStream_t stream;
     int batch;
-    int variant = 0;      // row passes: 0 persistent (where built), 1 one block per line group
+    int variant = -1;     // row passes: -1 default, 0 persistent, 1 per group, 2 units, 3 pairs
 };
 
 // Implemented per precision in passes_f32.cu / passes_f64.cu.
@@ -1160,6 +1160,8 @@ int col_lines_default(int n, bool dbl);
 // (complex64).
 int col_candidates(int n, int* out);
 int row_variant_count(int n);
+// The kernels used without tuning (CORO_AUTOTUNE=0, or sizes without candidates).
+int row_variant_default(int n);
 // The kernel a pass with these settings launches: persistent (1) or not, and its lines.
 void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persistent, int* out_lines);
 

@@ -4,8 +4,10 @@
 namespace coro {
 
 template <>
-cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassLaunch& l) {
+cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassLaunch& l0) {
     using namespace detail;
+    PassLaunch l = l0;
+    if (l.variant < 0) l.variant = row_variant_default(n);
     switch (n) {
         case 32: return row_launch<float2, 32>(a, l);
         case 64: return row_launch<float2, 64>(a, l);
@@ -78,11 +80,12 @@ int col_lines_default(int n, bool dbl) {
     }
     switch (n) {
         case 8192: return 2;
-        case 4096: return 4;
-        case 2048: return 8;
+        case 4096: case 2048: case 1024: return -3;   // packed column pairs
         default: return 16;
     }
 }
+
+int row_variant_default(int n) { return (n >= 1024 && n <= 4096) ? 3 : 0; }
 
 int col_candidates(int n, int* out) {
     switch (n) {
@@ -99,6 +102,7 @@ int row_variant_count(int n) { return (n >= 1024 && n <= 4096) ? 4 : n == 8192 ?
 
 void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persistent, int* out_lines) {
     int p = 0, w = 0;
+    if (variant < 0) variant = row_variant_default(n);
     if (row) {                                              // mirrors launch_row_pass
         p = (!dbl && n >= 1024) ? (variant == 1 ? 0 : (variant == 2 || variant == 3) && n <= 4096 ? variant : 1) : 0;
     } else if (dbl) {
