@@ -138,8 +138,10 @@ coro_status coro_apply_element(coro_ctx ctx, const coro_wavefront* wf, const cor
  * CORO_FRESNEL_AS: angular spectrum (Sec. 1.1, Lawrence Eqs. 82-89 cited):
  *     E(z) = IDFT2[ exp(-i pi lambda z (fx^2 + fy^2)) DFT2[E] ], pixelscale unchanged.
  * CORO_FRESNEL_DIRECT: single-FFT Fresnel (Sec. 1.1):
- *     E'(u) = 1/(i lambda z) exp(i pi u^2/(lambda z)) dx^2 DFT2[E exp(i pi x^2/(lambda z))],
- *     pixelscale[b] <- lambda_b z / (n dx_b).
+ *     E'(u) = 1/(i lambda z) exp(i pi u^2/(lambda z)) dx^2 sum_x E(x) exp(i pi x^2/(lambda z))
+ *             exp(-2 pi i x u/(lambda z)) on the grid u_k = (k - n/2) du,
+ *     pixelscale[b] <- du = |lambda_b z / (n dx_b)| (a forward DFT for z > 0, the unscaled
+ *     inverse DFT for z < 0; one more pass for z < 0).
  * DFTs are centred (fftshift folded into the kernels). The global piston exp(2 pi i z/lambda)
  * is dropped. z != 0. Three HBM passes (row FFT, column FFT*H*IFFT, row IFFT).
  * ------------------------------------------------------------------------------------------ */
@@ -182,6 +184,41 @@ typedef struct {
 } coro_fresnel_desc;
 
 coro_status coro_fresnel_plan_create(coro_ctx ctx, const coro_fresnel_desc* desc, coro_plan* out);
+/* f2: a Fresnel system with the propagation method chosen automatically (Sec. 1.1: the
+ * angular-spectrum / direct choice the paper takes from Lawrence; POPPY's Fresnel wavefront).
+ * A Gaussian pilot beam with waist `beam_radius` at plane 0 is carried through the system by
+ * its complex parameter q (q += d per hop; 1/q -= 1/f per CORO_EL_LENS). A plane is inside
+ * when |Re q| < |Im q| (within one Rayleigh distance of the pilot waist) and stores the field
+ * on a planar reference; outside planes store it divided by exp(i pi r^2/(lambda R)), R = Re q
+ * (the distance from the pilot waist). Hops: inside -> inside angular spectrum; inside ->
+ * outside angular spectrum to the waist, then a direct hop without output quadratic phase;
+ * outside -> inside a direct hop without input quadratic phase to the waist, then angular
+ * spectrum; outside -> outside two direct hops through the waist. Direct hops change the pixel
+ * scale (|lambda z/(n dx)|); a direct hop with z < 0 is the inverse DFT, keeping the natural
+ * orientation. Lenses become quadratic phases that also swap the reference surface. The last
+ * plane's field is returned on a planar reference. Decisions are made per item and must agree
+ * across the batch (else CORO_ENOTIMPL). The result is a Fresnel plan (execute, pass info,
+ * graphs, timing apply); pixelscale_out of execute gives the final pitch. */
+typedef struct {
+    int dtype;
+    int batch;
+    int n;
+    const double* pixelscale;   /* host [batch], pixelscale at plane 0                       */
+    const double* wavelength;   /* host [batch]                                              */
+    double beam_radius;         /* pilot-beam waist radius at plane 0, metres (> 0)          */
+    int n_planes;
+    const double* distance;     /* host [n_planes-1], metres, finite and nonzero             */
+    int n_elements;
+    const coro_element* elements;   /* CORO_EL_LENS elements also refocus the pilot beam     */
+    int flags;                  /* CORO_PLAN_INIT_UNIFORM                                    */
+} coro_fresnel_system_desc;
+
+coro_status coro_fresnel_system_create(coro_ctx ctx, const coro_fresnel_system_desc* desc, coro_plan* out);
+/* For a plan made by coro_fresnel_system_create: spherical (host [n_planes], may be NULL)
+ * receives 1 for planes outside the pilot beam's Rayleigh range, *direct_hops the number of
+ * direct sub-hops. */
+coro_status coro_fresnel_system_info(coro_plan plan, int* spherical, int* direct_hops);
+
 /* Run the plan in place on `field` (device, [batch][n][n]). pixelscale_out (host [batch], may
  * be NULL) receives the final pixel scale. */
 coro_status coro_fresnel_plan_execute(coro_plan plan, void* field, double* pixelscale_out);

@@ -53,6 +53,13 @@ class FresnelDesc(ct.Structure):
                 ("n_elements", ct.c_int), ("elements", ct.POINTER(Element)), ("flags", ct.c_int)]
 
 
+class FresnelSystemDesc(ct.Structure):
+    _fields_ = [("dtype", ct.c_int), ("batch", ct.c_int), ("n", ct.c_int),
+                ("pixelscale", ct.POINTER(ct.c_double)), ("wavelength", ct.POINTER(ct.c_double)),
+                ("beam_radius", ct.c_double), ("n_planes", ct.c_int), ("distance", ct.POINTER(ct.c_double)),
+                ("n_elements", ct.c_int), ("elements", ct.POINTER(Element)), ("flags", ct.c_int)]
+
+
 class LyotItem(ct.Structure):
     _fields_ = [("m_occ", ct.c_int), ("du_occ", ct.c_double), ("spot_radius", ct.c_double),
                 ("du_det", ct.c_double), ("dh_in", ct.c_double), ("dh_out", ct.c_double)]
@@ -98,6 +105,8 @@ _SIGS = {
     "coro_propagate_fresnel": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_double, ct.c_int]),
     "coro_fft2": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_int]),
     "coro_fresnel_plan_create": (ct.c_int, [_P, ct.POINTER(FresnelDesc), ct.POINTER(_P)]),
+    "coro_fresnel_system_create": (ct.c_int, [_P, ct.POINTER(FresnelSystemDesc), ct.POINTER(_P)]),
+    "coro_fresnel_system_info": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "coro_fresnel_plan_execute": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double)]),
     "coro_plan_launch_count": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "coro_fresnel_plan_execute_range": (ct.c_int, [_P, _P, ct.c_int, ct.c_int]),
@@ -540,3 +549,41 @@ class FresnelPlan:
             self.close()
         except Exception:
             pass
+
+
+class FresnelSystem(FresnelPlan):
+    """Fresnel system with the propagation method chosen by a Gaussian pilot beam
+    (coro_fresnel_system_create): lenses refocus the pilot beam, planes within its Rayleigh
+    range use angular-spectrum hops, others direct hops with spherical references."""
+
+    def __init__(self, ctx: Context, *, n: int, batch: int, pixelscale, wavelength, beam_radius: float,
+                 distances, elements: Sequence[Element], dtype: int = C64, init_uniform: bool = False):
+        self.ctx = ctx
+        self.batch = batch
+        self.n = n
+        self.n_planes = len(distances) + 1
+        d = FresnelSystemDesc()
+        d.dtype, d.batch, d.n = dtype, batch, n
+        self._ps = _dbl(np.broadcast_to(np.asarray(pixelscale, float), (batch,)))
+        self._lam = _dbl(np.broadcast_to(np.asarray(wavelength, float), (batch,)))
+        d.pixelscale, d.wavelength = self._ps, self._lam
+        d.beam_radius = float(beam_radius)
+        d.n_planes = self.n_planes
+        self._dist = _dbl(distances) if len(distances) else None
+        d.distance = self._dist
+        self._els = (Element * max(1, len(elements)))(*elements)
+        self._keep = list(elements)
+        d.n_elements = len(elements)
+        d.elements = self._els
+        d.flags = PLAN_INIT_UNIFORM if init_uniform else 0
+        h = ct.c_void_p()
+        ctx.lib.check(ctx.lib.coro_fresnel_system_create(ctx.handle, ct.byref(d), ct.byref(h)))
+        self.handle = h
+        ctx._track(self)
+
+    def info(self) -> tuple[list[bool], int]:
+        """(per plane: spherical reference?, number of direct sub-hops)."""
+        sph = (ct.c_int * self.n_planes)()
+        nd = ct.c_int()
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_system_info(self.handle, sph, ct.byref(nd)))
+        return [bool(v) for v in sph], nd.value

@@ -4,6 +4,8 @@
 // launches.
 #include <cuda_runtime.h>
 
+#include <complex>
+
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -445,6 +447,7 @@ coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int
 DevElem checker_elem() { DevElem e; std::memset(&e, 0, sizeof(e)); e.kind = DK_CHECKER; return e; }
 
 DevElem table_elem(const void* tab) { DevElem e; std::memset(&e, 0, sizeof(e)); e.kind = DK_TABLE; e.tab = tab; return e; }
+DevElem conj_elem() { DevElem e; std::memset(&e, 0, sizeof(e)); e.kind = DK_CONJ; return e; }
 
 // ------------------------------------------------------------------------------ pass ops
 
@@ -512,33 +515,41 @@ coro_status run_ops_any(coro_ctx ctx, int dtype, int n, int batch, const std::ve
 
 // Angular-spectrum transfer function per axis, 1/n folded in (1/n^2 overall for the IDFT).
 coro_status as_table(DevBlocks& db, bool dbl, int n, int batch, const double* ps, const double* lam,
-                     double z, const void** out) {
+                     const double* z, const void** out) {
     coro_status st = CORO_OK;
     std::vector<TabSpec> sp(batch);
     for (int b = 0; b < batch; ++b) {
         const double L = n * ps[b];
-        sp[b] = TabSpec{lam[b] * z / (2.0 * L * L), 1.0 / n, 0.0, -1, 0};
+        sp[b] = TabSpec{lam[b] * z[b] / (2.0 * L * L), 1.0 / n, 0.0, -1, 0};
     }
     *out = make_table(db, dbl, n, sp, &st);
     return *out ? CORO_OK : st;
 }
 
 // Direct Fresnel: input QPF exp(+i pi x^2/(lambda z)); output QPF with (-1)^k folded in, the
-// y-table also carrying dx^2 / (i lambda z).
+// y-table also carrying dx^2 / (i lambda z); output pitch |lambda z / (n dx)|. qin / qout
+// drop the input or output QPF (hops from or to a waist in the pilot-beam scheme). For z < 0
+// the kernel exp(-2 pi i x u / (lambda z)) is the inverse DFT on the grid u_k = (k - n/2)|du|;
+// it is computed as conj(DFT(conj(.))): the tables returned are then the conjugates of the
+// input QPF and of the output factor, and the caller conjugates the field before the row FFT
+// and after the column pass (the next row pass).
 coro_status direct_tables(DevBlocks& db, bool dbl, int n, int batch, const double* ps, const double* lam,
-                          double z, const void** qin, const void** qx, const void** qy, std::vector<double>& ps_out) {
+                          const double* z, bool qin_on, bool qout_on, const void** qin, const void** qx,
+                          const void** qy, std::vector<double>& ps_out) {
     coro_status st = CORO_OK;
     std::vector<TabSpec> a(batch), bx(batch), by(batch);
     ps_out.resize(batch);
     for (int b = 0; b < batch; ++b) {
-        const double dx = ps[b];
-        const double du = lam[b] * z / (n * dx);
-        ps_out[b] = std::fabs(du);
-        a[b] = TabSpec{dx * dx / (2.0 * lam[b] * z), 1.0, 0.0, +1, 0};
-        bx[b] = TabSpec{du * du / (2.0 * lam[b] * z), 1.0, 0.0, +1, 1};
-        by[b] = TabSpec{du * du / (2.0 * lam[b] * z), 0.0, -dx * dx / (lam[b] * z), +1, 1};
+        const double dx = ps[b], zb = z[b];
+        const double du = std::fabs(lam[b] * zb / (n * dx));
+        const int cj = zb < 0 ? -1 : 1;                          // conjugate every table for z < 0
+        ps_out[b] = du;
+        a[b] = TabSpec{qin_on ? dx * dx / (2.0 * lam[b] * zb) : 0.0, 1.0, 0.0, +cj, 0};
+        bx[b] = TabSpec{qout_on ? du * du / (2.0 * lam[b] * zb) : 0.0, 1.0, 0.0, +cj, 1};
+        by[b] = TabSpec{qout_on ? du * du / (2.0 * lam[b] * zb) : 0.0, 0.0, -cj * dx * dx / (lam[b] * zb), +cj, 1};
     }
-    if (!(*qin = make_table(db, dbl, n, a, &st))) return st;
+    *qin = nullptr;
+    if (qin_on && !(*qin = make_table(db, dbl, n, a, &st))) return st;
     if (!(*qx = make_table(db, dbl, n, bx, &st))) return st;
     if (!(*qy = make_table(db, dbl, n, by, &st))) return st;
     return CORO_OK;
@@ -611,9 +622,10 @@ extern "C" coro_status coro_propagate_fresnel(coro_ctx ctx, coro_wavefront* wf, 
     db.ctx = ctx;
     std::vector<Op> ops;
     std::vector<double> ps_out;
+    const std::vector<double> zb(batch, z);
     if (method == CORO_FRESNEL_AS) {
         const void* h = nullptr;
-        st = as_table(db, dbl, n, batch, wf->pixelscale, wf->wavelength, z, &h);
+        st = as_table(db, dbl, n, batch, wf->pixelscale, wf->wavelength, zb.data(), &h);
         if (st == CORO_OK) {
             Op r0; r0.row = true; r0.row_flags = RF_FWD_AFTER; r0.elems.count = 1; r0.elems.e[0] = checker_elem();
             Op c; c.row = false; c.col_flags = CF_FWD | CF_TABLE | CF_INV; c.tab_x = h; c.tab_y = h;
@@ -622,12 +634,18 @@ extern "C" coro_status coro_propagate_fresnel(coro_ctx ctx, coro_wavefront* wf, 
         }
     } else {
         const void *qin = nullptr, *qx = nullptr, *qy = nullptr;
-        st = direct_tables(db, dbl, n, batch, wf->pixelscale, wf->wavelength, z, &qin, &qx, &qy, ps_out);
+        st = direct_tables(db, dbl, n, batch, wf->pixelscale, wf->wavelength, zb.data(), true, true, &qin, &qx, &qy, ps_out);
         if (st == CORO_OK) {
-            Op r0; r0.row = true; r0.row_flags = RF_FWD_AFTER; r0.elems.count = 2;
-            r0.elems.e[0] = table_elem(qin); r0.elems.e[1] = checker_elem();
+            Op r0; r0.row = true; r0.row_flags = RF_FWD_AFTER;
+            if (z < 0) r0.elems.e[r0.elems.count++] = conj_elem();
+            r0.elems.e[r0.elems.count++] = table_elem(qin);
+            r0.elems.e[r0.elems.count++] = checker_elem();
             Op c; c.row = false; c.col_flags = CF_FWD | CF_TABLE; c.tab_x = qx; c.tab_y = qy;
             ops = {r0, c};
+            if (z < 0) {                                      // undo the conjugation of the output
+                Op r1; r1.row = true; r1.elems.count = 1; r1.elems.e[0] = conj_elem();
+                ops.push_back(r1);
+            }
         }
     }
     if (st == CORO_OK) st = run_ops_any(ctx, wf->dtype, n, batch, ops, wf->data);
@@ -747,6 +765,8 @@ struct FresnelPlan : coro_plan_s {
     DevBlocks db;
     std::vector<double> ps_final;
     std::vector<std::string> tune_log;
+    std::vector<int> sys_spherical;    // pilot-beam plans: per user plane, 1 = spherical reference
+    int sys_direct = -1;               // pilot-beam plans: direct sub-hops (-1: not a system plan)
     int kind() const override { return 1; }
     int launches() const override { return (int)ops.size(); }
     int timing_units() const override { return (int)ops.size(); }
@@ -758,6 +778,140 @@ struct FresnelPlan : coro_plan_s {
         db.release();
     }
 };
+
+}  // namespace
+
+namespace {
+
+// A hop between consecutive planes of a plan: method and per-item signed distance; direct
+// hops may omit the input or output quadratic phase (pilot-beam scheme, waist planes).
+struct HopSpec {
+    int method = CORO_FRESNEL_AS;
+    std::vector<double> z;
+    bool qin = true, qout = true;
+};
+// A plane: user elements, then optional per-item quadratic phases exp(i pi r^2 c_b / lambda_b)
+// (curvature c_b in 1/m; reference-surface changes and lenses of the pilot-beam scheme).
+struct PlaneSpec {
+    std::vector<const coro_element*> user;
+    std::vector<std::vector<double>> qpf;
+};
+
+// exp(i pi r^2 c_b / lambda_b) on the plane's grid as a separable table element.
+coro_status qpf_elem(DevBlocks& db, bool dbl, int n, int batch, const double* ps, const double* lam,
+                     const std::vector<double>& c, DevElem* out) {
+    coro_status st = CORO_OK;
+    std::vector<TabSpec> sp(batch);
+    for (int b = 0; b < batch; ++b) sp[b] = TabSpec{ps[b] * ps[b] * c[b] / (2.0 * lam[b]), 1.0, 0.0, +1, 0};
+    *out = table_elem(make_table(db, dbl, n, sp, &st));
+    return out->tab ? CORO_OK : st;
+}
+
+// Compile planes and hops into row / column passes (the fused pass scheduler shared by the
+// explicit and the pilot-beam plan builders).
+coro_status build_passes(FresnelPlan* plan, int n, int batch, const double* ps0, const double* lam,
+                         const std::vector<PlaneSpec>& planes, const std::vector<HopSpec>& hops, int flags) {
+    coro_status st = CORO_OK;
+    const bool dbl = plan->dtype == CORO_C128;
+    std::vector<double> ps(ps0, ps0 + batch);
+    enum { NATURAL, UNIFORM, SPECTRUM } state = (flags & CORO_PLAN_INIT_UNIFORM) ? UNIFORM : NATURAL;
+    bool conj_pending = false;                 // the stored field is the conjugate of the true one
+    const int n_planes = (int)planes.size();
+    for (int p = 0; p < n_planes; ++p) {
+        PassElems pe{};
+        auto push = [&](const DevElem& e) -> bool {
+            if (pe.count >= kMaxPassElems - 3) {
+                set_error("plane %d: more than %d elements", p, kMaxPassElems - 3);
+                return false;
+            }
+            pe.e[pe.count++] = e;
+            return true;
+        };
+        if (conj_pending) {
+            if (!push(conj_elem())) return CORO_ENOTIMPL;
+            conj_pending = false;
+        }
+        for (const coro_element* el : planes[p].user) {
+            DevElem e;
+            if ((st = compile_element(plan->db, el, dbl, n, batch, ps.data(), lam, &e)) != CORO_OK) return st;
+            if (!push(e)) return CORO_ENOTIMPL;
+        }
+        for (const auto& c : planes[p].qpf) {
+            DevElem e;
+            if ((st = qpf_elem(plan->db, dbl, n, batch, ps.data(), lam, c, &e)) != CORO_OK) return st;
+            if (!push(e)) return CORO_ENOTIMPL;
+        }
+        Op r;
+        r.row = true;
+        r.elems = pe;
+        if (state == SPECTRUM) r.row_flags |= RF_INV_FIRST;
+        if (state == UNIFORM) r.row_flags |= RF_INIT_ONE;
+        if (p + 1 < n_planes) {
+            const HopSpec& h = hops[p];
+            r.row_flags |= RF_FWD_AFTER;
+            Op c;
+            c.row = false;
+            if (h.method == CORO_FRESNEL_AS) {
+                const void* tab = nullptr;
+                if ((st = as_table(plan->db, dbl, n, batch, ps.data(), lam, h.z.data(), &tab)) != CORO_OK) return st;
+                if (state != SPECTRUM) r.elems.e[r.elems.count++] = checker_elem();
+                c.col_flags = CF_FWD | CF_TABLE | CF_INV;
+                c.tab_x = c.tab_y = tab;
+                state = SPECTRUM;
+            } else {
+                const bool neg = h.z[0] < 0;
+                for (int b = 1; b < batch; ++b)
+                    if ((h.z[b] < 0) != neg) { set_error("hop %d: items disagree on the direction of a direct hop", p); return CORO_ENOTIMPL; }
+                const void *qin = nullptr, *qx = nullptr, *qy = nullptr;
+                std::vector<double> ps_next;
+                if ((st = direct_tables(plan->db, dbl, n, batch, ps.data(), lam, h.z.data(), h.qin, h.qout, &qin, &qx, &qy,
+                                        ps_next)) != CORO_OK)
+                    return st;
+                if (neg) r.elems.e[r.elems.count++] = conj_elem();
+                if (qin) r.elems.e[r.elems.count++] = table_elem(qin);
+                if (state != SPECTRUM) r.elems.e[r.elems.count++] = checker_elem();
+                c.col_flags = CF_FWD | CF_TABLE;
+                c.tab_x = qx;
+                c.tab_y = qy;
+                ps = ps_next;
+                state = NATURAL;
+                conj_pending = neg;
+            }
+            plan->ops.push_back(r);
+            plan->ops.push_back(c);
+        } else {
+            if (state == SPECTRUM) r.elems.e[r.elems.count++] = checker_elem();
+            if (r.row_flags || r.elems.count) plan->ops.push_back(r);
+            state = NATURAL;
+        }
+    }
+    plan->ps_final = ps;
+    return CORO_OK;
+}
+
+coro_status finish_plan(coro_ctx ctx, std::unique_ptr<FresnelPlan>& plan, coro_plan* out, const char* who) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);   // tables ready; plan owns them
+    if (e == cudaSuccess) {
+        autotune_ops(ctx, plan->dtype, plan->n, plan->batch, plan->ops, &plan->tune_log);
+        e = cudaStreamSynchronize(ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    *out = plan.release();
+    return CORO_OK;
+}
+
+std::unique_ptr<FresnelPlan> new_plan(coro_ctx ctx, int dtype, int n, int batch) {
+    auto plan = std::unique_ptr<FresnelPlan>(new (std::nothrow) FresnelPlan);
+    if (!plan) return plan;
+    plan->ctx = ctx;
+    plan->device = ctx->device;
+    plan->dtype = dtype;
+    plan->n = n;
+    plan->batch = batch;
+    plan->db.ctx = ctx;
+    plan->db.plan_owned = true;
+    return plan;
+}
 
 }  // namespace
 
@@ -780,76 +934,151 @@ extern "C" coro_status coro_fresnel_plan_create(coro_ctx ctx, const coro_fresnel
         if (d->elements[i].plane < 0 || d->elements[i].plane >= d->n_planes) { set_error("element %d: plane %d out of range", i, d->elements[i].plane); return CORO_EINVAL; }
 
     DeviceGuard g(ctx->device);
-    auto plan = std::unique_ptr<FresnelPlan>(new (std::nothrow) FresnelPlan);
+    auto plan = new_plan(ctx, d->dtype, d->n, d->batch);
     if (!plan) { set_error("out of host memory"); return CORO_ENOMEM; }
-    plan->ctx = ctx;
-    plan->device = ctx->device;
-    plan->dtype = d->dtype;
-    plan->n = d->n;
-    plan->batch = d->batch;
-    plan->db.ctx = ctx;
-    plan->db.plan_owned = true;
-    const bool dbl = d->dtype == CORO_C128;
-    const int n = d->n, batch = d->batch;
-    std::vector<double> ps(d->pixelscale, d->pixelscale + batch);
-    const double* lam = d->wavelength;
+    std::vector<PlaneSpec> planes(d->n_planes);
+    std::vector<HopSpec> hops(d->n_planes > 0 ? d->n_planes - 1 : 0);
+    for (int i = 0; i < d->n_elements; ++i) planes[d->elements[i].plane].user.push_back(&d->elements[i]);
+    for (int p = 0; p + 1 < d->n_planes; ++p) {
+        hops[p].method = d->method ? d->method[p] : CORO_FRESNEL_AS;
+        hops[p].z.assign(d->batch, d->distance[p]);
+    }
+    if ((st = build_passes(plan.get(), d->n, d->batch, d->pixelscale, d->wavelength, planes, hops, d->flags)) != CORO_OK)
+        return st;
+    return finish_plan(ctx, plan, out, "coro_fresnel_plan_create");
+}
 
-    enum { NATURAL, UNIFORM, SPECTRUM } state = (d->flags & CORO_PLAN_INIT_UNIFORM) ? UNIFORM : NATURAL;
+// ------------------------------------------------------------------------------ f2: pilot beam
+
+extern "C" coro_status coro_fresnel_system_create(coro_ctx ctx, const coro_fresnel_system_desc* d, coro_plan* out) {
+    clear_error();
+    if (!ctx || !d || !out) { set_error("coro_fresnel_system_create: NULL argument"); return CORO_EINVAL; }
+    *out = nullptr;
+    coro_wavefront probe{(void*)1, d->dtype, d->batch, d->n, const_cast<double*>(d->pixelscale), d->wavelength};
+    coro_status st = check_wf("coro_fresnel_system_create", ctx, &probe);
+    if (st != CORO_OK) return st;
+    if (!(d->beam_radius > 0) || !std::isfinite(d->beam_radius)) { set_error("coro_fresnel_system_create: beam_radius must be > 0"); return CORO_EINVAL; }
+    if (d->n_planes < 1) { set_error("coro_fresnel_system_create: n_planes must be >= 1"); return CORO_EINVAL; }
+    if (d->n_planes > 1 && !d->distance) { set_error("coro_fresnel_system_create: distance is NULL"); return CORO_EINVAL; }
+    if (d->n_elements < 0 || (d->n_elements > 0 && !d->elements)) { set_error("coro_fresnel_system_create: bad element list"); return CORO_EINVAL; }
+    for (int p = 0; p + 1 < d->n_planes; ++p)
+        if (!(d->distance[p] != 0.0) || !std::isfinite(d->distance[p])) { set_error("distance[%d] must be finite and nonzero", p); return CORO_EINVAL; }
+    for (int i = 0; i < d->n_elements; ++i) {
+        const coro_element& el = d->elements[i];
+        if (el.plane < 0 || el.plane >= d->n_planes) { set_error("element %d: plane %d out of range", i, el.plane); return CORO_EINVAL; }
+        if (el.kind == CORO_EL_LENS && (el.focal_length == 0 || !std::isfinite(el.focal_length))) {
+            set_error("element %d: lens focal length must be finite and nonzero", i);
+            return CORO_EINVAL;
+        }
+    }
+    const int B = d->batch;
+    // pilot beam per item: q = z - z_waist - i z_R (the sign convention of the Fresnel kernel
+    // exp(+i pi r^2/(lambda z)): a Gaussian exp(i pi r^2/(lambda q)) stays Gaussian)
+    std::vector<std::complex<double>> q(B);
+    for (int b = 0; b < B; ++b) q[b] = std::complex<double>(0.0, -M_PI * d->beam_radius * d->beam_radius / d->wavelength[b]);
+    auto inside = [](std::complex<double> v) { return std::fabs(v.real()) < std::fabs(v.imag()); };
+    auto agree = [&](const std::vector<std::complex<double>>& v, bool* in) -> bool {
+        *in = inside(v[0]);
+        for (int b = 1; b < B; ++b)
+            if (inside(v[b]) != *in) return false;
+        return true;
+    };
+    std::vector<PlaneSpec> planes;
+    std::vector<HopSpec> hops;
+    std::vector<int> spherical(d->n_planes, 0);
+    int direct = 0;
+    bool sph = false;                           // current plane: spherical reference (R = Re q)
     for (int p = 0; p < d->n_planes; ++p) {
-        PassElems pe{};
+        PlaneSpec ps;
+        std::vector<double> curv(B, 0.0);
+        bool lens = false;
         for (int i = 0; i < d->n_elements; ++i) {
-            if (d->elements[i].plane != p) continue;
-            if (pe.count >= kMaxPassElems - 2) { set_error("plane %d: more than %d elements", p, kMaxPassElems - 2); return CORO_ENOTIMPL; }
-            st = compile_element(plan->db, &d->elements[i], dbl, n, batch, ps.data(), lam, &pe.e[pe.count]);
-            if (st != CORO_OK) return st;
-            ++pe.count;
-        }
-        Op r;
-        r.row = true;
-        r.elems = pe;
-        if (state == SPECTRUM) r.row_flags |= RF_INV_FIRST;
-        if (state == UNIFORM) r.row_flags |= RF_INIT_ONE;
-        if (p + 1 < d->n_planes) {
-            const int m = d->method ? d->method[p] : CORO_FRESNEL_AS;
-            const double z = d->distance[p];
-            r.row_flags |= RF_FWD_AFTER;
-            Op c;
-            c.row = false;
-            if (m == CORO_FRESNEL_AS) {
-                const void* h = nullptr;
-                if ((st = as_table(plan->db, dbl, n, batch, ps.data(), lam, z, &h)) != CORO_OK) return st;
-                if (state != SPECTRUM) r.elems.e[r.elems.count++] = checker_elem();
-                c.col_flags = CF_FWD | CF_TABLE | CF_INV;
-                c.tab_x = c.tab_y = h;
-                state = SPECTRUM;
-            } else {
-                const void *qin = nullptr, *qx = nullptr, *qy = nullptr;
-                std::vector<double> ps_next;
-                if ((st = direct_tables(plan->db, dbl, n, batch, ps.data(), lam, z, &qin, &qx, &qy, ps_next)) != CORO_OK) return st;
-                r.elems.e[r.elems.count++] = table_elem(qin);
-                if (state != SPECTRUM) r.elems.e[r.elems.count++] = checker_elem();
-                c.col_flags = CF_FWD | CF_TABLE;
-                c.tab_x = qx;
-                c.tab_y = qy;
-                ps = ps_next;
-                state = NATURAL;
+            const coro_element& el = d->elements[i];
+            if (el.plane != p) continue;
+            if (el.kind != CORO_EL_LENS) { ps.user.push_back(&el); continue; }
+            if (!lens && sph)                   // restore the true field: x exp(+i pi r^2/(lambda R))
+                for (int b = 0; b < B; ++b) curv[b] += 1.0 / q[b].real();
+            lens = true;
+            for (int b = 0; b < B; ++b) {
+                curv[b] -= 1.0 / el.focal_length;
+                q[b] = 1.0 / (1.0 / q[b] - 1.0 / el.focal_length);
             }
-            plan->ops.push_back(r);
-            plan->ops.push_back(c);
-        } else {
-            if (state == SPECTRUM) r.elems.e[r.elems.count++] = checker_elem();
-            if (r.row_flags || r.elems.count) plan->ops.push_back(r);
-            state = NATURAL;
         }
+        if (lens) {
+            bool in = true;
+            if (!agree(q, &in)) { set_error("plane %d: items disagree on the pilot-beam regime after the lens", p); return CORO_ENOTIMPL; }
+            sph = !in;
+            if (sph)
+                for (int b = 0; b < B; ++b) curv[b] -= 1.0 / q[b].real();
+        }
+        if (p + 1 == d->n_planes && sph) {      // hand back the true field on a planar reference
+            if (!lens) std::fill(curv.begin(), curv.end(), 0.0);
+            for (int b = 0; b < B; ++b) curv[b] += 1.0 / q[b].real();
+            lens = true;
+        }
+        spherical[p] = sph ? 1 : 0;
+        bool any = false;
+        for (double c : curv) any = any || c != 0.0;
+        if (lens && any) ps.qpf.push_back(curv);
+        planes.push_back(ps);
+        if (p + 1 == d->n_planes) break;
+        // hop to plane p + 1
+        const double dz = d->distance[p];
+        std::vector<std::complex<double>> qb(B);
+        for (int b = 0; b < B; ++b) qb[b] = q[b] + dz;
+        bool in_a = !sph, in_b = true;
+        if (!agree(qb, &in_b)) { set_error("hop %d: items disagree on the pilot-beam regime", p); return CORO_ENOTIMPL; }
+        auto add_hop = [&](int method, std::vector<double> z, bool qin, bool qout) {
+            HopSpec h;
+            h.method = method;
+            h.z = std::move(z);
+            h.qin = qin;
+            h.qout = qout;
+            hops.push_back(h);
+            if (method == CORO_FRESNEL_DIRECT) ++direct;
+        };
+        std::vector<double> to_waist(B), from_waist(B), whole(B, dz);
+        bool zero_to = true, zero_from = true;
+        for (int b = 0; b < B; ++b) {
+            to_waist[b] = -q[b].real();
+            from_waist[b] = qb[b].real();
+            zero_to = zero_to && to_waist[b] == 0.0;
+            zero_from = zero_from && from_waist[b] == 0.0;
+        }
+        if (in_a && in_b) {
+            add_hop(CORO_FRESNEL_AS, whole, true, true);
+        } else if (in_a) {                      // inside -> outside: to the waist, then WTS
+            if (!zero_to) { add_hop(CORO_FRESNEL_AS, to_waist, true, true); planes.push_back(PlaneSpec{}); }
+            add_hop(CORO_FRESNEL_DIRECT, from_waist, true, false);
+        } else if (in_b) {                      // outside -> inside: STW, then from the waist
+            add_hop(CORO_FRESNEL_DIRECT, to_waist, false, true);
+            if (!zero_from) { planes.push_back(PlaneSpec{}); add_hop(CORO_FRESNEL_AS, from_waist, true, true); }
+        } else {                                // outside -> outside through the waist
+            add_hop(CORO_FRESNEL_DIRECT, to_waist, false, true);
+            planes.push_back(PlaneSpec{});
+            add_hop(CORO_FRESNEL_DIRECT, from_waist, true, false);
+        }
+        for (int b = 0; b < B; ++b) q[b] = qb[b];
+        sph = !in_b;
     }
-    plan->ps_final = ps;
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);   // tables ready; plan owns them
-    if (e == cudaSuccess) {
-        autotune_ops(ctx, d->dtype, n, batch, plan->ops, &plan->tune_log);
-        e = cudaStreamSynchronize(ctx->stream);
+    DeviceGuard g(ctx->device);
+    auto plan = new_plan(ctx, d->dtype, d->n, B);
+    if (!plan) { set_error("out of host memory"); return CORO_ENOMEM; }
+    plan->sys_spherical = spherical;
+    plan->sys_direct = direct;
+    if ((st = build_passes(plan.get(), d->n, B, d->pixelscale, d->wavelength, planes, hops, d->flags)) != CORO_OK) return st;
+    return finish_plan(ctx, plan, out, "coro_fresnel_system_create");
+}
+
+extern "C" coro_status coro_fresnel_system_info(coro_plan plan, int* spherical, int* direct_hops) {
+    clear_error();
+    if (!plan || plan->kind() != 1 || static_cast<FresnelPlan*>(plan)->sys_direct < 0) {
+        set_error("coro_fresnel_system_info: not a plan made by coro_fresnel_system_create");
+        return CORO_EINVAL;
     }
-    if (e != cudaSuccess) return cuda_fail(e, "coro_fresnel_plan_create");
-    *out = plan.release();
+    auto* p = static_cast<FresnelPlan*>(plan);
+    if (spherical) std::copy(p->sys_spherical.begin(), p->sys_spherical.end(), spherical);
+    if (direct_hops) *direct_hops = p->sys_direct;
     return CORO_OK;
 }
 

@@ -25,7 +25,8 @@ enum DevElemKind : int {
     DK_ZERNIKE = 5,    // ithr: [r2 max]; fpar: [2 / lambda, dx/R]; zpoly: combined polynomials
     DK_SINE = 6,       // fpar: [2 amp / lambda, f_hi, f_lo] (cycles per pixel split), flags: axis
     DK_SCALAR = 7,     // fpar: [s]
-    DK_CHECKER = 8     // (-1)^(x+y)
+    DK_CHECKER = 8,    // (-1)^(x+y)
+    DK_CONJ = 9        // complex conjugate (direct hops with z < 0: IDFT(y) = conj(DFT(conj y)))
 };
 
 // Zernike evaluation table: OPD = sum_{m=0}^{ZM-1} A_m(rho^2) Re(z^m) + B_m(rho^2) Im(z^m),
@@ -45,7 +46,7 @@ struct DevElem {
     const float* zpoly;       // [2][ZM][ZD]
 };
 
-constexpr int kMaxPassElems = 6;
+constexpr int kMaxPassElems = 8;   // up to 5 user / plane elements + conj, input QPF, checker
 
 struct PassElems {
     int count;
@@ -189,6 +190,11 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
 #pragma unroll
                 for (int s = 0; s < 16; ++s)
                     if ((x0 + s * XS + y) & 1) v[s] = mk<C>(-v[s].x, -v[s].y);
+                break;
+            }
+            case DK_CONJ: {
+#pragma unroll
+                for (int s = 0; s < 16; ++s) v[s] = cconj(v[s]);
                 break;
             }
             default:
@@ -346,6 +352,12 @@ __device__ __forceinline__ void apply_elems_pair(pk::CP (&v)[16], int x0, int ya
                     const u64 m = pk::pack(sa, -sa);        // rows ya and ya + 1 have opposite parity
                     v[s] = CP{pk::mul2(v[s].re, m), pk::mul2(v[s].im, m)};
                 }
+                break;
+            }
+            case DK_CONJ: {
+                const u64 m = pk::pack(-1.f, -1.f);
+#pragma unroll
+                for (int s = 0; s < 16; ++s) v[s].im = pk::mul2(v[s].im, m);
                 break;
             }
             default:
