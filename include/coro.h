@@ -218,6 +218,10 @@ coro_status coro_fresnel_system_create(coro_ctx ctx, const coro_fresnel_system_d
  * receives 1 for planes outside the pilot beam's Rayleigh range, *direct_hops the number of
  * direct sub-hops. */
 coro_status coro_fresnel_system_info(coro_plan plan, int* spherical, int* direct_hops);
+/* pitch (host [batch]): the pixel scale (metres) at which plane `plane`'s elements act, per
+ * item -- for masks generated on the host at planes whose sampling the plan chose (a focal
+ * plane mask behind a direct hop). Works for any Fresnel plan. */
+coro_status coro_fresnel_system_pitch(coro_plan plan, int plane, double* pitch);
 
 /* Run the plan in place on `field` (device, [batch][n][n]). pixelscale_out (host [batch], may
  * be NULL) receives the final pixel scale. */

@@ -107,6 +107,7 @@ _SIGS = {
     "coro_fresnel_plan_create": (ct.c_int, [_P, ct.POINTER(FresnelDesc), ct.POINTER(_P)]),
     "coro_fresnel_system_create": (ct.c_int, [_P, ct.POINTER(FresnelSystemDesc), ct.POINTER(_P)]),
     "coro_fresnel_system_info": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "coro_fresnel_system_pitch": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_double)]),
     "coro_fresnel_plan_execute": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double)]),
     "coro_plan_launch_count": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "coro_fresnel_plan_execute_range": (ct.c_int, [_P, _P, ct.c_int, ct.c_int]),
@@ -502,6 +503,12 @@ class FresnelPlan:
     @property
     def timing_units(self) -> int:
         return self.launch_count
+
+    def plane_pitch(self, plane: int) -> np.ndarray:
+        """Per-item pixel scale at which plane `plane`'s elements act."""
+        buf = (ct.c_double * self.batch)()
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_system_pitch(self.handle, plane, buf))
+        return np.array(buf[:])
 
     def execute_n(self, field, times: int):
         """`times` executes back to back (coro_fresnel_plan_execute_n)."""

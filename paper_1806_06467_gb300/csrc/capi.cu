@@ -767,6 +767,8 @@ struct FresnelPlan : coro_plan_s {
     std::vector<std::string> tune_log;
     std::vector<int> sys_spherical;    // pilot-beam plans: per user plane, 1 = spherical reference
     int sys_direct = -1;               // pilot-beam plans: direct sub-hops (-1: not a system plan)
+    std::vector<std::vector<double>> plane_pitch;   // per compiled plane: per-item pixel scale
+    std::vector<int> user_plane;                    // pilot-beam plans: compiled index of user plane p
     int kind() const override { return 1; }
     int launches() const override { return (int)ops.size(); }
     int timing_units() const override { return (int)ops.size(); }
@@ -817,7 +819,9 @@ coro_status build_passes(FresnelPlan* plan, int n, int batch, const double* ps0,
     enum { NATURAL, UNIFORM, SPECTRUM } state = (flags & CORO_PLAN_INIT_UNIFORM) ? UNIFORM : NATURAL;
     bool conj_pending = false;                 // the stored field is the conjugate of the true one
     const int n_planes = (int)planes.size();
+    plan->plane_pitch.assign(n_planes, std::vector<double>());
     for (int p = 0; p < n_planes; ++p) {
+        plan->plane_pitch[p] = ps;
         PassElems pe{};
         auto push = [&](const DevElem& e) -> bool {
             if (pe.count >= kMaxPassElems - 3) {
@@ -988,7 +992,9 @@ extern "C" coro_status coro_fresnel_system_create(coro_ctx ctx, const coro_fresn
     std::vector<int> spherical(d->n_planes, 0);
     int direct = 0;
     bool sph = false;                           // current plane: spherical reference (R = Re q)
+    std::vector<int> user_plane(d->n_planes, 0);
     for (int p = 0; p < d->n_planes; ++p) {
+        user_plane[p] = (int)planes.size();
         PlaneSpec ps;
         std::vector<double> curv(B, 0.0);
         bool lens = false;
@@ -1066,8 +1072,21 @@ extern "C" coro_status coro_fresnel_system_create(coro_ctx ctx, const coro_fresn
     if (!plan) { set_error("out of host memory"); return CORO_ENOMEM; }
     plan->sys_spherical = spherical;
     plan->sys_direct = direct;
+    plan->user_plane = user_plane;
     if ((st = build_passes(plan.get(), d->n, B, d->pixelscale, d->wavelength, planes, hops, d->flags)) != CORO_OK) return st;
     return finish_plan(ctx, plan, out, "coro_fresnel_system_create");
+}
+
+extern "C" coro_status coro_fresnel_system_pitch(coro_plan plan, int plane, double* pitch) {
+    clear_error();
+    if (!plan || plan->kind() != 1 || !pitch) { set_error("coro_fresnel_system_pitch: bad argument"); return CORO_EINVAL; }
+    auto* p = static_cast<FresnelPlan*>(plan);
+    const bool sys = p->sys_direct >= 0;
+    const int count = sys ? (int)p->user_plane.size() : (int)p->plane_pitch.size();
+    if (plane < 0 || plane >= count) { set_error("coro_fresnel_system_pitch: plane %d of %d", plane, count); return CORO_EINVAL; }
+    const std::vector<double>& v = p->plane_pitch[sys ? p->user_plane[plane] : plane];
+    std::copy(v.begin(), v.end(), pitch);
+    return CORO_OK;
 }
 
 extern "C" coro_status coro_fresnel_system_info(coro_plan plan, int* spherical, int* direct_hops) {

@@ -22,6 +22,12 @@ are not available, so inputs of the same shape stand in for it):
                      to the 1024^2 Lyot plane (stop 80 % of D), MFT to 512^2 at 0.25 lambda/D.
 * ``broadband``   -- the Lyot system at 21 wavelengths over 500-600 nm x 8 DM probes.
 * ``wfc``         -- two 48x48 DMs 0.3 m apart (Fresnel 4096^2), Lyot chain at 11 wavelengths.
+* ``spc``         -- the shape of App. B's shaped-pupil coronagraph system: a 2.37 m f/7.8
+                     telescope, a 20 mm relay beam, four f/20 relay optics, a shaped pupil and a
+                     bow-tie focal-plane mask, nine planes through three foci. The two masks are
+                     binary amplitude maps standing in for the App. B mask files (not available):
+                     like the PSD surfaces they are inputs, generated here at a pitch the caller
+                     gives and passed to both paths.
 """
 from __future__ import annotations
 
@@ -191,6 +197,79 @@ class BroadbandWorkload:
 
     def probes(self) -> np.ndarray:
         return sinc_probes(self.n_act, self.n_probe)
+
+
+@dataclasses.dataclass
+class SpcWorkload:
+    """Optical system of App. B's shape (its prescription: primary f/7.8 of 2.37 m, a secondary
+    that collimates a 20 mm beam, f/20 relay optics); masks are stand-ins (see module doc)."""
+    npix: int = 256
+    oversample: int = 4
+    wavelength_m: float = 550e-9
+    d_prim_m: float = 2.37
+    f_ratio_prim: float = 7.8
+    d_relay_m: float = 0.02
+    f_ratio_relay: float = 20.0
+    obscuration: float = 0.3
+    n_spiders: int = 4
+    spider_width_frac: float = 0.01
+    bowtie_inner_lamd: float = 2.5
+    bowtie_outer_lamd: float = 9.0
+    bowtie_half_angle_deg: float = 32.5
+    n_rings: int = 6
+    seed: int = 0
+
+    @property
+    def n(self) -> int:
+        return self.npix * self.oversample
+
+    @property
+    def dx(self) -> float:
+        return self.d_prim_m / self.npix
+
+    @property
+    def f_pri(self) -> float:
+        return self.f_ratio_prim * self.d_prim_m
+
+    @property
+    def f_m2(self) -> float:
+        return self.f_pri * self.d_relay_m / self.d_prim_m
+
+    @property
+    def f_m3(self) -> float:
+        return self.f_ratio_relay * self.d_relay_m
+
+    def layout(self) -> list:
+        """Per plane, what sits there: ("aperture",), ("lens", f), ("shaped_pupil",), ("fpm",)."""
+        f3 = self.f_m3
+        return [[("aperture",), ("lens", self.f_pri)], [("lens", self.f_m2)], [("lens", f3)], [("lens", f3)],
+                [("shaped_pupil",)], [("lens", f3)], [("fpm",)], [("lens", f3)], []]
+
+    def distances(self) -> list:
+        f3 = self.f_m3
+        return [self.f_pri + self.f_m2, self.f_m2 + f3, 2 * f3, f3, f3, f3, 2 * f3, 2 * f3]
+
+    def shaped_pupil(self, n: int, pitch: float) -> np.ndarray:
+        """Binary concentric-ring amplitude mask over the relayed 20 mm pupil: ring edges drawn
+        from the seed, alternately open and closed, closed inside the obscuration."""
+        r_pup = 0.5 * self.d_relay_m
+        edges = np.sort(rng(self.seed + 500).uniform(self.obscuration, 1.0, 2 * self.n_rings - 1)) * r_pup
+        k = np.arange(n, dtype=np.float64) - n // 2
+        r = np.sqrt(k[None, :] ** 2 + k[:, None] ** 2) * pitch
+        zone = np.searchsorted(edges, r)                   # 0 .. 2 n_rings - 1
+        m = (zone % 2 == 0) & (r >= self.obscuration * r_pup) & (r <= r_pup)
+        return m.astype(np.float32)
+
+    def bowtie(self, n: int, pitch: float, wavelength: float) -> np.ndarray:
+        """Bow-tie focal-plane mask: open for inner <= r <= outer (lambda/D of the f/20 relay
+        beam) within +-half_angle of the x axis on both sides."""
+        lamd = wavelength * self.f_ratio_relay
+        k = np.arange(n, dtype=np.float64) - n // 2
+        x, y = k[None, :] * pitch, k[:, None] * pitch
+        r = np.hypot(x, y)
+        wedge = np.abs(y) <= np.tan(np.radians(self.bowtie_half_angle_deg)) * np.abs(x)
+        m = (r >= self.bowtie_inner_lamd * lamd) & (r <= self.bowtie_outer_lamd * lamd) & wedge
+        return m.astype(np.float32)
 
 
 def configs_summary() -> dict:

@@ -125,3 +125,69 @@ def test_pilot_system_regime_disagreement_is_rejected(ctx):
     with pytest.raises(coro.CoroError):
         coro.FresnelSystem(ctx, n=n, batch=2, pixelscale=dx, wavelength=lams, beam_radius=w0, distances=[10.0],
                            elements=[])
+
+
+def spc_elements(w, maps):
+    """GPU elements of the App.-B-shaped system; maps: dict of device tensors for the two masks."""
+    els = []
+    for p, plane in enumerate(w.layout()):
+        for el in plane:
+            if el[0] == "aperture":
+                els.append(coro.element(coro.EL_APERTURE, plane=p, radius=w.d_prim_m / 2, obscuration=w.obscuration,
+                                        n_spiders=w.n_spiders, spider_width=w.spider_width_frac * w.d_prim_m))
+            elif el[0] == "lens":
+                els.append(coro.element(coro.EL_LENS, plane=p, focal_length=el[1]))
+            else:
+                els.append(coro.element(coro.EL_OPD_MAP, plane=p, opd=maps["zero"], amplitude=maps[el[0]],
+                                        flags=coro.ELF_MAP_BATCHED))
+    return els
+
+
+def spc_oracle(w, lam, pitch_sp, pitch_fpm):
+    def ap(nn, p):
+        return optics.circular_aperture(nn, p, w.d_prim_m / 2, w.obscuration, w.n_spiders,
+                                        w.spider_width_frac * w.d_prim_m)
+
+    def sp(nn, p):
+        assert abs(p - pitch_sp) < 1e-13 * p         # the GPU plan chose the same sampling
+        return w.shaped_pupil(nn, p)
+
+    def fpm(nn, p):
+        assert abs(p - pitch_fpm) < 1e-13 * p
+        return w.bowtie(nn, p, lam)
+
+    planes = []
+    for plane in w.layout():
+        row = []
+        for el in plane:
+            row.append({"aperture": ap, "shaped_pupil": sp, "fpm": fpm}[el[0]] if el[0] != "lens" else ("lens", el[1]))
+        planes.append(row)
+    return propagation.fresnel_system_pilot(np.ones((w.n, w.n), complex), w.dx, lam, w.d_prim_m / 2, planes,
+                                            w.distances())
+
+
+def test_spc_shaped_system(ctx):
+    """Next row f1: the nine-plane system of App. B's shape (telescope, 20 mm relay, shaped
+    pupil, bow-tie focal-plane mask, three foci; seven direct legs) at two wavelengths, with
+    the masks generated at the sampling the plan chose, against the oracle."""
+    w = inputs.SpcWorkload(npix=128)
+    n, lams = w.n, np.array([545e-9, 555e-9])
+    maps = {"zero": torch.zeros((2, n, n), device="cuda"), "shaped_pupil": torch.zeros((2, n, n), device="cuda"),
+            "fpm": torch.zeros((2, n, n), device="cuda")}
+    plan = coro.FresnelSystem(ctx, n=n, batch=2, pixelscale=w.dx, wavelength=lams, beam_radius=w.d_prim_m / 2,
+                              distances=w.distances(), elements=spc_elements(w, maps), init_uniform=True)
+    p_sp, p_fpm = plan.plane_pitch(4), plan.plane_pitch(6)
+    for b, lam in enumerate(lams):
+        maps["shaped_pupil"][b] = torch.from_numpy(w.shaped_pupil(n, p_sp[b]))
+        maps["fpm"][b] = torch.from_numpy(w.bowtie(n, p_fpm[b], lam))
+    flags, legs = plan.info()
+    x = torch.empty((2, n, n), dtype=torch.complex64, device="cuda")
+    ps = plan.execute(x)
+    got = x.cpu().numpy()
+    for b, lam in enumerate(lams):
+        ref, pitch, rflags, rlegs = spc_oracle(w, lam, p_sp[b], p_fpm[b])
+        assert rflags == flags and rlegs == legs == 7
+        assert abs(ps[b] - pitch) < 1e-13 * pitch
+        err = rel_l2(got[b], ref)
+        print(f"spc item {b}: final pitch {pitch:.3e} m, rel L2 {err:.2e}")
+        assert err < 1e-5
