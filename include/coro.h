@@ -63,6 +63,12 @@ coro_status coro_ctx_destroy(coro_ctx ctx);
 coro_status coro_ctx_set_stream(coro_ctx ctx, void* stream);
 /* Block the host until the context's stream has drained; reports asynchronous faults. */
 coro_status coro_ctx_synchronize(coro_ctx ctx);
+/* Failure-path self-test (no counterpart in the paper): launches one thread that waits, for at
+ * most `polls` (1 .. 2^20) polls, on an mbarrier nothing completes. The bounded wait expires
+ * as a stalled copy or MMA would, sets the context's error flag and returns; the next
+ * coro_ctx_synchronize reports CORO_ETIMEOUT (and clears the flag), and the context stays
+ * usable. No fault, trap or hang is involved. */
+coro_status coro_selftest_wait_timeout(coro_ctx ctx, int polls);
 /* Thread-local description of the last failure ("" if none). Valid until the next call. */
 const char* coro_last_error(void);
 int coro_version(void);

@@ -114,6 +114,7 @@ _SIGS = {
     "coro_fresnel_plan_pass_info": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]),
     "coro_fresnel_plan_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "coro_fresnel_plan_set_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.c_int]),
+    "coro_selftest_wait_timeout": (ct.c_int, [_P, ct.c_int]),
     "coro_plan_set_timing": (ct.c_int, [_P, ct.c_int]),
     "coro_plan_unit_times": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_float)]),
     "coro_fresnel_plan_execute_n": (ct.c_int, [_P, _P, ct.c_int]),

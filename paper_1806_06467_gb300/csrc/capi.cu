@@ -14,6 +14,7 @@
 
 #include "capi_common.h"
 #include "passes.cuh"
+#include "tc_ptx.cuh"
 
 using namespace coro;
 
@@ -237,6 +238,26 @@ extern "C" coro_status coro_ctx_synchronize(coro_ctx ctx) {
         return CORO_ETIMEOUT;
     }
     return CORO_OK;
+}
+
+// Failure-path check: one thread waits, with a short bound, on an mbarrier that nothing will
+// ever complete, so the bounded wait expires and raises the context's error flag exactly as a
+// stalled copy or MMA would; the kernel then returns and the context stays usable.
+__global__ void wait_timeout_probe_kernel(int* err, int polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    coro::tc::mbar_init(&bar, 1);
+    coro::tc::fence_mbar_init();
+    coro::tc::mbar_wait(&bar, 0, err, 99, polls);          // phase 0 never completes
+}
+
+extern "C" coro_status coro_selftest_wait_timeout(coro_ctx ctx, int polls) {
+    clear_error();
+    if (!ctx || polls < 1 || polls > (1 << 20)) { set_error("coro_selftest_wait_timeout: bad argument"); return CORO_EINVAL; }
+    DeviceGuard g(ctx->device);
+    wait_timeout_probe_kernel<<<1, 32, 0, ctx->stream>>>(ctx->err, polls);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CORO_OK : cuda_fail(e, "wait_timeout_probe_kernel");
 }
 
 // =========================================================================== validation
