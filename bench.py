@@ -59,6 +59,20 @@ def dist_env():
     return world, rank, local
 
 
+def replica_throughput(units_per_rank: float, ms: float, world: int, device=None) -> tuple[float, float]:
+    """Replicas only: every rank runs its own system on its own GPU, with no exchange on the
+    data path. Whole-job throughput = all ranks' units / the slowest rank's time (max over
+    ranks; the only collective). Returns (units per second, max ms)."""
+    t_max = ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return units_per_rank * world / (t_max / 1e3), t_max
+
+
 # ------------------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -573,12 +587,7 @@ def main():
     per_pass = plan.unit_times(args.steps)             # [K][passes]
     clk = clocks.stop()
     total_ms = t0.elapsed_time(t1)
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = HOPS * args.steps * world / (t_max / 1e3)
+    value, t_max = replica_throughput(HOPS * args.steps, total_ms, world, device)
 
     # -------- roofline of the dominant pass kind
     kinds = {"row": [0.0, 0.0, 0, set()], "col": [0.0, 0.0, 0, set()]}
