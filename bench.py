@@ -470,6 +470,45 @@ def spc_system_bench(ctx, device, steps: int, npix: int = 1024) -> dict:
     return out
 
 
+def wfc_bench(ctx, device, steps: int) -> dict:
+    """Differentiable wavefront control at full size: loss and dL/dh for 2 x 48 x 48 DM heights,
+    Fresnel 4096^2 between the DMs, Lyot chain at 11 wavelengths (3xTF32); one step is one
+    forward + adjoint evaluation (each returns its loss to the host)."""
+    import numpy as np
+    import torch
+
+    from paper_1806_06467_gb300 import coro, inputs, wfc
+    w = inputs.WfcWorkload()
+    lw = w.lyot
+    lams = list(w.wavelengths())
+    plan = wfc.WfcPlan(ctx, wavelengths=lams, n_fresnel=w.n_fresnel, diam_m=w.diam_m, npix=lw.npix, z_m=w.z_m,
+                       n_act=w.n_act, pitch_m=w.pitch_m, fwhm_m=w.pitch_m, lyot_frac=lw.lyot_frac, m_det=lw.m_det,
+                       items=[w.item(l) for l in lams], precision=coro.MFT_3XTF32)
+    plan.peak()
+    h = torch.from_numpy(w.heights().astype(np.float32)).to(device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(2):
+        plan.evaluate(h)
+    torch.cuda.synchronize()
+
+    def timed(want_grad):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            plan.evaluate(h, want_grad=want_grad)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    ms = timed(True)
+    ms_fwd = timed(False)
+    plan.close()
+    return {"value": 1e3 / ms, "unit": "gradients/s", "ms_per_gradient": ms, "ms_forward_only": ms_fwd,
+            "wavelengths": len(lams), "n_fresnel": w.n_fresnel,
+            "workload": "two 48x48 DMs (+-5 nm) 0.3 m apart on a 4096^2 Fresnel grid, Lyot chain at 11 "
+                        "wavelengths 525-575 nm (3xTF32); loss + dL/dh per step"}
+
+
 def coronagraph_plain(device, steps: int, n_lambda: int = 21, n_probe: int = 8) -> dict:
     """Plain per-wavelength FP32 GPU form: torch.matmul (cuBLAS cgemm, complex64) MFT chain per
     wavelength over the 8 probe pupils, bases precomputed; same sizes as the batched plan."""
@@ -692,6 +731,7 @@ def main():
                 extras["coronagraph"]["value"] / world / extras["coronagraph"]["plain_gpu"]["value"])
     if not args.no_coronagraph:
         extras["spc_system"] = spc_system_bench(ctx, device, max(3, args.steps // 2))
+        extras["wfc_gradient"] = wfc_bench(ctx, device, max(3, args.steps // 4))
     if rank == 0 and not args.no_plain:
         extras["plain_gpu"] = plain_gpu(n, maps_np, w, max(3, args.steps // 4), 2, device)
         extras["plain_gpu"]["speedup_of_coro"] = value / world / extras["plain_gpu"]["value"]

@@ -79,6 +79,16 @@ def forward(h: np.ndarray, wavelength: float, p: WfcParams, static_opd: np.ndarr
                 mask=mask, loss=loss)
 
 
+def loss(h: np.ndarray, wavelength: float, p: WfcParams, peak: float) -> float:
+    """The loss alone (what a central difference needs), for process pools."""
+    return forward(h, wavelength, p, peak=peak)["loss"]
+
+
+def zero_height_peak(wavelength: float, p: WfcParams) -> float:
+    """The normalisation peak: the system with both DMs flat."""
+    return forward(np.zeros((2, p.n_act, p.n_act)), wavelength, p)["peak"]
+
+
 def lyot_adjoint(g_det: np.ndarray, p: coronagraph.LyotParams) -> np.ndarray:
     """Conjugate transpose of the Babinet Lyot chain: detector gradient -> pupil gradient."""
     g_d = propagation.imft(g_det, p.npix, p.n, p.du_det)              # MFT_3^H

@@ -200,6 +200,44 @@ class BroadbandWorkload:
 
 
 @dataclasses.dataclass
+class WfcWorkload:
+    """Two-DM wavefront control: 48x48 Gaussian-influence DMs (FWHM one pitch) over a 48 mm
+    pupil, DM2 0.3 m from DM1 on a Fresnel grid of n_fresnel^2, then the Lyot system at
+    n_lambda wavelengths over 525-575 nm. The focal-plane masks are fixed in lambda_c/D, so
+    each wavelength's item scales by lambda_c / lambda (uneven occulter sizes)."""
+    lyot: LyotWorkload = dataclasses.field(default_factory=LyotWorkload)
+    n_fresnel: int = 4096
+    diam_m: float = 0.048
+    z_m: float = 0.3
+    n_act: int = 48
+    act_amp_m: float = 5e-9
+    n_lambda: int = 11
+    lambda_lo_m: float = 525e-9
+    lambda_hi_m: float = 575e-9
+    lambda_c_m: float = 550e-9
+    seed: int = 0
+
+    @property
+    def pitch_m(self) -> float:
+        return self.diam_m / self.n_act
+
+    def wavelengths(self) -> np.ndarray:
+        return np.linspace(self.lambda_lo_m, self.lambda_hi_m, self.n_lambda)
+
+    def heights(self) -> np.ndarray:
+        return dm_heights(self.seed, self.n_act, 2, self.act_amp_m)
+
+    def item(self, wavelength: float) -> dict:
+        """One wavelength's Lyot item (occulter, spot, detector pitch, dark hole in lambda/D)."""
+        lw, r = self.lyot, self.lambda_c_m / wavelength
+        return dict(m_occ=int(np.rint(lw.m_occ * r)), du_occ=lw.du_occ * r, spot_radius=lw.spot_radius_lamd * r,
+                    du_det=lw.du_det * r, dh_in=lw.dh_inner * r, dh_out=lw.dh_outer * r)
+
+    def fd_actuators(self, count: int = 16) -> np.ndarray:
+        return actuator_offsets(self.seed + 11, self.n_act, count)
+
+
+@dataclasses.dataclass
 class SpcWorkload:
     """Optical system of App. B's shape (its prescription: primary f/7.8 of 2.37 m, a secondary
     that collimates a 20 mm beam, f/20 relay optics); masks are stand-ins (see module doc)."""

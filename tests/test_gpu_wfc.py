@@ -112,3 +112,91 @@ def test_wfc_forward_only_matches_gradient_pass(ctx):
     l1, per1, g = plan.evaluate(h, want_grad=True)
     assert l0 == pytest.approx(l1, rel=1e-12)
     assert torch.isfinite(g).all()
+
+
+def full_size_params(w, lam):
+    """The oracle's parameters for one wavelength of the 4096^2, 48x48-actuator workload."""
+    it = w.item(lam)
+    lw = w.lyot
+    lyot = coronagraph.LyotParams(n=lw.n, npix=lw.npix, m_occ=it["m_occ"], du_occ=it["du_occ"],
+                                  spot_radius=it["spot_radius"], lyot_frac=lw.lyot_frac, m_det=lw.m_det,
+                                  du_det=it["du_det"])
+    return adjoint.WfcParams(n_f=w.n_fresnel, npix=lw.npix, diam_m=w.diam_m, z_m=w.z_m, n_act=w.n_act, lyot=lyot,
+                             dh_in=it["dh_in"], dh_out=it["dh_out"])
+
+
+def oracle_pool():
+    """Spawned FP64 oracle workers, one BLAS thread each (about 2.5 GB per worker at 4096^2)."""
+    import multiprocessing as mp
+    import os
+    keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in keep:
+        os.environ[k] = "1"
+    try:
+        return mp.get_context("spawn").Pool(max(1, min(12, (os.cpu_count() or 2) - 2)))
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k)
+            else:
+                os.environ[k] = v
+
+
+@pytest.mark.slow
+def test_wfc_full_size_gradient(ctx):
+    """The full workload: 2 x 48 x 48 heights (uniform +-5 nm), Fresnel 4096^2 over 0.3 m,
+    Lyot chain at 11 wavelengths over 525-575 nm (3xTF32). Per-wavelength sums and the summed
+    gradient against the FP64 oracle's adjoint; then, at 550 nm alone, the GPU gradient
+    against FP64 central differences (h = 1e-3 nm) on 16 seeded actuators."""
+    w = inputs.WfcWorkload()
+    lw = w.lyot
+    lams = list(w.wavelengths())
+    h32 = w.heights().astype(np.float32).astype(np.float64)
+    ht = torch.from_numpy(h32.astype(np.float32)).cuda()
+
+    def plan_for(ls):
+        return wfc.WfcPlan(ctx, wavelengths=ls, n_fresnel=w.n_fresnel, diam_m=w.diam_m, npix=lw.npix, z_m=w.z_m,
+                           n_act=w.n_act, pitch_m=w.pitch_m, fwhm_m=w.pitch_m, lyot_frac=lw.lyot_frac,
+                           m_det=lw.m_det, items=[w.item(l) for l in ls], precision=coro.MFT_3XTF32)
+
+    plan = plan_for(lams)
+    peaks = plan.peak()
+    loss, per, grad = plan.evaluate(ht)
+    got = grad.cpu().numpy().astype(np.float64)
+    plan.close()
+    lc = w.lambda_c_m
+    plan1 = plan_for([lc])
+    _, per1, g1 = plan1.evaluate(ht)
+    got1 = g1.cpu().numpy().astype(np.float64)
+    plan1.close()
+
+    params = [full_size_params(w, l) for l in lams]
+    pc = full_size_params(w, lc)
+    picks = w.fd_actuators(16)
+    d = 1e-12
+    with oracle_pool() as pool:
+        ref_peaks = pool.starmap(adjoint.zero_height_peak, [(l, p) for l, p in zip(lams, params)])
+        pk_c = ref_peaks[lams.index(lc)] if lc in lams else adjoint.zero_height_peak(lc, pc)
+        jobs = [(h32, l, p, None, pk) for l, p, pk in zip(lams, params, ref_peaks)]
+        ref = pool.starmap(adjoint.gradient, jobs)
+        fd_jobs = []
+        for dm, r, c in picks:
+            for s in (1.0, -1.0):
+                hh = h32.copy()
+                hh[dm, r, c] += s * d
+                fd_jobs.append((hh, lc, pc, pk_c))
+        fd_loss = pool.starmap(adjoint.loss, fd_jobs)
+    np.testing.assert_allclose(peaks, ref_peaks, rtol=1e-5)
+    ref_per = np.array([r[0] for r in ref])
+    ref_grad = sum(r[1] for r in ref)
+    per_err = np.max(np.abs(per / ref_per - 1))
+    err = np.linalg.norm(got - ref_grad) / np.linalg.norm(ref_grad)
+    print(f"full-size wfc: per-wavelength dark-hole sums max rel {per_err:.3e}; gradient rel L2 {err:.3e}")
+    assert per_err < 1e-3
+    assert err < 1e-3
+    fd = (np.array(fd_loss[0::2]) - np.array(fd_loss[1::2])) / (2 * d)
+    gp = np.array([got1[dm, r, c] for dm, r, c in picks])
+    scale = np.abs(got1).max()
+    worst = np.max(np.abs(gp - fd)) / scale
+    print(f"full-size wfc at 550 nm: GPU gradient vs FP64 central differences, max |diff| / max |grad| {worst:.3e}")
+    assert worst <= 1e-3, list(zip(gp, fd))
