@@ -110,7 +110,15 @@ typedef enum {
                              * outside the disk (unit-RMS Noll normalisation)                 */
     CORO_EL_SINE = 6,     /* OPD = sine_amplitude * sin(2 pi sine_freq x) along x (axis 0) or y
                              * (axis 1) (App. A SineWaveWFE)                                   */
-    CORO_EL_SCALAR = 7    /* multiply by a real scalar (ScalarTransmission, App. B)            */
+    CORO_EL_SCALAR = 7,   /* multiply by a real scalar (ScalarTransmission, App. B)            */
+    CORO_EL_CHECKPOINT = 8 /* copy the field as it stands at this point of the plane (after the
+                             * plane's elements listed before it) to `store`, field unchanged:
+                             * per-plane wavefront checkpoints for adjoints (intermediate planes
+                             * of Sec. 1.1 systems). store: device, the wavefront's dtype,
+                             * [batch][n][n]; it must stay allocated for the plan's life and is
+                             * also written while a plan is tuned at creation. In pilot-beam
+                             * systems the copy is the field relative to the plane's reference
+                             * surface, as the plane's other elements see it.                 */
 } coro_element_kind;
 
 #define CORO_ELF_OPAQUE_INSIDE 1  /* CORO_EL_CIRCLE: block r <= radius instead of passing it */
@@ -134,6 +142,7 @@ typedef struct {
     double sine_amplitude;    /* SINE: metres                                                */
     int axis;                 /* SINE: 0 = varies along x, 1 = along y                       */
     double scalar;            /* SCALAR                                                      */
+    void* store;              /* CHECKPOINT: device destination [batch][n][n]                */
 } coro_element;
 
 /* Apply one element in place (unfused elementwise kernel). */

@@ -357,7 +357,7 @@ void noll_nm(int j, int* n_out, int* m_out) {
 double factorial(int k) { double f = 1; for (int i = 2; i <= k; ++i) f *= i; return f; }
 
 // Combined Zernike polynomial table: A_m(rho^2) multiplies Re(z^m), B_m(rho^2) Im(z^m).
-bool zernike_table(const coro_element* el, std::vector<float>& out) {
+bool zernike_table(const coro_element* el, std::vector<double>& out) {
     std::vector<double> acc(2 * ZM * ZD, 0.0);
     for (int i = 0; i < el->n_coeffs; ++i) {
         int n, m;
@@ -376,13 +376,20 @@ bool zernike_table(const coro_element* el, std::vector<float>& out) {
     return true;
 }
 
+// x = hi + lo with hi = float(x): complex64 passes use hi, complex128 passes the FP64 sum
+// (about 48 significant bits).
+void split_f32(double x, float* hi, float* lo) {
+    *hi = (float)x;
+    *lo = (float)(x - (double)*hi);
+}
+
 // Compile one API element for a batch at the given per-item pixel scales.
 coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int n, int batch,
                             const double* ps, const double* lam, DevElem* out) {
     coro_status st = CORO_OK;
     std::memset(out, 0, sizeof(DevElem));
     std::vector<int> ithr((size_t)batch * 4, 0);
-    std::vector<float> fpar((size_t)batch * 4, 0.f);
+    std::vector<float> fpar((size_t)batch * 4, 0.f);   // [batch][4]
     switch (el->kind) {
         case CORO_EL_APERTURE: {
             if (!(el->radius > 0)) { set_error("aperture: radius must be > 0"); return CORO_EINVAL; }
@@ -415,7 +422,7 @@ coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int
         }
         case CORO_EL_OPD_MAP: {
             if (!el->opd) { set_error("opd map: opd pointer is NULL"); return CORO_EINVAL; }
-            for (int b = 0; b < batch; ++b) fpar[4 * b] = (float)(2.0 / lam[b]);
+            for (int b = 0; b < batch; ++b) split_f32(2.0 / lam[b], &fpar[4 * b], &fpar[4 * b + 1]);
             out->kind = DK_OPD_MAP;
             out->map = el->opd;
             out->amp = el->amplitude;
@@ -425,14 +432,20 @@ coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int
         case CORO_EL_ZERNIKE: {
             if (!el->coeffs || el->n_coeffs < 1 || el->j_first < 1) { set_error("zernike: need coeffs, n_coeffs >= 1, j_first >= 1"); return CORO_EINVAL; }
             if (!(el->radius > 0)) { set_error("zernike: radius must be > 0"); return CORO_EINVAL; }
-            std::vector<float> zt;
+            std::vector<double> zt;
             if (!zernike_table(el, zt)) { set_error("zernike: Noll index beyond 36 (radial order 7)"); return CORO_ENOTIMPL; }
             for (int b = 0; b < batch; ++b) {
                 ithr[4 * b] = clamp_thr(disk_threshold(el->radius, ps[b], false));
-                fpar[4 * b] = (float)(2.0 / lam[b]);
-                fpar[4 * b + 1] = (float)(ps[b] / el->radius);
+                split_f32(2.0 / lam[b], &fpar[4 * b], &fpar[4 * b + 2]);
+                split_f32(ps[b] / el->radius, &fpar[4 * b + 1], &fpar[4 * b + 3]);
             }
-            out->zpoly = (const float*)db.add(zt.data(), zt.size() * sizeof(float), &st);
+            if (dbl) {                                   // complex128 passes: FP64 polynomials
+                std::vector<double> zd(zt.begin(), zt.end());
+                out->zpoly = (const float*)db.add(zd.data(), zd.size() * sizeof(double), &st);
+            } else {
+                std::vector<float> zf(zt.begin(), zt.end());
+                out->zpoly = (const float*)db.add(zf.data(), zf.size() * sizeof(float), &st);
+            }
             if (!out->zpoly) return st;
             out->kind = DK_ZERNIKE;
             break;
@@ -441,7 +454,7 @@ coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int
             for (int b = 0; b < batch; ++b) {
                 const double f = el->sine_freq * ps[b];                 // cycles per pixel
                 const double fhi = (double)(float)(std::ldexp(std::rint(std::ldexp(f, 11)), -11));
-                fpar[4 * b] = (float)(2.0 * el->sine_amplitude / lam[b]);
+                split_f32(2.0 * el->sine_amplitude / lam[b], &fpar[4 * b], &fpar[4 * b + 3]);
                 fpar[4 * b + 1] = (float)fhi;
                 fpar[4 * b + 2] = (float)(f - fhi);
             }
@@ -450,8 +463,15 @@ coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int
             break;
         }
         case CORO_EL_SCALAR: {
-            for (int b = 0; b < batch; ++b) fpar[4 * b] = (float)el->scalar;
+            for (int b = 0; b < batch; ++b) split_f32(el->scalar, &fpar[4 * b], &fpar[4 * b + 1]);
             out->kind = DK_SCALAR;
+            break;
+        }
+        case CORO_EL_CHECKPOINT: {
+            if (!el->store) { set_error("checkpoint: store is NULL"); return CORO_EINVAL; }
+            out->kind = DK_STORE;
+            out->dst = el->store;
+            out->map_bstride = (long long)n * n;
             break;
         }
         default:
@@ -859,6 +879,9 @@ coro_status build_passes(FresnelPlan* plan, int n, int batch, const double* ps0,
         for (const coro_element* el : planes[p].user) {
             DevElem e;
             if ((st = compile_element(plan->db, el, dbl, n, batch, ps.data(), lam, &e)) != CORO_OK) return st;
+            // after an angular-spectrum hop the row pass holds the field times (-1)^(x+y)
+            // (the fftshift sign is carried into the next forward FFT); checkpoints undo it
+            if (e.kind == DK_STORE && state == SPECTRUM) e.flags |= 1;
             if (!push(e)) return CORO_ENOTIMPL;
         }
         for (const auto& c : planes[p].qpf) {

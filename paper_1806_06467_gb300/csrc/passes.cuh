@@ -26,7 +26,9 @@ enum DevElemKind : int {
     DK_SINE = 6,       // fpar: [2 amp / lambda, f_hi, f_lo] (cycles per pixel split), flags: axis
     DK_SCALAR = 7,     // fpar: [s]
     DK_CHECKER = 8,    // (-1)^(x+y)
-    DK_CONJ = 9        // complex conjugate (direct hops with z < 0: IDFT(y) = conj(DFT(conj y)))
+    DK_CONJ = 9,       // complex conjugate (direct hops with z < 0: IDFT(y) = conj(DFT(conj y)))
+    DK_STORE = 10      // checkpoint: copy the field to dst[b * map_bstride + y * n + x], the field
+                       // itself unchanged; flags bit0: the copy is taken times (-1)^(x+y)
 };
 
 // Zernike evaluation table: OPD = sum_{m=0}^{ZM-1} A_m(rho^2) Re(z^m) + B_m(rho^2) Im(z^m),
@@ -44,6 +46,7 @@ struct DevElem {
     const float* amp;         // amplitude map (nullable)
     long long map_bstride;    // 0 (shared) or n*n
     const float* zpoly;       // [2][ZM][ZD]
+    void* dst;                // DK_STORE destination (complex, the pass's dtype)
 };
 
 constexpr int kMaxPassElems = 8;   // up to 5 user / plane elements + conj, input QPF, checker
@@ -64,6 +67,42 @@ template <typename C> __device__ __forceinline__ void phasor_hc(float ph, float&
         __sincosf(3.14159265358979323846f * r, &sn, &cs);
     } else {
         sincospif(ph, &sn, &cs);
+    }
+}
+
+template <typename C> constexpr bool kF64 = std::is_same<C, double2>::value;
+
+// Zernike phase for complex128 passes: the polynomial table is FP64 (zpoly then points at
+// doubles), 2 / lambda and dx / R come as float pairs (hi + lo).
+template <int N, int XS>
+__device__ __forceinline__ void zernike_f64(double2 (&v)[16], int x0, int ky, int b, const DevElem& e) {
+    const int t0 = e.ithr[4 * b];
+    const double k = (double)e.fpar[4 * b] + (double)e.fpar[4 * b + 2];
+    const double sc = (double)e.fpar[4 * b + 1] + (double)e.fpar[4 * b + 3];
+    const double* zp = reinterpret_cast<const double*>(e.zpoly);
+    const double zy = ky * sc;
+#pragma unroll 1
+    for (int s = 0; s < 16; ++s) {
+        const int kx = x0 + s * XS - N / 2;
+        if (kx * kx + ky * ky > t0) continue;        // zero OPD outside the disk
+        const double zx = kx * sc;
+        const double rho2 = zx * zx + zy * zy;
+        double pr = 1.0, pim = 0.0, opd = 0.0;
+#pragma unroll 1
+        for (int m = 0; m < ZM; ++m) {
+            const double* A = zp + m * ZD;
+            const double* Bc = zp + ZM * ZD + m * ZD;
+            double a = A[ZD - 1], bb = Bc[ZD - 1];
+#pragma unroll
+            for (int d = ZD - 2; d >= 0; --d) { a = fma(a, rho2, A[d]); bb = fma(bb, rho2, Bc[d]); }
+            opd += a * pr + bb * pim;
+            const double nr = pr * zx - pim * zy;
+            pim = pr * zy + pim * zx;
+            pr = nr;
+        }
+        double sn, cs;
+        sincospi(k * opd, &sn, &cs);
+        v[s] = cmul(v[s], make_double2(cs, sn));
     }
 }
 
@@ -112,76 +151,106 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                 break;
             }
             case DK_OPD_MAP: {
-                const float k = e.fpar[4 * b];
                 const size_t off = (size_t)b * e.map_bstride + (size_t)y * N + x0;
+                if constexpr (kF64<C>) {
+                    // complex128: 2 / lambda as a float pair, the phase in FP64
+                    const double k = (double)e.fpar[4 * b] + (double)e.fpar[4 * b + 1];
 #pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    // phase / pi = (2 / lambda) * OPD
-                    const float ph = k * (i == pre_idx ? pre[s] : __ldg(e.map + off + s * XS));
-                    float sn, cs;
-                    phasor_hc<C>(ph, sn, cs);
-                    R am = 1;
-                    if (e.amp) am = (R)__ldg(e.amp + off + s * XS);
-                    v[s] = cmul(v[s], mk<C>(am * (R)cs, am * (R)sn));
+                    for (int s = 0; s < 16; ++s) {
+                        const double ph = k * (double)(i == pre_idx ? pre[s] : __ldg(e.map + off + s * XS));
+                        double sn, cs;
+                        sincospi(ph, &sn, &cs);
+                        const double am = e.amp ? (double)__ldg(e.amp + off + s * XS) : 1.0;
+                        v[s] = cmul(v[s], mk<C>(am * cs, am * sn));
+                    }
+                } else {
+                    const float k = e.fpar[4 * b];
+#pragma unroll
+                    for (int s = 0; s < 16; ++s) {
+                        // phase / pi = (2 / lambda) * OPD
+                        const float ph = k * (i == pre_idx ? pre[s] : __ldg(e.map + off + s * XS));
+                        float sn, cs;
+                        phasor_hc<C>(ph, sn, cs);
+                        R am = 1;
+                        if (e.amp) am = (R)__ldg(e.amp + off + s * XS);
+                        v[s] = cmul(v[s], mk<C>(am * (R)cs, am * (R)sn));
+                    }
                 }
                 break;
             }
             case DK_ZERNIKE: {
-                const int t0 = e.ithr[4 * b];
-                const float k = e.fpar[4 * b], sc = e.fpar[4 * b + 1];
-                const float zy = ky * sc;
-                // the polynomial is evaluated in a rolled loop (few registers); only the phase
-                // of each of the 16 samples is kept
-                float ph[16];
+                if constexpr (kF64<C>) {
+                    zernike_f64<N, XS>(v, x0, ky, b, e);
+                } else {
+                    const int t0 = e.ithr[4 * b];
+                    const float k = e.fpar[4 * b], sc = e.fpar[4 * b + 1];
+                    const float zy = ky * sc;
+                    // the polynomial is evaluated in a rolled loop (few registers); only the phase
+                    // of each of the 16 samples is kept
+                    float ph[16];
 #pragma unroll 1
-                for (int s = 0; s < 16; ++s) {
-                    const int kx = x0 + s * XS - N / 2;
-                    float opd = 0.f;                          // zero OPD outside the disk
-                    if (kx * kx + ky * ky <= t0) {
-                        const float zx = kx * sc;
-                        const float rho2 = zx * zx + zy * zy;
-                        float pr = 1.f, pim = 0.f;
+                    for (int s = 0; s < 16; ++s) {
+                        const int kx = x0 + s * XS - N / 2;
+                        float opd = 0.f;                          // zero OPD outside the disk
+                        if (kx * kx + ky * ky <= t0) {
+                            const float zx = kx * sc;
+                            const float rho2 = zx * zx + zy * zy;
+                            float pr = 1.f, pim = 0.f;
 #pragma unroll 1
-                        for (int m = 0; m < ZM; ++m) {
-                            const float* A = e.zpoly + m * ZD;
-                            const float* Bc = e.zpoly + ZM * ZD + m * ZD;
-                            float a = A[ZD - 1], bb = Bc[ZD - 1];
+                            for (int m = 0; m < ZM; ++m) {
+                                const float* A = e.zpoly + m * ZD;
+                                const float* Bc = e.zpoly + ZM * ZD + m * ZD;
+                                float a = A[ZD - 1], bb = Bc[ZD - 1];
 #pragma unroll
-                            for (int d = ZD - 2; d >= 0; --d) { a = fmaf(a, rho2, A[d]); bb = fmaf(bb, rho2, Bc[d]); }
-                            opd += a * pr + bb * pim;
-                            const float nr = pr * zx - pim * zy;
-                            pim = pr * zy + pim * zx;
-                            pr = nr;
+                                for (int d = ZD - 2; d >= 0; --d) { a = fmaf(a, rho2, A[d]); bb = fmaf(bb, rho2, Bc[d]); }
+                                opd += a * pr + bb * pim;
+                                const float nr = pr * zx - pim * zy;
+                                pim = pr * zy + pim * zx;
+                                pr = nr;
+                            }
                         }
+                        ph[s] = k * opd;
                     }
-                    ph[s] = k * opd;
-                }
 #pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    float sn, cs;
-                    phasor_hc<C>(ph[s], sn, cs);
-                    v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
+                    for (int s = 0; s < 16; ++s) {
+                        float sn, cs;
+                        phasor_hc<C>(ph[s], sn, cs);
+                        v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
+                    }
                 }
                 break;
             }
             case DK_SINE: {
                 const float* p = e.fpar + 4 * b;
                 const bool along_y = e.flags & 1;
+                if constexpr (kF64<C>) {
+                    const double amp = (double)p[0] + (double)p[3], f = (double)p[1] + (double)p[2];
 #pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const int kk = along_y ? ky : x0 + s * XS - N / 2;
-                    // cycles = kk * f with f = f_hi + f_lo and kk * f_hi exact in FP32
-                    float a = (float)kk * p[1];
-                    a -= rintf(a);
-                    a += (float)kk * p[2];
-                    float sn, cs;
-                    phasor_hc<C>(p[0] * sinpif(2.f * a), sn, cs);
-                    v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
+                    for (int s = 0; s < 16; ++s) {
+                        const int kk = along_y ? ky : x0 + s * XS - N / 2;
+                        double a = (double)kk * f;
+                        a -= rint(a);
+                        double sn, cs;
+                        sincospi(amp * sinpi(2.0 * a), &sn, &cs);
+                        v[s] = cmul(v[s], mk<C>(cs, sn));
+                    }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < 16; ++s) {
+                        const int kk = along_y ? ky : x0 + s * XS - N / 2;
+                        // cycles = kk * f with f = f_hi + f_lo and kk * f_hi exact in FP32
+                        float a = (float)kk * p[1];
+                        a -= rintf(a);
+                        a += (float)kk * p[2];
+                        float sn, cs;
+                        phasor_hc<C>(p[0] * sinpif(2.f * a), sn, cs);
+                        v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
+                    }
                 }
                 break;
             }
             case DK_SCALAR: {
-                const R sc = (R)e.fpar[4 * b];
+                const R sc = kF64<C> ? (R)((double)e.fpar[4 * b] + (double)e.fpar[4 * b + 1]) : (R)e.fpar[4 * b];
 #pragma unroll
                 for (int s = 0; s < 16; ++s) v[s] = cscale(v[s], sc);
                 break;
@@ -195,6 +264,16 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
             case DK_CONJ: {
 #pragma unroll
                 for (int s = 0; s < 16; ++s) v[s] = cconj(v[s]);
+                break;
+            }
+            case DK_STORE: {
+                C* d = static_cast<C*>(e.dst) + (size_t)b * e.map_bstride + (size_t)y * N + x0;
+                const bool chk = e.flags & 1;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const bool neg = chk && ((x0 + s * XS + y) & 1);
+                    __stcs(d + s * XS, neg ? mk<C>(-v[s].x, -v[s].y) : v[s]);
+                }
                 break;
             }
             default:
@@ -358,6 +437,21 @@ __device__ __forceinline__ void apply_elems_pair(pk::CP (&v)[16], int x0, int ya
                 const u64 m = pk::pack(-1.f, -1.f);
 #pragma unroll
                 for (int s = 0; s < 16; ++s) v[s].im = pk::mul2(v[s].im, m);
+                break;
+            }
+            case DK_STORE: {
+                float2* d = static_cast<float2*>(e.dst) + (size_t)b * e.map_bstride + (size_t)ya * N + x0;
+                const bool chk = e.flags & 1;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    float ra, rb, ia, ib;
+                    pk::unpack(v[s].re, ra, rb);
+                    pk::unpack(v[s].im, ia, ib);
+                    // rows ya and ya + 1 have opposite parity
+                    const float sa = (chk && ((x0 + s * XS + ya) & 1)) ? -1.f : 1.f, sb = chk ? -sa : 1.f;
+                    __stcs(d + s * XS, make_float2(sa * ra, sa * ia));
+                    __stcs(d + N + s * XS, make_float2(sb * rb, sb * ib));
+                }
                 break;
             }
             default:

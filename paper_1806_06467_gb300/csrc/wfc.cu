@@ -11,6 +11,10 @@
 //   G0 = AS(-z)(exp(-i phi2) G2),  dL/dphi1 = 2 Im(G0 conj(E0)),
 //   dL/dh = sum_lambda (4 pi / lambda) G_infl^T (dL/dphi) G_infl.
 // The wavelength sum is folded into one weighted map per DM before the DM correlation.
+// Each chain runs as one fused Fresnel plan (five row / column passes for the two hops):
+// forward  init . aperture . phi1 . [checkpoint E0] -> AS(+z) -> [checkpoint E1] . phi2 -> AS(-z)
+// adjoint  G3 -> AS(+z) -> [checkpoint G2] . exp(-i phi2) -> AS(-z) -> G0
+// with the checkpoints written by the row passes themselves (no separate copies).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -51,6 +55,7 @@ struct WfcPlan : coro_plan_s {
     std::vector<double> lam, ps;
     std::vector<coro_lyot_item> items;
     coro_plan lyot = nullptr;
+    coro_plan fwd = nullptr, adj = nullptr;     // fused Fresnel plans of the two chains
     std::vector<void*> bufs;
     float2 *e0 = nullptr, *e1 = nullptr, *w = nullptr, *g = nullptr;
     float *opd1 = nullptr, *opd2 = nullptr, *opd2n = nullptr, *dphi = nullptr, *zero_h = nullptr;
@@ -61,6 +66,8 @@ struct WfcPlan : coro_plan_s {
     int timing_units() const override { return 0; }
     ~WfcPlan() override {
         if (lyot) coro_plan_destroy(lyot);
+        if (fwd) coro_plan_destroy(fwd);
+        if (adj) coro_plan_destroy(adj);
         coro::DeviceGuard gd(device);
         cudaDeviceSynchronize();
         for (void* p : bufs) cudaFree(p);
@@ -74,10 +81,6 @@ struct WfcPlan : coro_plan_s {
     }
 };
 
-coro_wavefront field(WfcPlan* p, float2* data) {
-    return coro_wavefront{data, CORO_C64, p->d.batch, p->d.n_fresnel, p->ps.data(), p->lam.data()};
-}
-
 coro_element opd_elem(const float* map) {
     coro_element e{};
     e.kind = CORO_EL_OPD_MAP;
@@ -85,35 +88,63 @@ coro_element opd_elem(const float* map) {
     return e;
 }
 
-// Forward through the Fresnel section: fills e0, e1 and leaves E3 in w.
+// Forward through the Fresnel section: the DM surfaces, then the fused plan, which writes
+// the checkpoints E0 and E1 and leaves E3 in w.
 coro_status fresnel_forward(WfcPlan* p, const float* heights) {
     const coro_wfc_desc& d = p->d;
     coro_ctx c = p->ctx;
     const int nf = d.n_fresnel, na = d.n_act;
     const double dx = d.diam_m / d.npix;
-    const size_t fbytes = (size_t)d.batch * nf * nf * sizeof(float2);
     coro_status st;
     if ((st = coro_dm_opd(c, heights, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, 2.0, p->opd1)) != CORO_OK) return st;
     if ((st = coro_dm_opd(c, heights + na * na, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, 2.0, p->opd2)) != CORO_OK) return st;
     if ((st = coro_dm_opd(c, heights + na * na, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, -2.0, p->opd2n)) != CORO_OK) return st;
-    coro_wavefront f0 = field(p, p->e0);
-    if ((st = coro_wavefront_init(c, &f0, 1.0)) != CORO_OK) return st;
-    coro_element ap{};
-    ap.kind = CORO_EL_APERTURE;
-    ap.radius = 0.5 * d.diam_m;
-    if ((st = coro_apply_element(c, &f0, &ap)) != CORO_OK) return st;
-    coro_element o1 = opd_elem(p->opd1);
-    if ((st = coro_apply_element(c, &f0, &o1)) != CORO_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(p->e1, p->e0, fbytes, cudaMemcpyDeviceToDevice, c->stream);
-    if (e != cudaSuccess) return coro::cuda_fail(e, "wfc: copy");
-    coro_wavefront f1 = field(p, p->e1);
-    if ((st = coro_propagate_fresnel(c, &f1, d.z_m, CORO_FRESNEL_AS)) != CORO_OK) return st;
-    e = cudaMemcpyAsync(p->w, p->e1, fbytes, cudaMemcpyDeviceToDevice, c->stream);
-    if (e != cudaSuccess) return coro::cuda_fail(e, "wfc: copy");
-    coro_wavefront fw = field(p, p->w);
-    coro_element o2 = opd_elem(p->opd2);
-    if ((st = coro_apply_element(c, &fw, &o2)) != CORO_OK) return st;
-    return coro_propagate_fresnel(c, &fw, -d.z_m, CORO_FRESNEL_AS);
+    return coro_fresnel_plan_execute(p->fwd, p->w, nullptr);
+}
+
+coro_element checkpoint_elem(int plane, void* store) {
+    coro_element e{};
+    e.kind = CORO_EL_CHECKPOINT;
+    e.plane = plane;
+    e.store = store;
+    return e;
+}
+
+// The two fused plans (their element maps and checkpoint buffers are the plan's own).
+coro_status make_chains(WfcPlan* p) {
+    const coro_wfc_desc& d = p->d;
+    const double z[2] = {d.z_m, -d.z_m};
+    coro_element fe[5]{};
+    fe[0].kind = CORO_EL_APERTURE;
+    fe[0].radius = 0.5 * d.diam_m;
+    fe[1] = opd_elem(p->opd1);
+    fe[2] = checkpoint_elem(0, p->e0);
+    fe[3] = checkpoint_elem(1, p->e1);
+    fe[4] = opd_elem(p->opd2);
+    fe[4].plane = 1;
+    coro_fresnel_desc fd{};
+    fd.dtype = CORO_C64;
+    fd.batch = d.batch;
+    fd.n = d.n_fresnel;
+    fd.pixelscale = p->ps.data();
+    fd.wavelength = p->lam.data();
+    fd.n_planes = 3;
+    fd.distance = z;
+    fd.n_elements = 5;
+    fd.elements = fe;
+    fd.flags = CORO_PLAN_INIT_UNIFORM;
+    coro_status st = coro_fresnel_plan_create(p->ctx, &fd, &p->fwd);
+    if (st != CORO_OK) return st;
+    coro_element ae[2]{};
+    ae[0] = checkpoint_elem(1, p->w);               // G2 (E3 is no longer needed by then)
+    ae[1] = opd_elem(p->opd2n);
+    ae[1].plane = 1;
+    fd.n_elements = 2;
+    fd.elements = ae;
+    fd.flags = 0;
+    if ((st = coro_fresnel_plan_create(p->ctx, &fd, &p->adj)) != CORO_OK) return st;
+    if ((st = coro_plan_set_graph(p->fwd, 1)) != CORO_OK) return st;
+    return coro_plan_set_graph(p->adj, 1);
 }
 
 float2* window(WfcPlan* p, float2* base) {
@@ -178,6 +209,7 @@ extern "C" coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* d
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->w_d, w.data(), d->batch * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return coro::cuda_fail(e, "coro_wfc_plan_create");
+    if ((st = make_chains(p.get())) != CORO_OK) return st;
     *out = p.release();
     return CORO_OK;
 }
@@ -218,20 +250,16 @@ extern "C" coro_status coro_wfc_plan_evaluate(coro_plan plan, const float* heigh
         if (e != cudaSuccess) return coro::cuda_fail(e, "wfc: memset");
         st = coro_lyot_plan_gradient(p->lyot, window(p, p->w), p->peak.data(), dh.data(), window(p, p->g), nf,
                                      (long long)nf * nf);
-        coro_wavefront fg = field(p, p->g);
+        // G3 -> G2 (checkpoint in w) -> G0 (in g)
+        if (st == CORO_OK) st = coro_fresnel_plan_execute(p->adj, p->g, nullptr);
         const size_t npx = (size_t)nf * nf;
         const int blocks = (int)std::min<size_t>((npx + 255) / 256, 152 * 8);
-        // G2 = AS(+z) G3; dL/dphi2 = 2 Im(G2 conj(E1 exp(i phi2)))
-        if (st == CORO_OK) st = coro_propagate_fresnel(c, &fg, d.z_m, CORO_FRESNEL_AS);
+        // dL/dphi2 = 2 Im(G2 conj(E1 exp(i phi2))),  dL/dphi1 = 2 Im(G0 conj(E0))
         if (st == CORO_OK) {
-            phase_grad_kernel<<<blocks, 256, 0, c->stream>>>(p->g, p->e1, p->opd2, p->k_d, p->w_d, B, npx, p->dphi + npx);
+            phase_grad_kernel<<<blocks, 256, 0, c->stream>>>(p->w, p->e1, p->opd2, p->k_d, p->w_d, B, npx, p->dphi + npx);
             e = cudaGetLastError();
             if (e != cudaSuccess) st = coro::cuda_fail(e, "phase_grad_kernel");
         }
-        // G0 = AS(-z)(exp(-i phi2) G2); dL/dphi1 = 2 Im(G0 conj(E0))
-        coro_element o2n = opd_elem(p->opd2n);
-        if (st == CORO_OK) st = coro_apply_element(c, &fg, &o2n);
-        if (st == CORO_OK) st = coro_propagate_fresnel(c, &fg, -d.z_m, CORO_FRESNEL_AS);
         if (st == CORO_OK) {
             phase_grad_kernel<<<blocks, 256, 0, c->stream>>>(p->g, p->e0, nullptr, p->k_d, p->w_d, B, npx, p->dphi);
             e = cudaGetLastError();

@@ -57,3 +57,33 @@ def test_no_device_reports_ecuda(dll):
     from paper_1806_06467_gb300 import coro
     h = ct.c_void_p()
     assert dll.coro_ctx_create(0, None, ct.byref(h)) == coro.ECUDA
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's size and field offsets."""
+    import subprocess
+
+    from paper_1806_06467_gb300 import coro
+    mirrors = {"coro_wavefront": coro.Wavefront, "coro_element": coro.Element, "coro_fresnel_desc": coro.FresnelDesc,
+               "coro_fresnel_system_desc": coro.FresnelSystemDesc, "coro_lyot_item": coro.LyotItem,
+               "coro_lyot_desc": coro.LyotDesc, "coro_wfc_desc": coro.WfcDesc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "coro.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            c, f, v = line.split()
+            got[(c, f)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ct.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

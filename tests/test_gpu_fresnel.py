@@ -130,16 +130,17 @@ def test_lens(ctx, dtype):
     assert rel_l2(got[0], ref) < (2e-7 if dtype == torch.complex64 else tol(dtype, phase_max))
 
 
-def test_opd_map_and_amplitude(ctx):
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_opd_map_and_amplitude(ctx, dtype):
     n, lam = 256, 600e-9
     opd = inputs.psd_surface(n, 4) * 10
     amp = inputs.rng(2).uniform(0.5, 1.0, (n, n))
     opd_t = torch.from_numpy(opd.astype(np.float32)).cuda()
     amp_t = torch.from_numpy(amp.astype(np.float32)).cuda()
     el = coro.element(coro.EL_OPD_MAP, opd=opd_t, amplitude=amp_t)
-    f, got = apply(ctx, n, torch.complex64, el, lam=lam)
+    f, got = apply(ctx, n, dtype, el, lam=lam)
     ref = f[0] * optics.phasor(opd.astype(np.float32), lam, amp.astype(np.float32))
-    assert rel_l2(got[0], ref) < 1e-6
+    assert rel_l2(got[0], ref) < (1e-6 if dtype == torch.complex64 else TOL[dtype])
 
 
 def test_opd_map_batched(ctx):
@@ -154,22 +155,24 @@ def test_opd_map_batched(ctx):
         assert rel_l2(got[b], f[b] * optics.phasor(opd[b], lams[b])) < 1e-6
 
 
-def test_zernike(ctx):
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_zernike(ctx, dtype):
     n, dx, lam = 512, 1.0 / 500, 550e-9
     c = inputs.zernike_coefficients(3, 4, 21, 50e-9)
     el = coro.element(coro.EL_ZERNIKE, radius=0.5, coeffs=c, j_first=4)
-    f, got = apply(ctx, n, torch.complex64, el, dx=dx, lam=lam)
+    f, got = apply(ctx, n, dtype, el, dx=dx, lam=lam)
     ref = f[0] * optics.phasor(optics.zernike_opd(n, dx, 0.5, c, 4), lam)
-    assert rel_l2(got[0], ref) < 1e-6
+    assert rel_l2(got[0], ref) < (1e-6 if dtype == torch.complex64 else TOL[dtype])
 
 
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
 @pytest.mark.parametrize("axis", [0, 1])
-def test_sine_wfe(ctx, axis):
+def test_sine_wfe(ctx, axis, dtype):
     n, dx, lam = 2048, 0.04 / 256, 0.5e-6
     el = coro.element(coro.EL_SINE, sine_freq=500.0, sine_amplitude=5e-9, axis=axis)
-    f, got = apply(ctx, n, torch.complex64, el, dx=dx, lam=lam)
+    f, got = apply(ctx, n, dtype, el, dx=dx, lam=lam)
     ref = f[0] * optics.phasor(optics.sine_wfe(n, dx, 500.0, 5e-9, axis=1 if axis == 0 else 0), lam)
-    assert rel_l2(got[0], ref) < 1e-6
+    assert rel_l2(got[0], ref) < (1e-6 if dtype == torch.complex64 else TOL[dtype])
 
 
 def test_scalar_and_init(ctx):
@@ -177,6 +180,8 @@ def test_scalar_and_init(ctx):
     coro.wavefront_init(ctx, x, 1.0)
     coro.apply_element(ctx, x, 1e-3, 5e-7, coro.element(coro.EL_SCALAR, scalar=0.25))
     assert torch.all(x == 0.25)
+    f, got = apply(ctx, 64, torch.complex128, coro.element(coro.EL_SCALAR, scalar=0.1))
+    assert rel_l2(got[0], f[0] * 0.1) < 1e-15                 # 0.1 is not a float: FP64 scalar
 
 
 # ------------------------------------------------------------------------------ fused plan
@@ -321,6 +326,89 @@ def test_relay_every_pass_kernel_4096(ctx):
     seen = _relay_all_kernels(ctx, 4096, 1024, seed=0)
     assert "row_pass_units<4096>" in seen and "col_pass_units<4096,2>" in seen and "col_pass_pair<4096,2>" in seen
     assert "col_pass_wide<4096,4>" in seen and "row_pass_pair<4096>" in seen
+
+
+def relay_oracle_planes(w, maps_np):
+    """The relay's field at every plane: (before, after) the plane's element."""
+    n, dx, lam = w.n, w.dx, w.wavelength_m
+    r = w.diam_m / 2
+    els = [optics.circular_aperture(n, dx, r, w.obscuration, w.n_spiders, w.spider_width_frac * w.diam_m),
+           optics.thin_lens(n, dx, lam, w.lens1_m),
+           optics.phasor(maps_np[0], lam),
+           optics.thin_lens(n, dx, lam, w.lens2_m),
+           optics.phasor(maps_np[1], lam),
+           optics.circle_stop(n, dx, w.field_stop_frac * r)]
+    e = np.ones((n, n), complex)
+    out = []
+    for p, z in enumerate(list(w.distances()) + [None]):
+        before = e
+        e = e * els[p]
+        out.append((before, e))
+        if z is not None:
+            e = propagation.angular_spectrum(e, dx, lam, z)
+    return out
+
+
+@pytest.mark.parametrize("n,dtype", [(256, torch.complex128), (1024, torch.complex64)])
+def test_checkpoint_elements(ctx, n, dtype):
+    """Per-plane checkpoints inside the fused relay plan: after the aperture (first row pass),
+    before and after a PSD surface (mid-chain row passes, whose field carries the fftshift
+    sign), after the field stop (last pass: equal to the output). Every row kernel."""
+    w = inputs.RelayWorkload(n=n, npix=n // 2, seed=4)
+    maps = [m.astype(np.float32) for m in w.psd_maps()]
+    maps_t = [torch.from_numpy(m).cuda() for m in maps]
+    cps = [torch.zeros((1, n, n), dtype=dtype, device="cuda") for _ in range(4)]
+    els = relay_elements(w, maps_t)
+    els = [els[0], coro.element(coro.EL_CHECKPOINT, plane=0, store=cps[0]), els[1],
+           coro.element(coro.EL_CHECKPOINT, plane=2, store=cps[1]), els[2], els[3], els[4],
+           coro.element(coro.EL_CHECKPOINT, plane=4, store=cps[2]), els[5],
+           coro.element(coro.EL_CHECKPOINT, plane=5, store=cps[3])]
+    plan = coro.FresnelPlan(ctx, n=n, batch=1, pixelscale=w.dx, wavelength=w.wavelength_m,
+                            distances=list(w.distances()), elements=els, init_uniform=True,
+                            dtype=coro.C128 if dtype == torch.complex128 else coro.C64)
+    assert plan.launch_count == 11
+    ref = relay_oracle_planes(w, maps)
+    want = [ref[0][1], ref[2][0], ref[4][1], ref[5][1]]
+    x = torch.empty((1, n, n), dtype=dtype, device="cuda")
+    r_max = np.sqrt(2) * (n / 2) * w.dx                  # the lenses' largest quadratic phase
+    bound = tol(dtype, np.pi * r_max ** 2 / (w.wavelength_m * min(w.lens1_m, w.lens2_m)))
+    rows = KERNEL_CHOICES[n][0] if n in KERNEL_CHOICES and dtype == torch.complex64 else [None]
+    for rv in rows:
+        if rv is not None:
+            plan.set_pass_kernel(rv, 0)
+        for c in cps:
+            c.fill_(float("nan"))
+        plan.execute(x)
+        for i, (c, r) in enumerate(zip(cps, want)):
+            err = rel_l2(c.cpu().numpy()[0], r)
+            assert err < bound, (rv, i, err)
+        assert torch.equal(cps[3], x)
+
+
+def test_checkpoint_after_direct_hop_and_apply(ctx):
+    """A checkpoint at the focal plane of a direct hop (natural layout, new pixel scale), on
+    two wavelengths; coro_apply_element with a checkpoint copies the field."""
+    n, npix = 256, 128
+    dx = 1.0 / npix
+    lams = np.array([500e-9, 600e-9])
+    cp = torch.zeros((2, n, n), dtype=torch.complex64, device="cuda")
+    els = [coro.element(coro.EL_APERTURE, plane=0, radius=0.5),
+           coro.element(coro.EL_LENS, plane=0, focal_length=10.0),
+           coro.element(coro.EL_CHECKPOINT, plane=1, store=cp),
+           coro.element(coro.EL_CIRCLE, plane=1, radius=40e-6, flags=coro.ELF_OPAQUE_INSIDE)]
+    plan = coro.FresnelPlan(ctx, n=n, batch=2, pixelscale=dx, wavelength=lams, distances=[10.0, 0.05],
+                            methods=[coro.FRESNEL_DIRECT, coro.FRESNEL_AS], elements=els, init_uniform=True)
+    x = torch.empty((2, n, n), dtype=torch.complex64, device="cuda")
+    plan.execute(x)
+    got = cp.cpu().numpy()
+    for b in range(2):
+        e = optics.circular_aperture(n, dx, 0.5) * optics.thin_lens(n, dx, lams[b], 10.0)
+        e, _ = propagation.direct_fresnel(e, dx, lams[b], 10.0)
+        assert rel_l2(got[b], e) < 1e-5
+    y = to_dev(inputs.random_field((2, n, n), seed=9), torch.complex64)
+    out = torch.zeros_like(y)
+    coro.apply_element(ctx, y, dx, lams, coro.element(coro.EL_CHECKPOINT, store=out))
+    assert torch.equal(out, y)
 
 
 def test_mixed_plan_direct_then_as(ctx):
