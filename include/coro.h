@@ -111,7 +111,7 @@ typedef enum {
     CORO_EL_SINE = 6,     /* OPD = sine_amplitude * sin(2 pi sine_freq x) along x (axis 0) or y
                              * (axis 1) (App. A SineWaveWFE)                                   */
     CORO_EL_SCALAR = 7,   /* multiply by a real scalar (ScalarTransmission, App. B)            */
-    CORO_EL_CHECKPOINT = 8 /* copy the field as it stands at this point of the plane (after the
+    CORO_EL_CHECKPOINT = 8, /* copy the field as it stands at this point of the plane (after the
                              * plane's elements listed before it) to `store`, field unchanged:
                              * per-plane wavefront checkpoints for adjoints (intermediate planes
                              * of Sec. 1.1 systems). store: device, the wavefront's dtype,
@@ -119,6 +119,14 @@ typedef enum {
                              * also written while a plan is tuned at creation. In pilot-beam
                              * systems the copy is the field relative to the plane's reference
                              * surface, as the plane's other elements see it.                 */
+    CORO_EL_PHASE_GRAD = 9 /* adjoint tap: with the field holding the adjoint G = dL/dconj(E)
+                             * and `ref` the forward field E at the same point, writes the
+                             * float map store[b][y][x] = (scalar / lambda_b) * 2 Im(G conj(E)),
+                             * i.e. scalar / lambda_b times dL/dphi of a phase exp(i phi) applied
+                             * there (scalar = 4 pi: dL/dh per metre of a reflecting surface
+                             * at normal incidence). Field unchanged. ref: device, the
+                             * wavefront's dtype, [batch][n][n]; store: device float
+                             * [batch][n][n]. Same placement rules as CHECKPOINT.           */
 } coro_element_kind;
 
 #define CORO_ELF_OPAQUE_INSIDE 1  /* CORO_EL_CIRCLE: block r <= radius instead of passing it */
@@ -142,7 +150,8 @@ typedef struct {
     double sine_amplitude;    /* SINE: metres                                                */
     int axis;                 /* SINE: 0 = varies along x, 1 = along y                       */
     double scalar;            /* SCALAR                                                      */
-    void* store;              /* CHECKPOINT: device destination [batch][n][n]                */
+    void* store;              /* CHECKPOINT / PHASE_GRAD: device destination [batch][n][n]   */
+    const void* ref;          /* PHASE_GRAD: device forward field [batch][n][n]              */
 } coro_element;
 
 /* Apply one element in place (unfused elementwise kernel). */

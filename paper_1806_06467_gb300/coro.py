@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_PKG, "libcoro.so")
 # status codes
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, ESIZE = 0, -1, -2, -3, -4, -5, -6
 C64, C128 = 0, 1
-EL_APERTURE, EL_CIRCLE, EL_LENS, EL_OPD_MAP, EL_ZERNIKE, EL_SINE, EL_SCALAR, EL_CHECKPOINT = 1, 2, 3, 4, 5, 6, 7, 8
+EL_APERTURE, EL_CIRCLE, EL_LENS, EL_OPD_MAP, EL_ZERNIKE, EL_SINE, EL_SCALAR, EL_CHECKPOINT, EL_PHASE_GRAD = \
+    1, 2, 3, 4, 5, 6, 7, 8, 9
 ELF_OPAQUE_INSIDE, ELF_MAP_BATCHED = 1, 2
 FRESNEL_AS, FRESNEL_DIRECT = 0, 1
 PLAN_INIT_UNIFORM = 1
@@ -43,7 +44,7 @@ class Element(ct.Structure):
                 ("focal_length", ct.c_double), ("opd", ct.c_void_p), ("amplitude", ct.c_void_p),
                 ("coeffs", ct.POINTER(ct.c_double)), ("j_first", ct.c_int), ("n_coeffs", ct.c_int),
                 ("sine_freq", ct.c_double), ("sine_amplitude", ct.c_double), ("axis", ct.c_int),
-                ("scalar", ct.c_double), ("store", ct.c_void_p)]
+                ("scalar", ct.c_double), ("store", ct.c_void_p), ("ref", ct.c_void_p)]
 
 
 class FresnelDesc(ct.Structure):
@@ -248,7 +249,7 @@ def element(kind: int, plane: int = 0, **kw) -> Element:
             keep.append(arr)
             e.coeffs = arr
             e.n_coeffs = len(arr)
-        elif k in ("opd", "amplitude", "store"):
+        elif k in ("opd", "amplitude", "store", "ref"):
             if v is not None:
                 keep.append(v)
                 setattr(e, k, v.data_ptr())

@@ -467,6 +467,15 @@ coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int
             out->kind = DK_SCALAR;
             break;
         }
+        case CORO_EL_PHASE_GRAD: {
+            if (!el->store || !el->ref) { set_error("phase gradient: store and ref must be set"); return CORO_EINVAL; }
+            for (int b = 0; b < batch; ++b) split_f32(2.0 * el->scalar / lam[b], &fpar[4 * b], &fpar[4 * b + 1]);
+            out->kind = DK_PHASE_GRAD;
+            out->dst = el->store;
+            out->tab = el->ref;
+            out->map_bstride = (long long)n * n;
+            break;
+        }
         case CORO_EL_CHECKPOINT: {
             if (!el->store) { set_error("checkpoint: store is NULL"); return CORO_EINVAL; }
             out->kind = DK_STORE;
@@ -881,7 +890,7 @@ coro_status build_passes(FresnelPlan* plan, int n, int batch, const double* ps0,
             if ((st = compile_element(plan->db, el, dbl, n, batch, ps.data(), lam, &e)) != CORO_OK) return st;
             // after an angular-spectrum hop the row pass holds the field times (-1)^(x+y)
             // (the fftshift sign is carried into the next forward FFT); checkpoints undo it
-            if (e.kind == DK_STORE && state == SPECTRUM) e.flags |= 1;
+            if ((e.kind == DK_STORE || e.kind == DK_PHASE_GRAD) && state == SPECTRUM) e.flags |= 1;
             if (!push(e)) return CORO_ENOTIMPL;
         }
         for (const auto& c : planes[p].qpf) {

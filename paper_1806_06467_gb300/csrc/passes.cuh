@@ -27,8 +27,10 @@ enum DevElemKind : int {
     DK_SCALAR = 7,     // fpar: [s]
     DK_CHECKER = 8,    // (-1)^(x+y)
     DK_CONJ = 9,       // complex conjugate (direct hops with z < 0: IDFT(y) = conj(DFT(conj y)))
-    DK_STORE = 10      // checkpoint: copy the field to dst[b * map_bstride + y * n + x], the field
+    DK_STORE = 10,     // checkpoint: copy the field to dst[b * map_bstride + y * n + x], the field
                        // itself unchanged; flags bit0: the copy is taken times (-1)^(x+y)
+    DK_PHASE_GRAD = 11 // float dst[...] = fpar[4b] * Im(v conj(ref)), ref = tab (complex, same
+                       // layout as dst); flags bit0 as DK_STORE. Field unchanged.
 };
 
 // Zernike evaluation table: OPD = sum_{m=0}^{ZM-1} A_m(rho^2) Re(z^m) + B_m(rho^2) Im(z^m),
@@ -266,6 +268,21 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                 for (int s = 0; s < 16; ++s) v[s] = cconj(v[s]);
                 break;
             }
+            case DK_PHASE_GRAD: {
+                const size_t off = (size_t)b * e.map_bstride + (size_t)y * N + x0;
+                const C* rf = static_cast<const C*>(e.tab) + off;
+                float* d = static_cast<float*>(e.dst) + off;
+                const R wgt = kF64<C> ? (R)((double)e.fpar[4 * b] + (double)e.fpar[4 * b + 1]) : (R)e.fpar[4 * b];
+                const bool chk = e.flags & 1;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const C r = __ldg(rf + s * XS);
+                    R im = v[s].y * r.x - v[s].x * r.y;                 // Im(v conj(r))
+                    if (chk && ((x0 + s * XS + y) & 1)) im = -im;
+                    __stcs(d + s * XS, (float)(wgt * im));
+                }
+                break;
+            }
             case DK_STORE: {
                 C* d = static_cast<C*>(e.dst) + (size_t)b * e.map_bstride + (size_t)y * N + x0;
                 const bool chk = e.flags & 1;
@@ -437,6 +454,24 @@ __device__ __forceinline__ void apply_elems_pair(pk::CP (&v)[16], int x0, int ya
                 const u64 m = pk::pack(-1.f, -1.f);
 #pragma unroll
                 for (int s = 0; s < 16; ++s) v[s].im = pk::mul2(v[s].im, m);
+                break;
+            }
+            case DK_PHASE_GRAD: {
+                const size_t off = (size_t)b * e.map_bstride + (size_t)ya * N + x0;
+                const float2* rf = static_cast<const float2*>(e.tab) + off;
+                float* d = static_cast<float*>(e.dst) + off;
+                const float wgt = e.fpar[4 * b];
+                const bool chk = e.flags & 1;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const float2 ra = __ldg(rf + s * XS), rb = __ldg(rf + N + s * XS);
+                    float vra, vrb, via, vib;
+                    pk::unpack(v[s].re, vra, vrb);
+                    pk::unpack(v[s].im, via, vib);
+                    const float sa = (chk && ((x0 + s * XS + ya) & 1)) ? -wgt : wgt, sb = chk ? -sa : wgt;
+                    __stcs(d + s * XS, sa * (via * ra.x - vra * ra.y));
+                    __stcs(d + N + s * XS, sb * (vib * rb.x - vrb * rb.y));
+                }
                 break;
             }
             case DK_STORE: {

@@ -13,8 +13,11 @@
 // The wavelength sum is folded into one weighted map per DM before the DM correlation.
 // Each chain runs as one fused Fresnel plan (five row / column passes for the two hops):
 // forward  init . aperture . phi1 . [checkpoint E0] -> AS(+z) -> [checkpoint E1] . phi2 -> AS(-z)
-// adjoint  G3 -> AS(+z) -> [checkpoint G2] . exp(-i phi2) -> AS(-z) -> G0
-// with the checkpoints written by the row passes themselves (no separate copies).
+// adjoint  G3 -> AS(+z) -> exp(-i phi2) . [dL/dphi2 tap vs E1] -> AS(-z) -> [dL/dphi1 tap vs E0]
+// with checkpoints and taps written by the row passes themselves (no separate copies). The
+// dphi2 tap uses 2 Im(G2 conj(E2)) = 2 Im(G1 conj(E1)) with G1 = exp(-i phi2) G2, so it sits
+// after the conjugate phase and needs only E1. Each tap writes one weighted map per
+// wavelength; the DM correlation reads them per wavelength and a last kernel sums over them.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -25,27 +28,14 @@
 
 namespace {
 
-// out[y][x] = sum_b w[b] 2 Im(g_b conj(f_b)),  f_b = e_b exp(i pi k_b opd)  (e, opd optional),
-// k_b = 2 / lambda_b in half-cycles per metre.
-__global__ void phase_grad_kernel(const float2* __restrict__ g, const float2* __restrict__ e,
-                                  const float* __restrict__ opd, const float* __restrict__ k,
-                                  const float* __restrict__ w, int batch, size_t npx, float* __restrict__ out) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npx; i += (size_t)gridDim.x * blockDim.x) {
-        const float ph = opd ? opd[i] : 0.f;
-        float acc = 0.f;
-        for (int b = 0; b < batch; ++b) {
-            const float2 gv = g[b * npx + i];
-            float2 f = e ? e[b * npx + i] : make_float2(1.f, 0.f);
-            if (opd) {
-                float sn, cs;
-                sincospif(k[b] * ph, &sn, &cs);
-                f = make_float2(f.x * cs - f.y * sn, f.x * sn + f.y * cs);
-            }
-            // Im(g conj(f)) = g.y f.x - g.x f.y
-            acc = fmaf(w[b] * 2.f, gv.y * f.x - gv.x * f.y, acc);
-        }
-        out[i] = acc;
-    }
+// grad[dm][p][q] = sum_b part[dm][b][p][q]
+__global__ void sum_items_kernel(const float* __restrict__ part, int batch, int per_dm, float* __restrict__ grad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, dm = blockIdx.y;
+    if (i >= per_dm) return;
+    const float* src = part + (size_t)dm * batch * per_dm + i;
+    float acc = 0.f;
+    for (int b = 0; b < batch; ++b) acc += src[(size_t)b * per_dm];
+    grad[(size_t)dm * per_dm + i] = acc;
 }
 
 struct WfcPlan : coro_plan_s {
@@ -58,8 +48,8 @@ struct WfcPlan : coro_plan_s {
     coro_plan fwd = nullptr, adj = nullptr;     // fused Fresnel plans of the two chains
     std::vector<void*> bufs;
     float2 *e0 = nullptr, *e1 = nullptr, *w = nullptr, *g = nullptr;
-    float *opd1 = nullptr, *opd2 = nullptr, *opd2n = nullptr, *dphi = nullptr, *zero_h = nullptr;
-    float *k_d = nullptr, *w_d = nullptr;
+    float *opd1 = nullptr, *opd2 = nullptr, *opd2n = nullptr, *zero_h = nullptr;
+    float* part = nullptr;                      // [2][batch][n_act][n_act] per-wavelength dL/dh
     std::vector<double> peak;
     int kind() const override { return 3; }
     int launches() const override { return 0; }
@@ -135,11 +125,23 @@ coro_status make_chains(WfcPlan* p) {
     fd.flags = CORO_PLAN_INIT_UNIFORM;
     coro_status st = coro_fresnel_plan_create(p->ctx, &fd, &p->fwd);
     if (st != CORO_OK) return st;
-    coro_element ae[2]{};
-    ae[0] = checkpoint_elem(1, p->w);               // G2 (E3 is no longer needed by then)
-    ae[1] = opd_elem(p->opd2n);
+    // per-wavelength dL/dh density maps in w (E3 is no longer needed by then): DM2 first
+    const size_t npx = (size_t)d.n_fresnel * d.n_fresnel;
+    float* dphi2 = reinterpret_cast<float*>(p->w);
+    float* dphi1 = dphi2 + (size_t)d.batch * npx;
+    coro_element ae[3]{};
+    ae[0] = opd_elem(p->opd2n);
+    ae[0].plane = 1;
+    ae[1].kind = CORO_EL_PHASE_GRAD;                 // (4 pi / lambda) 2 Im(G1 conj(E1))
     ae[1].plane = 1;
-    fd.n_elements = 2;
+    ae[1].scalar = 4.0 * M_PI;
+    ae[1].ref = p->e1;
+    ae[1].store = dphi2;
+    ae[2] = ae[1];                                   // (4 pi / lambda) 2 Im(G0 conj(E0))
+    ae[2].plane = 2;
+    ae[2].ref = p->e0;
+    ae[2].store = dphi1;
+    fd.n_elements = 3;
     fd.elements = ae;
     fd.flags = 0;
     if ((st = coro_fresnel_plan_create(p->ctx, &fd, &p->adj)) != CORO_OK) return st;
@@ -193,20 +195,12 @@ extern "C" coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* d
     p->opd1 = p->g ? (float*)p->alloc(mbytes, &st) : nullptr;
     p->opd2 = p->opd1 ? (float*)p->alloc(mbytes, &st) : nullptr;
     p->opd2n = p->opd2 ? (float*)p->alloc(mbytes, &st) : nullptr;
-    p->dphi = p->opd2n ? (float*)p->alloc(2 * mbytes, &st) : nullptr;
-    p->zero_h = p->dphi ? (float*)p->alloc((size_t)2 * d->n_act * d->n_act * sizeof(float), &st) : nullptr;
-    p->k_d = p->zero_h ? (float*)p->alloc(d->batch * sizeof(float), &st) : nullptr;
-    p->w_d = p->k_d ? (float*)p->alloc(d->batch * sizeof(float), &st) : nullptr;
-    if (!p->w_d) return st;
-    std::vector<float> k(d->batch), w(d->batch);
-    for (int b = 0; b < d->batch; ++b) {
+    p->zero_h = p->opd2n ? (float*)p->alloc((size_t)2 * d->n_act * d->n_act * sizeof(float), &st) : nullptr;
+    p->part = p->zero_h ? (float*)p->alloc((size_t)2 * d->batch * d->n_act * d->n_act * sizeof(float), &st) : nullptr;
+    if (!p->part) return st;
+    for (int b = 0; b < d->batch; ++b)
         if (!(d->wavelength[b] > 0)) { coro::set_error("coro_wfc_plan_create: wavelength[%d] must be > 0", b); return CORO_EINVAL; }
-        k[b] = (float)(2.0 / d->wavelength[b]);
-        w[b] = (float)(4.0 * M_PI / d->wavelength[b]);     // dphi/dh = 2 (reflection) x 2 pi / lambda
-    }
     cudaError_t e = cudaMemsetAsync(p->zero_h, 0, (size_t)2 * d->n_act * d->n_act * sizeof(float), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->k_d, k.data(), d->batch * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->w_d, w.data(), d->batch * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return coro::cuda_fail(e, "coro_wfc_plan_create");
     if ((st = make_chains(p.get())) != CORO_OK) return st;
@@ -250,25 +244,21 @@ extern "C" coro_status coro_wfc_plan_evaluate(coro_plan plan, const float* heigh
         if (e != cudaSuccess) return coro::cuda_fail(e, "wfc: memset");
         st = coro_lyot_plan_gradient(p->lyot, window(p, p->w), p->peak.data(), dh.data(), window(p, p->g), nf,
                                      (long long)nf * nf);
-        // G3 -> G2 (checkpoint in w) -> G0 (in g)
+        // G3 -> G0 (in g), the row passes writing the per-wavelength dL/dh density maps into w
         if (st == CORO_OK) st = coro_fresnel_plan_execute(p->adj, p->g, nullptr);
         const size_t npx = (size_t)nf * nf;
-        const int blocks = (int)std::min<size_t>((npx + 255) / 256, 152 * 8);
-        // dL/dphi2 = 2 Im(G2 conj(E1 exp(i phi2))),  dL/dphi1 = 2 Im(G0 conj(E0))
-        if (st == CORO_OK) {
-            phase_grad_kernel<<<blocks, 256, 0, c->stream>>>(p->w, p->e1, p->opd2, p->k_d, p->w_d, B, npx, p->dphi + npx);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) st = coro::cuda_fail(e, "phase_grad_kernel");
-        }
-        if (st == CORO_OK) {
-            phase_grad_kernel<<<blocks, 256, 0, c->stream>>>(p->g, p->e0, nullptr, p->k_d, p->w_d, B, npx, p->dphi);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) st = coro::cuda_fail(e, "phase_grad_kernel");
-        }
         const double dx = d.diam_m / d.npix;
-        if (st == CORO_OK) st = coro_dm_correlate(c, p->dphi, 1, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, grad);
+        const float* dphi2 = reinterpret_cast<const float*>(p->w);
+        const int per = na * na;
         if (st == CORO_OK)
-            st = coro_dm_correlate(c, p->dphi + npx, 1, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, grad + na * na);
+            st = coro_dm_correlate(c, dphi2 + (size_t)B * npx, B, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, p->part);
+        if (st == CORO_OK)
+            st = coro_dm_correlate(c, dphi2, B, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, p->part + (size_t)B * per);
+        if (st == CORO_OK) {
+            sum_items_kernel<<<dim3((per + 255) / 256, 2), 256, 0, c->stream>>>(p->part, B, per, grad);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) st = coro::cuda_fail(e, "sum_items_kernel");
+        }
         if (st == CORO_OK) {
             e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) st = coro::cuda_fail(e, "coro_wfc_plan_evaluate");

@@ -385,6 +385,44 @@ def test_checkpoint_elements(ctx, n, dtype):
         assert torch.equal(cps[3], x)
 
 
+@pytest.mark.parametrize("n,dtype", [(256, torch.complex128), (1024, torch.complex64)])
+def test_phase_grad_tap(ctx, n, dtype):
+    """The adjoint tap (scalar / lambda_b) 2 Im(G conj(E)) inside a plan, mid-chain (after an
+    angular-spectrum hop: the row pass holds the fftshift sign) and at the last plane, on two
+    wavelengths, against the oracle's fields; every row kernel for complex64."""
+    lams = np.array([530e-9, 570e-9])
+    dx, z, scal = 2e-3 / n * 4, 0.05, 4 * np.pi
+    f0 = inputs.random_field((2, n, n), seed=21)
+    ref = inputs.random_field((2, n, n), seed=22)
+    cdt = coro.C128 if dtype == torch.complex128 else coro.C64
+    x = to_dev(f0, dtype)
+    ref_t = to_dev(ref, dtype)
+    out = [torch.zeros((2, n, n), dtype=torch.float32, device="cuda") for _ in range(2)]
+    els = [coro.element(coro.EL_PHASE_GRAD, plane=1, scalar=scal, ref=ref_t, store=out[0]),
+           coro.element(coro.EL_PHASE_GRAD, plane=2, scalar=scal, ref=ref_t, store=out[1])]
+    plan = coro.FresnelPlan(ctx, n=n, batch=2, pixelscale=dx, wavelength=lams, distances=[z, -0.5 * z],
+                            elements=els, dtype=cdt)
+    want = []
+    for b in range(2):
+        g1 = propagation.angular_spectrum(f0[b], dx, lams[b], z)
+        g2 = propagation.angular_spectrum(g1, dx, lams[b], -0.5 * z)
+        want.append([scal / lams[b] * 2 * np.imag(g * np.conj(ref[b])) for g in (g1, g2)])
+    rows = KERNEL_CHOICES[n][0] if dtype == torch.complex64 else [None]
+    for rv in rows:
+        if rv is not None:
+            plan.set_pass_kernel(rv, 0)
+        y = x.clone()
+        for o in out:
+            o.fill_(float("nan"))
+        plan.execute(y)
+        for k in range(2):
+            got = out[k].cpu().numpy()
+            for b in range(2):
+                w = want[b][k]
+                err = np.linalg.norm(got[b] - w) / np.linalg.norm(w)
+                assert err < 1e-5, (rv, k, b, err)             # the map is written in float
+
+
 def test_checkpoint_after_direct_hop_and_apply(ctx):
     """A checkpoint at the focal plane of a direct hop (natural layout, new pixel scale), on
     two wavelengths; coro_apply_element with a checkpoint copies the field."""

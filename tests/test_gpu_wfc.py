@@ -23,9 +23,12 @@ def rel_l2(got, ref):
     return float(np.linalg.norm(np.asarray(got, np.complex128) - ref) / np.linalg.norm(ref))
 
 
-def test_dm_opd_and_correlate(ctx):
-    n, dx, na = 256, 1.0 / 200, 12
-    pitch = 1.0 / na
+@pytest.mark.parametrize("n,dx,na,pitch", [(256, 1.0 / 200, 12, 1.0 / 12), (1024, 0.048 / 1024, 48, 1e-3),
+                                           (4096, 0.048 / 1024, 48, 1e-3)])
+def test_dm_opd_and_correlate(ctx, n, dx, na, pitch):
+    """Gaussian-influence synthesis and its transpose (FWHM one pitch) against the oracle's
+    influence matrices: a coarse grid, the 1024^2 pupil of the Lyot workloads and the 4096^2
+    grid of the wavefront-control workload (DM over its central 1024 pixels)."""
     h = inputs.dm_heights(5, na, 2)
     ht = torch.from_numpy(h.astype(np.float32)).cuda()
     opd = coro.dm_opd(ctx, ht, pitch, pitch, n, dx, 2.0).cpu().numpy()
