@@ -532,7 +532,7 @@ class FresnelPlan:
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_kernel(self.handle, i, ct.byref(p), ct.byref(w)))
         row, _ = self.pass_info(i)
         kind = "row_pass" if row else "col_pass"
-        name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide")[p.value]
+        name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide", "", "_mixed")[p.value]
         return f"{name}<{self.n}>" if row else f"{name}<{self.n},{w.value}>"
 
     def set_pass_kernel(self, row_variant: int, col_lines: int) -> None:

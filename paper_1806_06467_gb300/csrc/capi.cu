@@ -73,6 +73,16 @@ namespace {
 // Per-pass twiddle blocks of an n-point line FFT (radix 16 then one smaller radix): entry
 // m of the block with span ns is W_{ns R}^{r k}, r = 1 + m / ns, k = m % ns, evaluated in FP64
 // (sincospi of an exact rational) and rounded. Entries past the last block stay unused.
+// W_n^m = exp(-2 pi i m / n) for m in [0, n), FP64-evaluated.
+template <typename C>
+__global__ void lin_twiddle_kernel(C* tw, int n) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)n, &s, &c);
+    tw[m] = mk<C>((typename real_of<C>::type)c, (typename real_of<C>::type)s);
+}
+
 template <typename C>
 __global__ void twiddle_kernel(C* tw, int n) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,8 +146,14 @@ const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st) {
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) { *st = cuda_fail(e, "cudaMalloc(twiddles)"); return nullptr; }
     const int th = 256;
-    if (dbl) twiddle_kernel<double2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((double2*)p, n);
-    else twiddle_kernel<float2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((float2*)p, n);
+    if (!is_pow2(n)) {                          // mixed-radix passes: the linear table W_n^m
+        if (dbl) lin_twiddle_kernel<double2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((double2*)p, n);
+        else lin_twiddle_kernel<float2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((float2*)p, n);
+    } else if (dbl) {
+        twiddle_kernel<double2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((double2*)p, n);
+    } else {
+        twiddle_kernel<float2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((float2*)p, n);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) { cudaFree(p); *st = cuda_fail(e, "twiddle_kernel"); return nullptr; }
     cache[n] = p;
@@ -269,8 +285,10 @@ static coro_status check_wf(const char* fn, coro_ctx ctx, const coro_wavefront* 
     if (wf->dtype != CORO_C64 && wf->dtype != CORO_C128) { set_error("%s: bad dtype %d", fn, wf->dtype); return CORO_EINVAL; }
     if (wf->batch < 1 || wf->batch > 65535) { set_error("%s: batch %d outside [1, 65535]", fn, wf->batch); return CORO_ESIZE; }
     const int nmax = wf->dtype == CORO_C64 ? 8192 : 4096;
-    if (!is_pow2(wf->n) || wf->n < 32 || wf->n > nmax) {
-        set_error("%s: n = %d must be a power of two in [32, %d]", fn, wf->n, nmax);
+    const bool pow2_ok = is_pow2(wf->n) && wf->n >= 32 && wf->n <= nmax;
+    if (!pow2_ok && (is_pow2(wf->n) || wf->n > 8192 || !mixed_length_ok(wf->n, wf->dtype == CORO_C128))) {
+        set_error("%s: n = %d must be a power of two in [32, %d], or even with prime factors up to 61 "
+                  "(complex64: n <= 8192, complex128: n <= 6022)", fn, wf->n, nmax);
         return CORO_ESIZE;
     }
     if (need_ps) {
@@ -457,6 +475,15 @@ coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int
                 split_f32(2.0 * el->sine_amplitude / lam[b], &fpar[4 * b], &fpar[4 * b + 3]);
                 fpar[4 * b + 1] = (float)fhi;
                 fpar[4 * b + 2] = (float)(f - fhi);
+            }
+            if (dbl) {                                   // complex128 passes: f and 2 amp / lambda in FP64
+                std::vector<double> dp((size_t)2 * batch);
+                for (int b = 0; b < batch; ++b) {
+                    dp[2 * b] = el->sine_freq * ps[b];
+                    dp[2 * b + 1] = 2.0 * el->sine_amplitude / lam[b];
+                }
+                out->zpoly = (const float*)db.add(dp.data(), dp.size() * sizeof(double), &st);
+                if (!out->zpoly) return st;
             }
             out->kind = DK_SINE;
             out->flags = el->axis ? 1 : 0;

@@ -162,39 +162,41 @@ __global__ void dm_gx_table(DmGeom g, int len, float* __restrict__ gx, int* __re
 }
 
 // grid (ceil(span / 8), batch), 256 threads: one warp per row, all na columns of U. Shared:
-// the gx table (na * len) and each warp's row over the union of the windows (span).
+// each warp's row over the union of the windows (span); the gx table is read through L1.
 __global__ void __launch_bounds__(256)
 dm_correlate_u(const float* __restrict__ w, DmGeom g, int len, int span, const float* __restrict__ gx,
                const int* __restrict__ xs_tab, float* __restrict__ U) {
     extern __shared__ float usm[];
-    float* gxs = usm;                                        // [na][len]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* row = usm + (size_t)g.na * len + (size_t)warp * span;
-    for (int i = threadIdx.x; i < g.na * len; i += blockDim.x) gxs[i] = __ldg(gx + i);
+    float* row = usm + (size_t)warp * span;
     const int r = blockIdx.x * 8 + warp, b = blockIdx.y;
+    if (r >= span) return;                                   // warps are independent
     const int xs0 = xs_tab[0];
     const int y = xs0 + r;
-    const bool live = r < span && y >= 0 && y < g.n;
-    if (live) {
-        const float* wr = w + ((size_t)b * g.n + y) * g.n;
-        for (int i = lane; i < span; i += 32) {
-            const int x = xs0 + i;
-            row[i] = (x >= 0 && x < g.n) ? __ldg(wr + x) : 0.f;
-        }
-    }
-    __syncthreads();                                         // gx table in place
-    if (r >= span) return;
     float* ub = U + ((size_t)b * span + r) * g.na;
-    if (!live) {
+    if (y < 0 || y >= g.n) {
         for (int q = lane; q < g.na; q += 32) ub[q] = 0.f;
         return;
     }
+    const float* wr = w + ((size_t)b * g.n + y) * g.n;
+#pragma unroll 4
+    for (int i = lane; i < span; i += 32) {
+        const int x = xs0 + i;
+        row[i] = (x >= 0 && x < g.n) ? __ldg(wr + x) : 0.f;
+    }
+    __syncwarp();
     for (int q = 0; q < g.na; ++q) {
         const int off = xs_tab[q] - xs0;
         const int kend = min(len, span - off);
-        const float* gq = gxs + (size_t)q * len;
-        float sum = 0.f;
-        for (int k = lane; k < kend; k += 32) sum = fmaf(row[off + k], gq[k], sum);
+        const float* gq = gx + (size_t)q * len;
+        float s0 = 0.f, s1 = 0.f;
+        int k = lane;
+        for (; k + 32 < kend; k += 64) {
+            s0 = fmaf(row[off + k], __ldg(gq + k), s0);
+            s1 = fmaf(row[off + k + 32], __ldg(gq + k + 32), s1);
+        }
+        if (k < kend) s0 = fmaf(row[off + k], __ldg(gq + k), s0);
+        float sum = s0 + s1;
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
         if (lane == 0) ub[q] = sum;
     }
@@ -253,7 +255,7 @@ size_t correlate_sizes(const DmGeom& g, double dx, double pitch, int* len, int* 
     if (l > 65536 || sp > 65536) return 0;
     *len = (int)l;
     *span = (int)sp;
-    const size_t bytes = ((size_t)g.na * *len + 8 * (size_t)*span) * sizeof(float);
+    const size_t bytes = 8 * (size_t)*span * sizeof(float);
     return bytes <= 200 * 1024 ? bytes : 0;
 }
 

@@ -21,10 +21,12 @@ enum DevElemKind : int {
     DK_APERTURE = 1,   // ithr: [outer r2 max, obscuration r2 max (-1 none), spider |k| max (-1 none)]
     DK_CIRCLE = 2,     // ithr: [r2 max]; flags bit0: opaque inside
     DK_TABLE = 3,      // separable table tab[b][x] * tab[b][y] (lens, QPF)
-    DK_OPD_MAP = 4,    // fpar: [2 / lambda]; map [n][n] or [b][n][n]; optional amplitude
-    DK_ZERNIKE = 5,    // ithr: [r2 max]; fpar: [2 / lambda, dx/R]; zpoly: combined polynomials
-    DK_SINE = 6,       // fpar: [2 amp / lambda, f_hi, f_lo] (cycles per pixel split), flags: axis
-    DK_SCALAR = 7,     // fpar: [s]
+    DK_OPD_MAP = 4,    // fpar: [2 / lambda as hi, lo]; map [n][n] or [b][n][n]; optional amplitude
+    DK_ZERNIKE = 5,    // ithr: [r2 max]; fpar: [2 / lambda, dx/R, their lo parts]; zpoly: combined
+                       // polynomials (doubles for complex128)
+    DK_SINE = 6,       // fpar: [2 amp / lambda, f_hi, f_lo, -] (cycles per pixel split), flags: axis;
+                       // complex128: zpoly -> [batch][f, 2 amp / lambda] doubles
+    DK_SCALAR = 7,     // fpar: [s as hi, lo]
     DK_CHECKER = 8,    // (-1)^(x+y)
     DK_CONJ = 9,       // complex conjugate (direct hops with z < 0: IDFT(y) = conj(DFT(conj y)))
     DK_STORE = 10,     // checkpoint: copy the field to dst[b * map_bstride + y * n + x], the field
@@ -76,16 +78,16 @@ template <typename C> constexpr bool kF64 = std::is_same<C, double2>::value;
 
 // Zernike phase for complex128 passes: the polynomial table is FP64 (zpoly then points at
 // doubles), 2 / lambda and dx / R come as float pairs (hi + lo).
-template <int N, int XS>
-__device__ __forceinline__ void zernike_f64(double2 (&v)[16], int x0, int ky, int b, const DevElem& e) {
+template <int XS, int S>
+__device__ __forceinline__ void zernike_f64(double2 (&v)[S], int x0, int ky, int b, int n, const DevElem& e) {
     const int t0 = e.ithr[4 * b];
     const double k = (double)e.fpar[4 * b] + (double)e.fpar[4 * b + 2];
     const double sc = (double)e.fpar[4 * b + 1] + (double)e.fpar[4 * b + 3];
     const double* zp = reinterpret_cast<const double*>(e.zpoly);
     const double zy = ky * sc;
 #pragma unroll 1
-    for (int s = 0; s < 16; ++s) {
-        const int kx = x0 + s * XS - N / 2;
+    for (int s = 0; s < S; ++s) {
+        const int kx = x0 + s * XS - n / 2;
         if (kx * kx + ky * ky > t0) continue;        // zero OPD outside the disk
         const double zx = kx * sc;
         const double rho2 = zx * zx + zy * zy;
@@ -108,15 +110,16 @@ __device__ __forceinline__ void zernike_f64(double2 (&v)[16], int x0, int ky, in
     }
 }
 
-// Multiply the 16 samples a thread holds (row y of item b, columns x0 + s*XS) by every
-// element of the list. The element loop is outermost and uniform across the block.
-// pre_idx >= 0: element pre_idx is an OPD map whose 16 values this thread already holds in
+// Multiply the S samples a thread holds (row y of item b of an n x n field, columns
+// x0 + s*XS) by every element of the list. The element loop is outermost and uniform across
+// the block.
+// pre_idx >= 0: element pre_idx is an OPD map whose S values this thread already holds in
 // pre (loaded early so that their latency hides behind the inverse FFT).
-template <typename C, int N, int XS>
-__device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, const PassElems& pe,
-                                            const float (&pre)[16], int pre_idx) {
+template <typename C, int XS, int S>
+__device__ __forceinline__ void apply_elems_n(C (&v)[S], int x0, int y, int b, int n, const PassElems& pe,
+                                              const float (&pre)[S], int pre_idx) {
     using R = typename real_of<C>::type;
-    const int ky = y - N / 2;
+    const int ky = y - n / 2;
     for (int i = 0; i < pe.count; ++i) {
         const DevElem& e = pe.e[i];
         switch (e.kind) {
@@ -124,8 +127,8 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                 const int* th = e.ithr + 4 * b;
                 const int t0 = th[0], t1 = th[1], t2 = th[2];
 #pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const int kx = x0 + s * XS - N / 2;
+                for (int s = 0; s < S; ++s) {
+                    const int kx = x0 + s * XS - n / 2;
                     const int r2 = kx * kx + ky * ky;
                     bool pass = r2 <= t0;
                     if (t1 >= 0 && r2 <= t1) pass = false;
@@ -138,27 +141,27 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                 const int t0 = e.ithr[4 * b];
                 const bool opaque_inside = e.flags & 1;
 #pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const int kx = x0 + s * XS - N / 2;
+                for (int s = 0; s < S; ++s) {
+                    const int kx = x0 + s * XS - n / 2;
                     const bool inside = kx * kx + ky * ky <= t0;
                     if (inside == opaque_inside) v[s] = mk<C>(0, 0);
                 }
                 break;
             }
             case DK_TABLE: {
-                const C* t = reinterpret_cast<const C*>(e.tab) + (size_t)b * N;
+                const C* t = reinterpret_cast<const C*>(e.tab) + (size_t)b * n;
                 const C ty = t[y];
 #pragma unroll
-                for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], cmul(__ldg(t + x0 + s * XS), ty));
+                for (int s = 0; s < S; ++s) v[s] = cmul(v[s], cmul(__ldg(t + x0 + s * XS), ty));
                 break;
             }
             case DK_OPD_MAP: {
-                const size_t off = (size_t)b * e.map_bstride + (size_t)y * N + x0;
+                const size_t off = (size_t)b * e.map_bstride + (size_t)y * n + x0;
                 if constexpr (kF64<C>) {
                     // complex128: 2 / lambda as a float pair, the phase in FP64
                     const double k = (double)e.fpar[4 * b] + (double)e.fpar[4 * b + 1];
 #pragma unroll
-                    for (int s = 0; s < 16; ++s) {
+                    for (int s = 0; s < S; ++s) {
                         const double ph = k * (double)(i == pre_idx ? pre[s] : __ldg(e.map + off + s * XS));
                         double sn, cs;
                         sincospi(ph, &sn, &cs);
@@ -168,7 +171,7 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                 } else {
                     const float k = e.fpar[4 * b];
 #pragma unroll
-                    for (int s = 0; s < 16; ++s) {
+                    for (int s = 0; s < S; ++s) {
                         // phase / pi = (2 / lambda) * OPD
                         const float ph = k * (i == pre_idx ? pre[s] : __ldg(e.map + off + s * XS));
                         float sn, cs;
@@ -182,17 +185,17 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
             }
             case DK_ZERNIKE: {
                 if constexpr (kF64<C>) {
-                    zernike_f64<N, XS>(v, x0, ky, b, e);
+                    zernike_f64<XS, S>(v, x0, ky, b, n, e);
                 } else {
                     const int t0 = e.ithr[4 * b];
                     const float k = e.fpar[4 * b], sc = e.fpar[4 * b + 1];
                     const float zy = ky * sc;
                     // the polynomial is evaluated in a rolled loop (few registers); only the phase
-                    // of each of the 16 samples is kept
-                    float ph[16];
+                    // of each of the S samples is kept
+                    float ph[S];
 #pragma unroll 1
-                    for (int s = 0; s < 16; ++s) {
-                        const int kx = x0 + s * XS - N / 2;
+                    for (int s = 0; s < S; ++s) {
+                        const int kx = x0 + s * XS - n / 2;
                         float opd = 0.f;                          // zero OPD outside the disk
                         if (kx * kx + ky * ky <= t0) {
                             const float zx = kx * sc;
@@ -214,7 +217,7 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                         ph[s] = k * opd;
                     }
 #pragma unroll
-                    for (int s = 0; s < 16; ++s) {
+                    for (int s = 0; s < S; ++s) {
                         float sn, cs;
                         phasor_hc<C>(ph[s], sn, cs);
                         v[s] = cmul(v[s], mk<C>((R)cs, (R)sn));
@@ -226,10 +229,12 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                 const float* p = e.fpar + 4 * b;
                 const bool along_y = e.flags & 1;
                 if constexpr (kF64<C>) {
-                    const double amp = (double)p[0] + (double)p[3], f = (double)p[1] + (double)p[2];
+                    // cycles per pixel and 2 amp / lambda in FP64 (zpoly points at [batch][2] doubles)
+                    const double* dp = reinterpret_cast<const double*>(e.zpoly) + 2 * b;
+                    const double f = dp[0], amp = dp[1];
 #pragma unroll
-                    for (int s = 0; s < 16; ++s) {
-                        const int kk = along_y ? ky : x0 + s * XS - N / 2;
+                    for (int s = 0; s < S; ++s) {
+                        const int kk = along_y ? ky : x0 + s * XS - n / 2;
                         double a = (double)kk * f;
                         a -= rint(a);
                         double sn, cs;
@@ -238,8 +243,8 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                     }
                 } else {
 #pragma unroll
-                    for (int s = 0; s < 16; ++s) {
-                        const int kk = along_y ? ky : x0 + s * XS - N / 2;
+                    for (int s = 0; s < S; ++s) {
+                        const int kk = along_y ? ky : x0 + s * XS - n / 2;
                         // cycles = kk * f with f = f_hi + f_lo and kk * f_hi exact in FP32
                         float a = (float)kk * p[1];
                         a -= rintf(a);
@@ -254,28 +259,28 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
             case DK_SCALAR: {
                 const R sc = kF64<C> ? (R)((double)e.fpar[4 * b] + (double)e.fpar[4 * b + 1]) : (R)e.fpar[4 * b];
 #pragma unroll
-                for (int s = 0; s < 16; ++s) v[s] = cscale(v[s], sc);
+                for (int s = 0; s < S; ++s) v[s] = cscale(v[s], sc);
                 break;
             }
             case DK_CHECKER: {
 #pragma unroll
-                for (int s = 0; s < 16; ++s)
+                for (int s = 0; s < S; ++s)
                     if ((x0 + s * XS + y) & 1) v[s] = mk<C>(-v[s].x, -v[s].y);
                 break;
             }
             case DK_CONJ: {
 #pragma unroll
-                for (int s = 0; s < 16; ++s) v[s] = cconj(v[s]);
+                for (int s = 0; s < S; ++s) v[s] = cconj(v[s]);
                 break;
             }
             case DK_PHASE_GRAD: {
-                const size_t off = (size_t)b * e.map_bstride + (size_t)y * N + x0;
+                const size_t off = (size_t)b * e.map_bstride + (size_t)y * n + x0;
                 const C* rf = static_cast<const C*>(e.tab) + off;
                 float* d = static_cast<float*>(e.dst) + off;
                 const R wgt = kF64<C> ? (R)((double)e.fpar[4 * b] + (double)e.fpar[4 * b + 1]) : (R)e.fpar[4 * b];
                 const bool chk = e.flags & 1;
 #pragma unroll
-                for (int s = 0; s < 16; ++s) {
+                for (int s = 0; s < S; ++s) {
                     const C r = __ldg(rf + s * XS);
                     R im = v[s].y * r.x - v[s].x * r.y;                 // Im(v conj(r))
                     if (chk && ((x0 + s * XS + y) & 1)) im = -im;
@@ -284,10 +289,10 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                 break;
             }
             case DK_STORE: {
-                C* d = static_cast<C*>(e.dst) + (size_t)b * e.map_bstride + (size_t)y * N + x0;
+                C* d = static_cast<C*>(e.dst) + (size_t)b * e.map_bstride + (size_t)y * n + x0;
                 const bool chk = e.flags & 1;
 #pragma unroll
-                for (int s = 0; s < 16; ++s) {
+                for (int s = 0; s < S; ++s) {
                     const bool neg = chk && ((x0 + s * XS + y) & 1);
                     __stcs(d + s * XS, neg ? mk<C>(-v[s].x, -v[s].y) : v[s]);
                 }
@@ -297,6 +302,13 @@ __device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, co
                 break;
         }
     }
+}
+
+// The same for a compile-time line length (the power-of-two pass kernels).
+template <typename C, int N, int XS>
+__device__ __forceinline__ void apply_elems(C (&v)[16], int x0, int y, int b, const PassElems& pe,
+                                            const float (&pre)[16], int pre_idx) {
+    apply_elems_n<C, XS, 16>(v, x0, y, b, N, pe, pre, pre_idx);
 }
 
 // Elements on a packed row pair: the samples a thread holds for rows ya (lane 0) and ya + 1
@@ -1300,6 +1312,9 @@ int col_lines_default(int n, bool dbl);
 // Candidate column variants (at most 8) and row variants the plan autotuner times for n
 // (complex64).
 int col_candidates(int n, int* out);
+// Whether the mixed-radix passes take line length n (even, not a power of two, prime factors
+// up to 61, two lines in 200 KB of shared memory).
+bool mixed_length_ok(int n, bool dbl);
 int row_variant_count(int n);
 // The kernels used without tuning (CORO_AUTOTUNE=0, or sizes without candidates).
 int row_variant_default(int n);

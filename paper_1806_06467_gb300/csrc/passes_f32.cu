@@ -1,5 +1,6 @@
 // passes_f32.cu -- complex64 row/column pass launchers (N = 32 ... 8192).
 #include "passes_launch.cuh"
+#include "mixed.cuh"
 
 namespace coro {
 
@@ -27,7 +28,7 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
             if (l.variant == 2) return row_launch_units<float2, 4096, 4, 2>(a, l);
             return l.variant == 1 ? row_launch<float2, 4096>(a, l) : row_launch_persistent<float2, 4096>(a, l);
         case 8192: return l.variant == 1 ? row_launch<float2, 8192>(a, l) : row_launch_persistent<float2, 8192>(a, l);
-        default: return cudaErrorInvalidValue;
+        default: return row_launch_mixed<float2>(n, a, l);
     }
 }
 
@@ -64,7 +65,7 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
             if (lines == -1) return col_launch_persistent<float2, 4096, 2>(a, l);
             return lines == 2 ? col_launch<float2, 4096, 2>(a, l) : col_launch<float2, 4096, 4>(a, l);
         case 8192: return lines == 1 ? col_launch<float2, 8192, 1>(a, l) : col_launch<float2, 8192, 2>(a, l);
-        default: return cudaErrorInvalidValue;
+        default: return col_launch_mixed<float2>(n, a, l);
     }
 }
 
@@ -100,8 +101,15 @@ int col_candidates(int n, int* out) {
 // row variants: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row pairs
 int row_variant_count(int n) { return (n >= 1024 && n <= 4096) ? 4 : n == 8192 ? 2 : 1; }
 
+bool mixed_length_ok(int n, bool dbl) { return dbl ? mixed_supported<double2>(n) : mixed_supported<float2>(n); }
+
 void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persistent, int* out_lines) {
     int p = 0, w = 0;
+    if (n & (n - 1)) {                                      // mixed-radix passes
+        if (persistent) *persistent = 6;
+        if (out_lines) *out_lines = row ? 1 : (dbl ? mixed_col_lines<double2>(n) : mixed_col_lines<float2>(n));
+        return;
+    }
     if (variant < 0) variant = row_variant_default(n);
     if (row) {                                              // mirrors launch_row_pass
         p = (!dbl && n >= 1024) ? (variant == 1 ? 0 : (variant == 2 || variant == 3) && n <= 4096 ? variant : 1) : 0;

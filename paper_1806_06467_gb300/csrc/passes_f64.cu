@@ -1,5 +1,7 @@
-// passes_f64.cu -- complex128 row/column pass launchers (N = 32 ... 4096).
+// passes_f64.cu -- complex128 row/column pass launchers (N = 32 ... 4096; other even N through
+// the mixed-radix passes).
 #include "passes_launch.cuh"
+#include "mixed.cuh"
 
 namespace coro {
 
@@ -15,7 +17,7 @@ cudaError_t launch_row_pass<double2>(int n, const RowArgs<double2>& a, const Pas
         case 1024: return row_launch<double2, 1024>(a, l);
         case 2048: return row_launch<double2, 2048>(a, l);
         case 4096: return row_launch<double2, 4096>(a, l);
-        default: return cudaErrorInvalidValue;
+        default: return row_launch_mixed<double2>(n, a, l);
     }
 }
 
@@ -32,7 +34,7 @@ cudaError_t launch_col_pass<double2>(int n, int lines, const ColArgs<double2>& a
         case 1024: return col_launch<double2, 1024, 4>(a, l);
         case 2048: return col_launch<double2, 2048, 2>(a, l);
         case 4096: return col_launch<double2, 4096, 1>(a, l);
-        default: return cudaErrorInvalidValue;
+        default: return col_launch_mixed<double2>(n, a, l);
     }
 }
 

@@ -472,6 +472,31 @@ def test_mixed_plan_direct_then_as(ctx):
         assert rel_l2(got[b], e) < 1e-5
 
 
+@pytest.mark.parametrize("col", [0, -1])
+def test_direct_hop_column_kernels_2048(ctx, col):
+    """A direct (single-transform) hop followed by an angular-spectrum hop at 2048^2 on two
+    wavelengths, with the default column kernel and with the persistent one (their
+    forward-only form for the direct hop)."""
+    n, npix = 2048, 512
+    dx = 1.0 / npix
+    lams = np.array([500e-9, 600e-9])
+    els = [coro.element(coro.EL_APERTURE, plane=0, radius=0.5),
+           coro.element(coro.EL_LENS, plane=0, focal_length=10.0),
+           coro.element(coro.EL_CIRCLE, plane=1, radius=40e-6, flags=coro.ELF_OPAQUE_INSIDE)]
+    plan = coro.FresnelPlan(ctx, n=n, batch=2, pixelscale=dx, wavelength=lams, distances=[10.0, 0.05],
+                            methods=[coro.FRESNEL_DIRECT, coro.FRESNEL_AS], elements=els, init_uniform=True)
+    plan.set_pass_kernel(3, col)
+    x = torch.empty((2, n, n), dtype=torch.complex64, device="cuda")
+    plan.execute(x)
+    got = x.cpu().numpy()
+    for b in range(2):
+        e = optics.circular_aperture(n, dx, 0.5) * optics.thin_lens(n, dx, lams[b], 10.0)
+        e, du = propagation.direct_fresnel(e, dx, lams[b], 10.0)
+        e = e * optics.circle_stop(n, du, 40e-6, opaque_inside=True)
+        e = propagation.angular_spectrum(e, du, lams[b], 0.05)
+        assert rel_l2(got[b], e) < 1e-5
+
+
 def test_airy_fp64_direct(ctx):
     """128-px 1 m aperture on 256^2 complex128, lens 10 m, direct Fresnel 10 m to focus."""
     n, npix, lam = 256, 128, 500e-9

@@ -28,8 +28,10 @@ def brute_centred_dft2(f):
     return out
 
 
-@pytest.mark.parametrize("n", [4, 8, 16])
+@pytest.mark.parametrize("n", [4, 8, 16, 12, 18, 30])
 def test_centred_dft_matches_brute_force(n):
+    """Powers of two and the lengths of the mixed-radix passes (12 = 4 x 3; 18 and 30 have an
+    odd N/2, where the per-axis sign (-1)^(N/2) of the checkerboard centring is -1)."""
     f = inputs.random_field((n, n), seed=n)
     np.testing.assert_allclose(propagation.centred_dft2(f), brute_centred_dft2(f),
                                rtol=0, atol=1e-12 * n * n)
