@@ -509,6 +509,34 @@ def wfc_bench(ctx, device, steps: int) -> dict:
                         "wavelengths 525-575 nm (3xTF32); loss + dL/dh per step"}
 
 
+def relay_mixed_bench(ctx, device, steps: int, n: int = 2800, npix: int = 700) -> dict:
+    """The six-plane relay at a line length that is not a power of two (Sec. 3.1 times
+    N = 2800 against the powers of two): mixed-radix passes, K relays replayed as one graph."""
+    import numpy as np
+    import torch
+
+    from paper_1806_06467_gb300 import coro, inputs
+    w = inputs.RelayWorkload(n=n, npix=npix, seed=0)
+    maps = [torch.from_numpy(m.astype(np.float32)).to(device) for m in w.psd_maps()]
+    plan = coro.FresnelPlan(ctx, n=n, batch=1, pixelscale=w.dx, wavelength=w.wavelength_m,
+                            distances=list(w.distances()), elements=relay_elements(w, maps), init_uniform=True)
+    field = torch.empty((1, n, n), dtype=torch.complex64, device=device)
+    stream = torch.cuda.current_stream(device)
+    plan.use_graph(True)
+    plan.execute_n(field, steps)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plan.execute_n(field, steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    kernels = sorted({plan.pass_kernel(i) for i in range(plan.launch_count)})
+    plan.close()
+    return {"value": HOPS * 1e3 / ms, "unit": "planes/s", "ms_per_relay": ms, "n": n, "kernels": kernels,
+            "workload": f"six-plane relay (5 hops) at N = {n} (npix {npix}), complex64, mixed-radix passes"}
+
+
 def coronagraph_plain(device, steps: int, n_lambda: int = 21, n_probe: int = 8) -> dict:
     """Plain per-wavelength FP32 GPU form: torch.matmul (cuBLAS cgemm, complex64) MFT chain per
     wavelength over the 8 probe pupils, bases precomputed; same sizes as the batched plan."""
@@ -732,6 +760,7 @@ def main():
     if not args.no_coronagraph:
         extras["spc_system"] = spc_system_bench(ctx, device, max(3, args.steps // 2))
         extras["wfc_gradient"] = wfc_bench(ctx, device, max(3, args.steps // 4))
+        extras["relay_mixed_radix"] = relay_mixed_bench(ctx, device, max(3, args.steps // 2))
     if rank == 0 and not args.no_plain:
         extras["plain_gpu"] = plain_gpu(n, maps_np, w, max(3, args.steps // 4), 2, device)
         extras["plain_gpu"]["speedup_of_coro"] = value / world / extras["plain_gpu"]["value"]
