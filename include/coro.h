@@ -421,7 +421,7 @@ coro_status coro_lyot_plan_gradient(coro_plan plan, const void* pupil, const dou
  * coro_wfc_plan_evaluate: heights device float [2][n_act][n_act] (metres of surface, DM1 then
  * DM2); loss (host) and per_item (host [batch]) optional; grad device float [2][n_act][n_act]
  * = dL/dheights, or NULL for the forward only. Synchronises the stream. The plan holds four
- * batch x n_fresnel^2 complex64 fields (checkpoints E0, E1, work, adjoint).
+ * resident x n_fresnel^2 complex64 fields (checkpoints E0, E1, work, adjoint).
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
     int batch;                    /* wavelengths                                           */
@@ -436,9 +436,15 @@ typedef struct {
     int m_det;
     const coro_lyot_item* items;  /* host [batch], one Lyot item per wavelength            */
     int precision;                /* CORO_MFT_3XTF32 or CORO_MFT_3XBF16                    */
+    int max_resident;             /* wavelengths held in HBM at once (4 x 8 n_fresnel^2    */
+                                  /* bytes each); 0 = as many as fit in 70 % of the free   */
+                                  /* device memory. The band runs in chunks of that many,  */
+                                  /* with the same results (per-item sums in item order).  */
 } coro_wfc_desc;
 
 coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* desc, coro_plan* out);
+/* Wavelengths resident at once and the number of chunks the band runs in (either may be NULL). */
+coro_status coro_wfc_plan_resident(coro_plan plan, int* resident, int* chunks);
 /* Normalisation peaks of the zero-height system (host [batch]); computed on first use. */
 coro_status coro_wfc_plan_peak(coro_plan plan, double* peak_out);
 coro_status coro_wfc_plan_evaluate(coro_plan plan, const float* heights, double* loss, double* per_item,

@@ -75,7 +75,8 @@ class WfcDesc(ct.Structure):
     _fields_ = [("batch", ct.c_int), ("wavelength", ct.POINTER(ct.c_double)), ("n_fresnel", ct.c_int),
                 ("diam_m", ct.c_double), ("npix", ct.c_int), ("z_m", ct.c_double), ("n_act", ct.c_int),
                 ("act_pitch_m", ct.c_double), ("act_fwhm_m", ct.c_double), ("lyot_frac", ct.c_double),
-                ("m_det", ct.c_int), ("items", ct.POINTER(LyotItem)), ("precision", ct.c_int)]
+                ("m_det", ct.c_int), ("items", ct.POINTER(LyotItem)), ("precision", ct.c_int),
+                ("max_resident", ct.c_int)]
 
 
 _P = ct.c_void_p
@@ -85,6 +86,7 @@ _SIGS = {
                                            ct.c_longlong]),
     "coro_wfc_plan_create": (ct.c_int, [_P, ct.POINTER(WfcDesc), ct.POINTER(_P)]),
     "coro_wfc_plan_peak": (ct.c_int, [_P, ct.POINTER(ct.c_double)]),
+    "coro_wfc_plan_resident": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "coro_wfc_plan_evaluate": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), _P]),
     "coro_dm_opd": (ct.c_int, [_P, _P, ct.c_int, ct.c_int, ct.c_double, ct.c_double, ct.c_int, ct.c_double,
                                ct.c_double, _P]),

@@ -18,8 +18,15 @@
 // dphi2 tap uses 2 Im(G2 conj(E2)) = 2 Im(G1 conj(E1)) with G1 = exp(-i phi2) G2, so it sits
 // after the conjugate phase and needs only E1. Each tap writes one weighted map per
 // wavelength; the DM correlation reads them per wavelength and a last kernel sums over them.
+//
+// HBM budget: the four full-grid fields per wavelength (checkpoints E0, E1, the Lyot pupil /
+// tap maps, the adjoint field) are 32 N^2 bytes each, 2 GiB per wavelength at N = 8192. The
+// plan keeps at most `resident` wavelengths in memory and runs the band in chunks of that
+// many (one set of fused plans and one Lyot plan per chunk, all on the same buffers); the
+// gradient sums the chunks' contributions in order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <memory>
 #include <vector>
@@ -28,15 +35,23 @@
 
 namespace {
 
-// grad[dm][p][q] = sum_b part[dm][b][p][q]
-__global__ void sum_items_kernel(const float* __restrict__ part, int batch, int per_dm, float* __restrict__ grad) {
+// grad[dm][p][q] (+)= sum_b part[dm][b][p][q]  (accumulate: add to what grad holds)
+__global__ void sum_items_kernel(const float* __restrict__ part, int batch, int per_dm, int accumulate,
+                                 float* __restrict__ grad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, dm = blockIdx.y;
     if (i >= per_dm) return;
     const float* src = part + (size_t)dm * batch * per_dm + i;
-    float acc = 0.f;
+    float acc = accumulate ? grad[(size_t)dm * per_dm + i] : 0.f;
     for (int b = 0; b < batch; ++b) acc += src[(size_t)b * per_dm];
     grad[(size_t)dm * per_dm + i] = acc;
 }
+
+// One group of wavelengths [b0, b0 + nb) resident at a time, with its own plans.
+struct Chunk {
+    int b0 = 0, nb = 0;
+    coro_plan lyot = nullptr;
+    coro_plan fwd = nullptr, adj = nullptr;     // fused Fresnel plans of the two chains
+};
 
 struct WfcPlan : coro_plan_s {
     coro_ctx ctx = nullptr;
@@ -44,20 +59,22 @@ struct WfcPlan : coro_plan_s {
     coro_wfc_desc d{};
     std::vector<double> lam, ps;
     std::vector<coro_lyot_item> items;
-    coro_plan lyot = nullptr;
-    coro_plan fwd = nullptr, adj = nullptr;     // fused Fresnel plans of the two chains
+    int resident = 0;                           // wavelengths whose fields fit at once
+    std::vector<Chunk> chunks;
     std::vector<void*> bufs;
     float2 *e0 = nullptr, *e1 = nullptr, *w = nullptr, *g = nullptr;
     float *opd1 = nullptr, *opd2 = nullptr, *opd2n = nullptr, *zero_h = nullptr;
-    float* part = nullptr;                      // [2][batch][n_act][n_act] per-wavelength dL/dh
+    float* part = nullptr;                      // [2][resident][n_act][n_act] per-wavelength dL/dh
     std::vector<double> peak;
     int kind() const override { return 3; }
     int launches() const override { return 0; }
     int timing_units() const override { return 0; }
     ~WfcPlan() override {
-        if (lyot) coro_plan_destroy(lyot);
-        if (fwd) coro_plan_destroy(fwd);
-        if (adj) coro_plan_destroy(adj);
+        for (Chunk& ch : chunks) {
+            if (ch.lyot) coro_plan_destroy(ch.lyot);
+            if (ch.fwd) coro_plan_destroy(ch.fwd);
+            if (ch.adj) coro_plan_destroy(ch.adj);
+        }
         coro::DeviceGuard gd(device);
         cudaDeviceSynchronize();
         for (void* p : bufs) cudaFree(p);
@@ -78,9 +95,8 @@ coro_element opd_elem(const float* map) {
     return e;
 }
 
-// Forward through the Fresnel section: the DM surfaces, then the fused plan, which writes
-// the checkpoints E0 and E1 and leaves E3 in w.
-coro_status fresnel_forward(WfcPlan* p, const float* heights) {
+// The DM surfaces of `heights` (shared by every wavelength and chunk).
+coro_status dm_maps(WfcPlan* p, const float* heights) {
     const coro_wfc_desc& d = p->d;
     coro_ctx c = p->ctx;
     const int nf = d.n_fresnel, na = d.n_act;
@@ -88,8 +104,7 @@ coro_status fresnel_forward(WfcPlan* p, const float* heights) {
     coro_status st;
     if ((st = coro_dm_opd(c, heights, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, 2.0, p->opd1)) != CORO_OK) return st;
     if ((st = coro_dm_opd(c, heights + na * na, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, 2.0, p->opd2)) != CORO_OK) return st;
-    if ((st = coro_dm_opd(c, heights + na * na, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, -2.0, p->opd2n)) != CORO_OK) return st;
-    return coro_fresnel_plan_execute(p->fwd, p->w, nullptr);
+    return coro_dm_opd(c, heights + na * na, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, -2.0, p->opd2n);
 }
 
 coro_element checkpoint_elem(int plane, void* store) {
@@ -100,10 +115,16 @@ coro_element checkpoint_elem(int plane, void* store) {
     return e;
 }
 
-// The two fused plans (their element maps and checkpoint buffers are the plan's own).
-coro_status make_chains(WfcPlan* p) {
+// The chunk's plans: Lyot chain and the two fused Fresnel chains (their element maps and
+// checkpoint buffers are the WFC plan's own).
+coro_status make_chunk(WfcPlan* p, Chunk& ch) {
     const coro_wfc_desc& d = p->d;
     const double z[2] = {d.z_m, -d.z_m};
+    const int nf = d.n_fresnel;
+    coro_lyot_desc ld{ch.nb, d.npix, (double)d.npix, d.lyot_frac, d.m_det, p->items.data() + ch.b0, d.precision};
+    coro_status st = coro_lyot_plan_create(p->ctx, &ld, &ch.lyot);
+    if (st != CORO_OK) return st;
+    if ((st = coro_lyot_plan_set_pupil_layout(ch.lyot, nf, (long long)nf * nf)) != CORO_OK) return st;
     coro_element fe[5]{};
     fe[0].kind = CORO_EL_APERTURE;
     fe[0].radius = 0.5 * d.diam_m;
@@ -114,21 +135,20 @@ coro_status make_chains(WfcPlan* p) {
     fe[4].plane = 1;
     coro_fresnel_desc fd{};
     fd.dtype = CORO_C64;
-    fd.batch = d.batch;
+    fd.batch = ch.nb;
     fd.n = d.n_fresnel;
-    fd.pixelscale = p->ps.data();
-    fd.wavelength = p->lam.data();
+    fd.pixelscale = p->ps.data() + ch.b0;
+    fd.wavelength = p->lam.data() + ch.b0;
     fd.n_planes = 3;
     fd.distance = z;
     fd.n_elements = 5;
     fd.elements = fe;
     fd.flags = CORO_PLAN_INIT_UNIFORM;
-    coro_status st = coro_fresnel_plan_create(p->ctx, &fd, &p->fwd);
-    if (st != CORO_OK) return st;
+    if ((st = coro_fresnel_plan_create(p->ctx, &fd, &ch.fwd)) != CORO_OK) return st;
     // per-wavelength dL/dh density maps in w (E3 is no longer needed by then): DM2 first
     const size_t npx = (size_t)d.n_fresnel * d.n_fresnel;
     float* dphi2 = reinterpret_cast<float*>(p->w);
-    float* dphi1 = dphi2 + (size_t)d.batch * npx;
+    float* dphi1 = dphi2 + (size_t)ch.nb * npx;
     coro_element ae[3]{};
     ae[0] = opd_elem(p->opd2n);
     ae[0].plane = 1;
@@ -144,9 +164,9 @@ coro_status make_chains(WfcPlan* p) {
     fd.n_elements = 3;
     fd.elements = ae;
     fd.flags = 0;
-    if ((st = coro_fresnel_plan_create(p->ctx, &fd, &p->adj)) != CORO_OK) return st;
-    if ((st = coro_plan_set_graph(p->fwd, 1)) != CORO_OK) return st;
-    return coro_plan_set_graph(p->adj, 1);
+    if ((st = coro_fresnel_plan_create(p->ctx, &fd, &ch.adj)) != CORO_OK) return st;
+    if ((st = coro_plan_set_graph(ch.fwd, 1)) != CORO_OK) return st;
+    return coro_plan_set_graph(ch.adj, 1);
 }
 
 float2* window(WfcPlan* p, float2* base) {
@@ -171,6 +191,9 @@ extern "C" coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* d
         coro::set_error("coro_wfc_plan_create: need diam, pitch, fwhm > 0, z != 0, n_act >= 1");
         return CORO_EINVAL;
     }
+    if (d->max_resident < 0) { coro::set_error("coro_wfc_plan_create: max_resident must be >= 0"); return CORO_EINVAL; }
+    for (int b = 0; b < d->batch; ++b)
+        if (!(d->wavelength[b] > 0)) { coro::set_error("coro_wfc_plan_create: wavelength[%d] must be > 0", b); return CORO_EINVAL; }
     coro::DeviceGuard gd(ctx->device);
     auto p = std::unique_ptr<WfcPlan>(new (std::nothrow) WfcPlan);
     if (!p) { coro::set_error("out of host memory"); return CORO_ENOMEM; }
@@ -182,12 +205,23 @@ extern "C" coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* d
     p->items.assign(d->items, d->items + d->batch);
     p->d.wavelength = p->lam.data();
     p->d.items = p->items.data();
-    coro_lyot_desc ld{d->batch, d->npix, (double)d->npix, d->lyot_frac, d->m_det, p->items.data(), d->precision};
-    coro_status st = coro_lyot_plan_create(ctx, &ld, &p->lyot);
-    if (st != CORO_OK) return st;
     const int nf = d->n_fresnel;
-    if ((st = coro_lyot_plan_set_pupil_layout(p->lyot, nf, (long long)nf * nf)) != CORO_OK) return st;
-    const size_t fbytes = (size_t)d->batch * nf * nf * sizeof(float2), mbytes = (size_t)nf * nf * sizeof(float);
+    const size_t item_bytes = (size_t)4 * nf * nf * sizeof(float2);       // E0, E1, w, g
+    // wavelengths resident at once: the caller's bound, else what fits in 70 % of the free
+    // memory next to a generous allowance for the Lyot plans' own buffers
+    int res = d->max_resident > 0 ? d->max_resident : d->batch;
+    if (d->max_resident == 0) {
+        size_t free_b = 0, total_b = 0;
+        cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+        if (e != cudaSuccess) return coro::cuda_fail(e, "coro_wfc_plan_create: cudaMemGetInfo");
+        const size_t per = item_bytes + (size_t)32 * d->npix * d->npix * sizeof(float2);
+        const size_t fit = (size_t)(0.7 * (double)free_b) / per;
+        res = (int)std::max<size_t>(1, std::min<size_t>((size_t)d->batch, fit));
+    }
+    p->resident = std::min(res, d->batch);
+    const int R = p->resident;
+    coro_status st = CORO_OK;
+    const size_t fbytes = (size_t)R * nf * nf * sizeof(float2), mbytes = (size_t)nf * nf * sizeof(float);
     p->e0 = (float2*)p->alloc(fbytes, &st);
     p->e1 = p->e0 ? (float2*)p->alloc(fbytes, &st) : nullptr;
     p->w = p->e1 ? (float2*)p->alloc(fbytes, &st) : nullptr;
@@ -196,15 +230,28 @@ extern "C" coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* d
     p->opd2 = p->opd1 ? (float*)p->alloc(mbytes, &st) : nullptr;
     p->opd2n = p->opd2 ? (float*)p->alloc(mbytes, &st) : nullptr;
     p->zero_h = p->opd2n ? (float*)p->alloc((size_t)2 * d->n_act * d->n_act * sizeof(float), &st) : nullptr;
-    p->part = p->zero_h ? (float*)p->alloc((size_t)2 * d->batch * d->n_act * d->n_act * sizeof(float), &st) : nullptr;
+    p->part = p->zero_h ? (float*)p->alloc((size_t)2 * R * d->n_act * d->n_act * sizeof(float), &st) : nullptr;
     if (!p->part) return st;
-    for (int b = 0; b < d->batch; ++b)
-        if (!(d->wavelength[b] > 0)) { coro::set_error("coro_wfc_plan_create: wavelength[%d] must be > 0", b); return CORO_EINVAL; }
     cudaError_t e = cudaMemsetAsync(p->zero_h, 0, (size_t)2 * d->n_act * d->n_act * sizeof(float), ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return coro::cuda_fail(e, "coro_wfc_plan_create");
-    if ((st = make_chains(p.get())) != CORO_OK) return st;
+    for (int b0 = 0; b0 < d->batch; b0 += R) {
+        p->chunks.emplace_back();
+        Chunk& ch = p->chunks.back();
+        ch.b0 = b0;
+        ch.nb = std::min(R, d->batch - b0);
+        if ((st = make_chunk(p.get(), ch)) != CORO_OK) return st;
+    }
     *out = p.release();
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_wfc_plan_resident(coro_plan plan, int* resident, int* chunks) {
+    coro::clear_error();
+    if (!plan || plan->kind() != 3) { coro::set_error("coro_wfc_plan_resident: not a wavefront-control plan"); return CORO_EINVAL; }
+    auto* p = static_cast<WfcPlan*>(plan);
+    if (resident) *resident = p->resident;
+    if (chunks) *chunks = (int)p->chunks.size();
     return CORO_OK;
 }
 
@@ -213,10 +260,16 @@ extern "C" coro_status coro_wfc_plan_peak(coro_plan plan, double* peak_out) {
     if (!plan || plan->kind() != 3) { coro::set_error("coro_wfc_plan_peak: not a wavefront-control plan"); return CORO_EINVAL; }
     auto* p = static_cast<WfcPlan*>(plan);
     coro::DeviceGuard gd(p->device);
-    coro_status st = fresnel_forward(p, p->zero_h);
-    if (st != CORO_OK) return st;
-    p->peak.assign(p->d.batch, 0.0);
-    if ((st = coro_lyot_plan_peak(p->lyot, window(p, p->w), p->peak.data())) != CORO_OK) return st;
+    if (p->peak.empty()) {
+        coro_status st = dm_maps(p, p->zero_h);
+        if (st != CORO_OK) return st;
+        std::vector<double> pk(p->d.batch, 0.0);
+        for (Chunk& ch : p->chunks) {
+            if ((st = coro_fresnel_plan_execute(ch.fwd, p->w, nullptr)) != CORO_OK) return st;
+            if ((st = coro_lyot_plan_peak(ch.lyot, window(p, p->w), pk.data() + ch.b0)) != CORO_OK) return st;
+        }
+        p->peak = pk;
+    }
     if (peak_out)
         for (int b = 0; b < p->d.batch; ++b) peak_out[b] = p->peak[b];
     return CORO_OK;
@@ -234,35 +287,41 @@ extern "C" coro_status coro_wfc_plan_evaluate(coro_plan plan, const float* heigh
     const coro_wfc_desc& d = p->d;
     coro_ctx c = p->ctx;
     const int B = d.batch, nf = d.n_fresnel, na = d.n_act;
-    if ((st = fresnel_forward(p, heights)) != CORO_OK) return st;
+    if ((st = dm_maps(p, heights)) != CORO_OK) return st;
     std::vector<double> dh(B, 0.0);
-    if (!grad) {
-        st = coro_lyot_plan_execute(p->lyot, window(p, p->w), p->peak.data(), nullptr, nullptr, dh.data());
-    } else {
-        const size_t fbytes = (size_t)B * nf * nf * sizeof(float2);
-        cudaError_t e = cudaMemsetAsync(p->g, 0, fbytes, c->stream);     // pad(): zero outside the window
+    const size_t npx = (size_t)nf * nf;
+    const double dx = d.diam_m / d.npix;
+    const int per = na * na;
+    for (size_t k = 0; k < p->chunks.size() && st == CORO_OK; ++k) {
+        Chunk& ch = p->chunks[k];
+        const int nb = ch.nb;
+        // E0, E1 checkpoints and E3 (in w)
+        if ((st = coro_fresnel_plan_execute(ch.fwd, p->w, nullptr)) != CORO_OK) break;
+        if (!grad) {
+            st = coro_lyot_plan_execute(ch.lyot, window(p, p->w), p->peak.data() + ch.b0, nullptr, nullptr,
+                                        dh.data() + ch.b0);
+            continue;
+        }
+        cudaError_t e = cudaMemsetAsync(p->g, 0, (size_t)nb * npx * sizeof(float2), c->stream);   // pad(): zero outside the window
         if (e != cudaSuccess) return coro::cuda_fail(e, "wfc: memset");
-        st = coro_lyot_plan_gradient(p->lyot, window(p, p->w), p->peak.data(), dh.data(), window(p, p->g), nf,
-                                     (long long)nf * nf);
+        st = coro_lyot_plan_gradient(ch.lyot, window(p, p->w), p->peak.data() + ch.b0, dh.data() + ch.b0,
+                                     window(p, p->g), nf, (long long)nf * nf);
         // G3 -> G0 (in g), the row passes writing the per-wavelength dL/dh density maps into w
-        if (st == CORO_OK) st = coro_fresnel_plan_execute(p->adj, p->g, nullptr);
-        const size_t npx = (size_t)nf * nf;
-        const double dx = d.diam_m / d.npix;
+        if (st == CORO_OK) st = coro_fresnel_plan_execute(ch.adj, p->g, nullptr);
         const float* dphi2 = reinterpret_cast<const float*>(p->w);
-        const int per = na * na;
         if (st == CORO_OK)
-            st = coro_dm_correlate(c, dphi2 + (size_t)B * npx, B, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, p->part);
+            st = coro_dm_correlate(c, dphi2 + (size_t)nb * npx, nb, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, p->part);
         if (st == CORO_OK)
-            st = coro_dm_correlate(c, dphi2, B, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, p->part + (size_t)B * per);
+            st = coro_dm_correlate(c, dphi2, nb, nf, dx, na, d.act_pitch_m, d.act_fwhm_m, 1.0, p->part + (size_t)nb * per);
         if (st == CORO_OK) {
-            sum_items_kernel<<<dim3((per + 255) / 256, 2), 256, 0, c->stream>>>(p->part, B, per, grad);
+            sum_items_kernel<<<dim3((per + 255) / 256, 2), 256, 0, c->stream>>>(p->part, nb, per, k > 0, grad);
             e = cudaGetLastError();
             if (e != cudaSuccess) st = coro::cuda_fail(e, "sum_items_kernel");
         }
-        if (st == CORO_OK) {
-            e = cudaStreamSynchronize(c->stream);
-            if (e != cudaSuccess) st = coro::cuda_fail(e, "coro_wfc_plan_evaluate");
-        }
+    }
+    if (st == CORO_OK && grad) {
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = coro::cuda_fail(e, "coro_wfc_plan_evaluate");
     }
     if (st != CORO_OK) return st;
     double total = 0.0;

@@ -16,22 +16,30 @@ from . import coro
 
 
 class WfcPlan:
-    """coro_wfc_plan_*: DM1 at the pupil, DM2 a Fresnel hop z away, Lyot chain per wavelength."""
+    """coro_wfc_plan_*: DM1 at the pupil, DM2 a Fresnel hop z away, Lyot chain per wavelength.
+    max_resident bounds the wavelengths whose fields are in memory at once (0: as many as fit
+    in 70 % of the free device memory); the band then runs in chunks."""
 
     def __init__(self, ctx: coro.Context, *, wavelengths, n_fresnel: int, diam_m: float, npix: int, z_m: float,
                  n_act: int, pitch_m: float, fwhm_m: float, lyot_frac: float, m_det: int, items,
-                 precision: int = coro.MFT_3XTF32):
+                 precision: int = coro.MFT_3XTF32, max_resident: int = 0):
         self.ctx = ctx
         self.batch = len(wavelengths)
         self.n_act = n_act
         self._lam = coro._dbl(wavelengths)
         self._items = (coro.LyotItem * self.batch)(*[coro.LyotItem(**it) for it in items])
         d = coro.WfcDesc(self.batch, self._lam, n_fresnel, diam_m, npix, z_m, n_act, pitch_m, fwhm_m, lyot_frac,
-                         m_det, self._items, precision)
+                         m_det, self._items, precision, max_resident)
         h = ct.c_void_p()
         ctx.lib.check(ctx.lib.coro_wfc_plan_create(ctx.handle, ct.byref(d), ct.byref(h)))
         self.handle = h
         ctx._track(self)
+
+    def resident(self) -> tuple[int, int]:
+        """(wavelengths held in memory at once, chunks the band runs in)."""
+        r, c = ct.c_int(), ct.c_int()
+        self.ctx.lib.check(self.ctx.lib.coro_wfc_plan_resident(self.handle, ct.byref(r), ct.byref(c)))
+        return r.value, c.value
 
     def peak(self) -> np.ndarray:
         out = (ct.c_double * self.batch)()

@@ -59,6 +59,22 @@ def test_no_device_reports_ecuda(dll):
     assert dll.coro_ctx_create(0, None, ct.byref(h)) == coro.ECUDA
 
 
+def header_members(struct: str) -> list[str]:
+    """Member names, in order, of `typedef struct { ... } struct;` in include/coro.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "coro.h")).read(), flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + struct + r"\s*;", text)
+    assert m, struct
+    names = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        parts = decl.split(",")
+        names.append(re.findall(r"\w+", parts[0])[-1])
+        names += [re.findall(r"\w+", q)[-1] for q in parts[1:]]
+    return names
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """Every ctypes mirror of a header struct has the C compiler's size and field offsets."""
     import subprocess
@@ -85,5 +101,7 @@ def test_struct_layouts_match_the_header(tmp_path):
             got[(c, f)] = int(v)
     for cname, py in mirrors.items():
         assert got[(cname, "size")] == ct.sizeof(py), cname
+        # a missing trailing member can hide in the padding: the names must match in order
+        assert header_members(cname) == [f for f, _ in py._fields_], cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

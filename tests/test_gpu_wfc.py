@@ -203,3 +203,72 @@ def test_wfc_full_size_gradient(ctx):
     worst = np.max(np.abs(gp - fd)) / scale
     print(f"full-size wfc at 550 nm: GPU gradient vs FP64 central differences, max |diff| / max |grad| {worst:.3e}")
     assert worst <= 1e-3, list(zip(gp, fd))
+
+
+def test_wfc_chunked_band_matches_resident(ctx):
+    """HBM budget: the same three-wavelength system with all wavelengths resident, two per
+    chunk and one per chunk gives the same per-wavelength sums and gradient."""
+    p, it = small_setup()
+    lams = [530e-9, 550e-9, 570e-9]
+    h = torch.from_numpy(inputs.dm_heights(9, p.n_act, 2).astype(np.float32)).cuda()
+    out = {}
+    for res in (0, 2, 1):
+        plan = wfc.WfcPlan(ctx, wavelengths=lams, n_fresnel=p.n_f, diam_m=p.diam_m, npix=p.npix, z_m=p.z_m,
+                           n_act=p.n_act, pitch_m=p.pitch, fwhm_m=p.pitch, lyot_frac=p.lyot.lyot_frac,
+                           m_det=p.lyot.m_det, items=[it] * 3, precision=coro.MFT_3XTF32, max_resident=res)
+        r, chunks = plan.resident()
+        assert (r, chunks) == {0: (3, 1), 2: (2, 2), 1: (1, 3)}[res]
+        loss, per, g = plan.evaluate(h)
+        out[res] = (loss, per, g.cpu().numpy().astype(np.float64), plan.peak())
+        plan.close()
+    for res in (2, 1):
+        np.testing.assert_allclose(out[res][3], out[0][3], rtol=1e-6)
+        np.testing.assert_allclose(out[res][1], out[0][1], rtol=1e-6)
+        assert np.linalg.norm(out[res][2] - out[0][2]) / np.linalg.norm(out[0][2]) < 1e-6
+
+
+@pytest.mark.slow
+def test_wfc_8192_grid_196_actuators(ctx):
+    """The N = 8192 case of Sec. 1.2: 196 x 196 actuators at seven pixels per actuator (a
+    1372-pixel pupil), two wavelengths run one per chunk (2 GiB of fields resident), against
+    the FP64 oracle: per-wavelength dark-hole sums and the summed gradient (adjoint)."""
+    nf, na, npix, D, z = 8192, 196, 1372, 0.0784, 0.3
+    pitch = D / na
+    lams = [540e-9, 560e-9]
+    lw = inputs.LyotWorkload(n=npix, npix=npix)
+
+    def item(lam):
+        r = 550e-9 / lam
+        return dict(m_occ=int(np.rint(lw.m_occ * r)), du_occ=lw.du_occ * r, spot_radius=lw.spot_radius_lamd * r,
+                    du_det=lw.du_det * r, dh_in=lw.dh_inner * r, dh_out=lw.dh_outer * r)
+
+    items = [item(l) for l in lams]
+    plan = wfc.WfcPlan(ctx, wavelengths=lams, n_fresnel=nf, diam_m=D, npix=npix, z_m=z, n_act=na, pitch_m=pitch,
+                       fwhm_m=pitch, lyot_frac=lw.lyot_frac, m_det=lw.m_det, items=items,
+                       precision=coro.MFT_3XTF32, max_resident=1)
+    assert plan.resident() == (1, 2)
+    h32 = inputs.dm_heights(21, na, 2).astype(np.float32).astype(np.float64)
+    peaks = plan.peak()
+    loss, per, g = plan.evaluate(torch.from_numpy(h32.astype(np.float32)).cuda())
+    got = g.cpu().numpy().astype(np.float64)
+    plan.close()
+
+    def params(lam, it):
+        lyot = coronagraph.LyotParams(n=npix, npix=npix, m_occ=it["m_occ"], du_occ=it["du_occ"],
+                                      spot_radius=it["spot_radius"], lyot_frac=lw.lyot_frac, m_det=lw.m_det,
+                                      du_det=it["du_det"])
+        return adjoint.WfcParams(n_f=nf, npix=npix, diam_m=D, z_m=z, n_act=na, lyot=lyot, dh_in=it["dh_in"],
+                                 dh_out=it["dh_out"])
+
+    ps = [params(l, it) for l, it in zip(lams, items)]
+    with oracle_pool() as pool:
+        ref_peaks = pool.starmap(adjoint.zero_height_peak, list(zip(lams, ps)))
+        ref = pool.starmap(adjoint.gradient, [(h32, l, p, None, pk) for l, p, pk in zip(lams, ps, ref_peaks)])
+    np.testing.assert_allclose(peaks, ref_peaks, rtol=1e-5)
+    ref_per = np.array([r[0] for r in ref])
+    ref_grad = ref[0][1] + ref[1][1]
+    per_err = np.max(np.abs(per / ref_per - 1))
+    err = np.linalg.norm(got - ref_grad) / np.linalg.norm(ref_grad)
+    print(f"8192^2 wfc, 196 actuators: dark-hole sums max rel {per_err:.3e}; gradient rel L2 {err:.3e}")
+    assert per_err < 1e-3
+    assert err < 1e-3
