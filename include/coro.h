@@ -92,6 +92,10 @@ typedef struct {
 
 /* a1: fill every sample with `amplitude` (App. A: a new wavefront has unit amplitude). */
 coro_status coro_wavefront_init(coro_ctx ctx, const coro_wavefront* wf, double amplitude);
+/* y <- y + alpha x, sample by sample, for two wavefronts of the same dtype, batch and n (alpha
+ * real). Used for Babinet's principle when a coronagraph is composed from single calls
+ * (E_C = E_A - IMFT(spot . MFT(E_A)), Sec. 1.1). */
+coro_status coro_wavefront_axpy(coro_ctx ctx, double alpha, const coro_wavefront* x, const coro_wavefront* y);
 
 /* ------------------------------------------------------------------------------------------
  * Optical elements (a2, a3). An element multiplies the field pointwise by a transmission.
@@ -312,14 +316,16 @@ coro_status coro_plan_destroy(coro_plan plan);
  *     X_j = (j - n/2)/npix (units of D), U_u = (u - m/2) du (units of lambda/D), s = du/npix.
  * direction +1 (focal plane -> pupil): input pitch du (lambda/D), output pitch 1/npix (D),
  *     exponent +2 pi i, same s.
- * in: [batch][n_in][n_in]; out: [batch][m][m]; C64 only. du: host [batch] (lambda/D per pixel
- * of the focal-plane side). npix: pupil pixels across D. precision: coro_mft_prec.
+ * in: [batch][n_in][n_in]; out: [batch][m][m], both C64 (precisions FP32 / 3XTF32 / 3XBF16) or
+ * both C128 (precision FP64). du: host [batch] (lambda/D per pixel of the focal-plane side).
+ * npix: pupil pixels across D. precision: coro_mft_prec.
  * Work buffers are taken from the context (allocated on first use, grown as needed).
  * ------------------------------------------------------------------------------------------ */
 typedef enum {
     CORO_MFT_FP32 = 0,    /* FP32 CUDA-core complex GEMM                                     */
     CORO_MFT_3XTF32 = 1,  /* split TF32 tensor-core GEMM (hi*hi + hi*lo + lo*hi), FP32 acc   */
-    CORO_MFT_3XBF16 = 2   /* split BF16 tensor-core GEMM, FP32 accumulate                    */
+    CORO_MFT_3XBF16 = 2,  /* split BF16 tensor-core GEMM, FP32 accumulate                    */
+    CORO_MFT_FP64 = 3     /* complex128 fields, FP64 CUDA-core GEMM (reference precision)    */
 } coro_mft_prec;
 
 coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in, double npix, int direction,

@@ -24,7 +24,7 @@ EL_APERTURE, EL_CIRCLE, EL_LENS, EL_OPD_MAP, EL_ZERNIKE, EL_SINE, EL_SCALAR, EL_
 ELF_OPAQUE_INSIDE, ELF_MAP_BATCHED = 1, 2
 FRESNEL_AS, FRESNEL_DIRECT = 0, 1
 PLAN_INIT_UNIFORM = 1
-MFT_FP32, MFT_3XTF32, MFT_3XBF16 = 0, 1, 2
+MFT_FP32, MFT_3XTF32, MFT_3XBF16, MFT_FP64 = 0, 1, 2, 3
 
 
 class CoroError(RuntimeError):
@@ -104,6 +104,7 @@ _SIGS = {
     "coro_ctx_set_stream": (ct.c_int, [_P, _P]),
     "coro_ctx_synchronize": (ct.c_int, [_P]),
     "coro_wavefront_init": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_double]),
+    "coro_wavefront_axpy": (ct.c_int, [_P, ct.c_double, ct.POINTER(Wavefront), ct.POINTER(Wavefront)]),
     "coro_apply_element": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.POINTER(Element)]),
     "coro_propagate_fresnel": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_double, ct.c_int]),
     "coro_fft2": (ct.c_int, [_P, ct.POINTER(Wavefront), ct.c_int]),
@@ -283,8 +284,20 @@ def fft2(ctx: Context, field, direction: int = -1):
     ctx.lib.check(ctx.lib.coro_fft2(ctx.handle, ct.byref(w.s), direction))
 
 
-def propagate_mft(ctx: Context, field, npix: float, direction: int, m: int, du, precision: int = MFT_FP32, out=None):
+def wavefront_axpy(ctx: Context, alpha: float, x, y):
+    """y += alpha x (two device fields of the same dtype and shape)."""
+    wx, wy = WF(x), WF(y)
+    ctx.lib.check(ctx.lib.coro_wavefront_axpy(ctx.handle, float(alpha), ct.byref(wx.s), ct.byref(wy.s)))
+    return y
+
+
+def propagate_mft(ctx: Context, field, npix: float, direction: int, m: int, du, precision: int | None = None,
+                  out=None):
+    """precision: MFT_FP32 / MFT_3XTF32 / MFT_3XBF16 for complex64 fields, MFT_FP64 for complex128
+    (the default follows the field's dtype: FP32 CUDA cores or FP64)."""
     import torch
+    if precision is None:
+        precision = MFT_FP64 if field.dtype == torch.complex128 else MFT_FP32
     w = WF(field)
     b = w.s.batch
     if out is None:

@@ -665,6 +665,39 @@ extern "C" coro_status coro_wavefront_init(coro_ctx ctx, const coro_wavefront* w
     return e == cudaSuccess ? CORO_OK : cuda_fail(e, "fill_kernel");
 }
 
+namespace {
+template <typename C>
+__global__ void axpy_kernel(typename real_of<C>::type alpha, const C* __restrict__ x, C* __restrict__ y, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const C a = x[i], b = y[i];
+        y[i] = mk<C>(fma(alpha, a.x, b.x), fma(alpha, a.y, b.y));
+    }
+}
+}  // namespace
+
+extern "C" coro_status coro_wavefront_axpy(coro_ctx ctx, double alpha, const coro_wavefront* x, const coro_wavefront* y) {
+    clear_error();
+    if (!ctx || !x || !y || !x->data || !y->data) { set_error("coro_wavefront_axpy: NULL argument"); return CORO_EINVAL; }
+    if (x->dtype != y->dtype || x->batch != y->batch || x->n != y->n) {
+        set_error("coro_wavefront_axpy: x and y differ in dtype, batch or n");
+        return CORO_EINVAL;
+    }
+    if ((x->dtype != CORO_C64 && x->dtype != CORO_C128) || x->batch < 1 || x->n < 1) {
+        set_error("coro_wavefront_axpy: bad dtype, batch or n");
+        return CORO_EINVAL;
+    }
+    if (!std::isfinite(alpha)) { set_error("coro_wavefront_axpy: alpha must be finite"); return CORO_EINVAL; }
+    DeviceGuard g(ctx->device);
+    const size_t n = (size_t)x->batch * x->n * x->n;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+    if (x->dtype == CORO_C64)
+        axpy_kernel<float2><<<blocks, 256, 0, ctx->stream>>>((float)alpha, (const float2*)x->data, (float2*)y->data, n);
+    else
+        axpy_kernel<double2><<<blocks, 256, 0, ctx->stream>>>(alpha, (const double2*)x->data, (double2*)y->data, n);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CORO_OK : cuda_fail(e, "axpy_kernel");
+}
+
 // =========================================================================== a2/a3: elements
 
 extern "C" coro_status coro_apply_element(coro_ctx ctx, const coro_wavefront* wf, const coro_element* el) {

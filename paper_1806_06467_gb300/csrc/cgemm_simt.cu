@@ -1,4 +1,5 @@
-// cgemm_simt.cu -- FP32 CUDA-core batched complex GEMM (the CORO_MFT_FP32 path of the MFT).
+// cgemm_simt.cu -- CUDA-core batched complex GEMMs: FP32 (the CORO_MFT_FP32 path of the MFT)
+// and FP64 on complex128 fields (CORO_MFT_FP64).
 // 64 x 64 output tile per block, 16-deep k slices staged in shared memory, each thread a
 // 4 x 4 block of complex outputs at stride 16 (conflict-free shared reads, coalesced stores).
 #include <cuda_runtime.h>
@@ -78,7 +79,82 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(const GemmDesc g) {
     }
 }
 
+// FP64 complex GEMM: 64 x 64 output tile, 8-deep k slices, each thread 4 x 4 outputs.
+constexpr int ZBK = 8;
+
+__global__ void __launch_bounds__(256) zgemm_simt_kernel(const ZGemmDesc g) {
+    __shared__ double2 As[ZBK][BM];
+    __shared__ double2 Bs[ZBK][BN];
+    const int b = blockIdx.z;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const double2* A = g.A + b * g.sA;
+    const double2* B = g.B + b * g.sB;
+    double2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+    for (int k0 = 0; k0 < g.K; k0 += ZBK) {
+        // 512 samples of each tile, 2 per thread
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int idx = threadIdx.x + r * 256;
+            int mm, kk;
+            if (g.a_trans) { mm = idx % BM; kk = idx / BM; } else { kk = idx % ZBK; mm = idx / ZBK; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            double2 v = make_double2(0.0, 0.0);
+            if (gm < g.M && gk < g.K) v = g.a_trans ? A[(size_t)gk * g.lda + gm] : A[(size_t)gm * g.lda + gk];
+            As[kk][mm] = v;
+            int nn;
+            if (g.b_trans) { kk = idx % ZBK; nn = idx / ZBK; } else { nn = idx % BN; kk = idx / BN; }
+            const int gn = n0 + nn, gk2 = k0 + kk;
+            double2 w = make_double2(0.0, 0.0);
+            if (gn < g.N && gk2 < g.K) w = g.b_trans ? B[(size_t)gn * g.ldb + gk2] : B[(size_t)gk2 * g.ldb + gn];
+            Bs[kk][nn] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < ZBK; ++k) {
+            double2 a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fma(a[i].x, bb[j].x, acc[i][j].x);
+                    acc[i][j].x = fma(-a[i].y, bb[j].y, acc[i][j].x);
+                    acc[i][j].y = fma(a[i].x, bb[j].y, acc[i][j].y);
+                    acc[i][j].y = fma(a[i].y, bb[j].x, acc[i][j].y);
+                }
+        }
+        __syncthreads();
+    }
+    const double s = g.scale_per_item ? g.scale_per_item[b] : g.alpha;
+    double2* C = g.C + b * g.sC;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + ty + 16 * i;
+        if (gm >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + tx + 16 * j;
+            if (gn < g.N) C[(size_t)gm * g.ldc + gn] = make_double2(acc[i][j].x * s, acc[i][j].y * s);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_zgemm(const ZGemmDesc& g, int batch, cudaStream_t stream) {
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch);
+    zgemm_simt_kernel<<<grid, 256, 0, stream>>>(g);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_cgemm(const GemmDesc& g, int batch, int precision, cudaStream_t stream) {
     if (precision != CORO_MFT_FP32) return cudaErrorNotSupported;

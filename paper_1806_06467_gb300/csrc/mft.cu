@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "capi_common.h"
@@ -22,7 +23,8 @@ using namespace coro;
 namespace {
 
 // basis[b][u][j] = exp(sign 2 pi i (j - n/2)(u - m/2) c_b), c_b = du_b / npix.
-__global__ void mft_basis_kernel(float2* basis, int m, int n, const double* __restrict__ c, int sign) {
+template <typename C>
+__global__ void mft_basis_kernel(C* basis, int m, int n, const double* __restrict__ c, int sign) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int u = blockIdx.y;
     const int b = blockIdx.z;
@@ -33,12 +35,13 @@ __global__ void mft_basis_kernel(float2* basis, int m, int n, const double* __re
     double s, co;
     sincospi(2.0 * cyc, &s, &co);
     if (sign < 0) s = -s;
-    basis[((size_t)b * m + u) * n + j] = make_float2((float)co, (float)s);
+    using R = typename real_of<C>::type;
+    basis[((size_t)b * m + u) * n + j] = mk<C>((R)co, (R)s);
 }
 
 coro_status check_mft_wf(const char* fn, const coro_wavefront* wf) {
     if (!wf || !wf->data) { coro::set_error("%s: wavefront or data is NULL", fn); return CORO_EINVAL; }
-    if (wf->dtype != CORO_C64) { coro::set_error("%s: the MFT is implemented for complex64 fields", fn); return CORO_ENOTIMPL; }
+    if (wf->dtype != CORO_C64 && wf->dtype != CORO_C128) { coro::set_error("%s: bad dtype %d", fn, wf->dtype); return CORO_EINVAL; }
     if (wf->batch < 1 || wf->batch > 65535) { coro::set_error("%s: batch %d", fn, wf->batch); return CORO_ESIZE; }
     if (wf->n < 1 || wf->n > 8192) { coro::set_error("%s: size %d outside [1, 8192]", fn, wf->n); return CORO_ESIZE; }
     return CORO_OK;
@@ -110,6 +113,70 @@ coro_status mft_tensor_core(coro_ctx ctx, const coro_wavefront* in, int directio
     return CORO_OK;
 }
 
+// CUDA-core MFT: complex64 with FP32 arithmetic or complex128 with FP64 arithmetic.
+template <typename C>
+coro_status mft_cuda_cores(coro_ctx ctx, const coro_wavefront* in, int direction, int m, const std::vector<double>& c,
+                           coro_wavefront* out) {
+    using Real = typename real_of<C>::type;
+    using Desc = typename std::conditional<std::is_same<C, float2>::value, GemmDesc, ZGemmDesc>::type;
+    coro_status st = CORO_OK;
+    const int batch = in->batch;
+    auto gemm = [&](const Desc& g) -> cudaError_t {
+        if constexpr (std::is_same<C, float2>::value) return launch_cgemm(g, batch, CORO_MFT_FP32, ctx->stream);
+        else return launch_zgemm(g, batch, ctx->stream);
+    };
+    // focal-plane side has m (forward) or in->n (inverse) samples; pupil side the other
+    const int nf = direction < 0 ? m : in->n;     // focal samples per axis
+    const int np = direction < 0 ? in->n : m;     // pupil samples per axis
+    const size_t basis_elems = (size_t)batch * nf * np;
+    const size_t t_elems = (size_t)batch * (direction < 0 ? (size_t)np * nf : (size_t)nf * np);
+    C* work = (C*)coro::ctx_work(ctx, (basis_elems + t_elems) * sizeof(C), &st);
+    if (!work) return st;
+    C* basis = work;
+    C* tmp = work + basis_elems;
+    void* c_d = coro::upload_async(ctx, c.data(), c.size() * sizeof(double), &st);
+    if (!c_d) return st;
+    dim3 bg((np + 127) / 128, nf, batch);
+    mft_basis_kernel<C><<<bg, 128, 0, ctx->stream>>>(basis, nf, np, (const double*)c_d, direction < 0 ? -1 : 1);
+    cudaError_t e = cudaGetLastError();
+    coro::free_async(ctx, c_d);
+    if (e != cudaSuccess) return coro::cuda_fail(e, "mft_basis_kernel");
+
+    const C* x = (const C*)in->data;
+    C* y = (C*)out->data;
+    const long long sb = (long long)nf * np;   // basis batch stride
+    Desc g1{}, g2{};
+    if (direction < 0) {
+        // T[i][u] = sum_j in[i][j] A[u][j]            (M = np, N = nf, K = np)
+        g1 = Desc{np, nf, np, x, (long long)np * np, np, false, basis, sb, np, true,
+                      tmp, (long long)np * nf, nf, (Real)1};
+        // out[v][u] = s sum_i A[v][i] T[i][u]         (M = nf, N = nf, K = np)
+        g2 = Desc{nf, nf, np, basis, sb, np, false, tmp, (long long)np * nf, nf, false,
+                      y, (long long)nf * nf, nf, (Real)0};
+    } else {
+        // T[v][j] = sum_u in[v][u] B[u][j]            (M = nf, N = np, K = nf)
+        g1 = Desc{nf, np, nf, x, (long long)nf * nf, nf, false, basis, sb, np, false,
+                      tmp, (long long)nf * np, np, (Real)1};
+        // out[i][j] = s sum_v B[v][i] T[v][j]         (M = np, N = np, K = nf)
+        g2 = Desc{np, np, nf, basis, sb, np, true, tmp, (long long)nf * np, np, false,
+                      y, (long long)np * np, np, (Real)0};
+    }
+    std::vector<Real> scale(batch);
+    for (int b = 0; b < batch; ++b) scale[b] = (Real)c[b];
+    void* s_d = coro::upload_async(ctx, scale.data(), batch * sizeof(Real), &st);
+    if (!s_d) return st;
+    g2.scale_per_item = (const Real*)s_d;
+    e = gemm(g1);
+    if (e == cudaSuccess) e = gemm(g2);
+    coro::free_async(ctx, s_d);
+    if (e == cudaErrorNotSupported) {
+        coro::set_error("coro_propagate_mft: CUDA-core GEMM not available in this build");
+        return CORO_ENOTIMPL;
+    }
+    if (e != cudaSuccess) return coro::cuda_fail(e, "mft gemm");
+    return CORO_OK;
+}
+
 }  // namespace
 
 extern "C" coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in, double npix, int direction,
@@ -124,8 +191,12 @@ extern "C" coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in
     if (!du) { coro::set_error("coro_propagate_mft: du is NULL"); return CORO_EINVAL; }
     if (out->batch != in->batch) { coro::set_error("coro_propagate_mft: batch mismatch"); return CORO_EINVAL; }
     if (out->n != m) { coro::set_error("coro_propagate_mft: out->n (%d) must equal m (%d)", out->n, m); return CORO_EINVAL; }
-    if (precision != CORO_MFT_FP32 && precision != CORO_MFT_3XTF32 && precision != CORO_MFT_3XBF16) {
-        coro::set_error("coro_propagate_mft: bad precision %d", precision);
+    if (in->dtype != out->dtype) { coro::set_error("coro_propagate_mft: in and out dtypes differ"); return CORO_EINVAL; }
+    const bool dbl = in->dtype == CORO_C128;
+    if (dbl ? precision != CORO_MFT_FP64
+            : (precision != CORO_MFT_FP32 && precision != CORO_MFT_3XTF32 && precision != CORO_MFT_3XBF16)) {
+        coro::set_error("coro_propagate_mft: precision %d does not apply to %s fields", precision,
+                        dbl ? "complex128 (use CORO_MFT_FP64)" : "complex64");
         return CORO_EINVAL;
     }
     const int batch = in->batch;
@@ -135,55 +206,8 @@ extern "C" coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in
         c[b] = du[b] / npix;
     }
     coro::DeviceGuard g(ctx->device);
-    if (precision != CORO_MFT_FP32) return mft_tensor_core(ctx, in, direction, m, c, precision == CORO_MFT_3XBF16, out);
-    // focal-plane side has m (forward) or in->n (inverse) samples; pupil side the other
-    const int nf = direction < 0 ? m : in->n;     // focal samples per axis
-    const int np = direction < 0 ? in->n : m;     // pupil samples per axis
-    const size_t basis_elems = (size_t)batch * nf * np;
-    const size_t t_elems = (size_t)batch * (direction < 0 ? (size_t)np * nf : (size_t)nf * np);
-    float2* work = (float2*)coro::ctx_work(ctx, (basis_elems + t_elems) * sizeof(float2), &st);
-    if (!work) return st;
-    float2* basis = work;
-    float2* tmp = work + basis_elems;
-    void* c_d = coro::upload_async(ctx, c.data(), c.size() * sizeof(double), &st);
-    if (!c_d) return st;
-    dim3 bg((np + 127) / 128, nf, batch);
-    mft_basis_kernel<<<bg, 128, 0, ctx->stream>>>(basis, nf, np, (const double*)c_d, direction < 0 ? -1 : 1);
-    cudaError_t e = cudaGetLastError();
-    coro::free_async(ctx, c_d);
-    if (e != cudaSuccess) return coro::cuda_fail(e, "mft_basis_kernel");
-
-    const float2* x = (const float2*)in->data;
-    float2* y = (float2*)out->data;
-    const long long sb = (long long)nf * np;   // basis batch stride
-    GemmDesc g1{}, g2{};
-    if (direction < 0) {
-        // T[i][u] = sum_j in[i][j] A[u][j]            (M = np, N = nf, K = np)
-        g1 = GemmDesc{np, nf, np, x, (long long)np * np, np, false, basis, sb, np, true,
-                      tmp, (long long)np * nf, nf, 1.0f};
-        // out[v][u] = s sum_i A[v][i] T[i][u]         (M = nf, N = nf, K = np)
-        g2 = GemmDesc{nf, nf, np, basis, sb, np, false, tmp, (long long)np * nf, nf, false,
-                      y, (long long)nf * nf, nf, 0.0f};
-    } else {
-        // T[v][j] = sum_u in[v][u] B[u][j]            (M = nf, N = np, K = nf)
-        g1 = GemmDesc{nf, np, nf, x, (long long)nf * nf, nf, false, basis, sb, np, false,
-                      tmp, (long long)nf * np, np, 1.0f};
-        // out[i][j] = s sum_v B[v][i] T[v][j]         (M = np, N = np, K = nf)
-        g2 = GemmDesc{np, np, nf, basis, sb, np, true, tmp, (long long)nf * np, np, false,
-                      y, (long long)np * np, np, 0.0f};
-    }
-    std::vector<float> scale(batch);
-    for (int b = 0; b < batch; ++b) scale[b] = (float)c[b];
-    void* s_d = coro::upload_async(ctx, scale.data(), batch * sizeof(float), &st);
-    if (!s_d) return st;
-    g2.scale_per_item = (const float*)s_d;
-    e = launch_cgemm(g1, batch, precision, ctx->stream);
-    if (e == cudaSuccess) e = launch_cgemm(g2, batch, precision, ctx->stream);
-    coro::free_async(ctx, s_d);
-    if (e == cudaErrorNotSupported) {
-        coro::set_error("coro_propagate_mft: precision %d is not available in this build", precision);
-        return CORO_ENOTIMPL;
-    }
-    if (e != cudaSuccess) return coro::cuda_fail(e, "mft gemm");
-    return CORO_OK;
+    if (precision == CORO_MFT_3XTF32 || precision == CORO_MFT_3XBF16)
+        return mft_tensor_core(ctx, in, direction, m, c, precision == CORO_MFT_3XBF16, out);
+    return dbl ? mft_cuda_cores<double2>(ctx, in, direction, m, c, out) : mft_cuda_cores<float2>(ctx, in, direction, m, c, out);
 }
+

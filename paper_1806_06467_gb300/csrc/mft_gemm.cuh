@@ -19,4 +19,15 @@ struct GemmDesc {
 // precision: CORO_MFT_FP32 (CUDA cores) or the split tensor-core modes.
 cudaError_t launch_cgemm(const GemmDesc& g, int batch, int precision, cudaStream_t stream);
 
+// The same contraction in complex128 with FP64 arithmetic (CORO_MFT_FP64).
+struct ZGemmDesc {
+    int M, N, K;
+    const double2* A; long long sA; int lda; bool a_trans;
+    const double2* B; long long sB; int ldb; bool b_trans;
+    double2* C; long long sC; int ldc;
+    double alpha;
+    const double* scale_per_item;
+};
+cudaError_t launch_zgemm(const ZGemmDesc& g, int batch, cudaStream_t stream);
+
 }  // namespace coro
