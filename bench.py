@@ -262,8 +262,40 @@ def cpu_baseline(n: int) -> dict:
         if k >= 4:
             break
     dt = time.perf_counter() - t0
-    return {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} planes (element + angular-spectrum hop) of the {n}^2 relay, FP64 numpy"}
+    out = {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{k} planes (element + angular-spectrum hop) of the {n}^2 relay, FP64 numpy"}
+    out["other_workloads"] = oracle_other_workloads()
+    return out
+
+
+def oracle_other_workloads() -> dict:
+    """The FP64 oracle on the other configurations, one sample each: the plain FP64 Airy
+    system (256^2: lens, direct Fresnel to focus, MFT to 64^2) and one PSF of the Lyot system
+    (1024^2 pupil, MFTs through the library matmul, whose BLAS may use every host core)."""
+    import os as _os
+
+    import numpy as np
+
+    from oracle import coronagraph, optics, propagation
+    from paper_1806_06467_gb300 import inputs
+    t0 = time.perf_counter()
+    npix, n = 128, 256
+    e = optics.circular_aperture(n, 1.0 / npix, 0.5).astype(complex) * optics.thin_lens(n, 1.0 / npix, 500e-9, 10.0)
+    propagation.direct_fresnel(e, 1.0 / npix, 500e-9, 10.0)
+    propagation.mft(optics.circular_aperture(n, 1.0 / npix, 0.5).astype(complex), npix, 64, 0.5)
+    t_airy = time.perf_counter() - t0
+    w = inputs.LyotWorkload()
+    c = inputs.zernike_coefficients(w.seed, w.zernike_first, w.zernike_last, w.zernike_rms_m)
+    pupil = coronagraph.pupil_field(w.n, w.npix, w.wavelength_m, optics.zernike_opd(w.n, 1.0 / w.npix, 0.5, c, 4))
+    p = coronagraph.LyotParams(n=w.n, npix=w.npix, m_occ=w.m_occ, du_occ=w.du_occ, spot_radius=w.spot_radius_lamd,
+                               lyot_frac=w.lyot_frac, m_det=w.m_det, du_det=w.du_det)
+    t0 = time.perf_counter()
+    coronagraph.lyot_fields(pupil, p)
+    t_psf = time.perf_counter() - t0
+    return {"airy_fp64_system_s": t_airy, "lyot_psf_s": t_psf, "lyot_psfs_per_s": 1.0 / t_psf,
+            "host_cpus": _os.cpu_count(),
+            "note": "one sample each; the relay value above runs numpy FFTs on one core, the PSF's MFT "
+                    "matmuls run in the host BLAS (all cores it uses)"}
 
 
 # ------------------------------------------------------------------------------ plain GPU form
