@@ -288,6 +288,11 @@ cudaError_t run_stages(LyotPlan* p, const void* pupil, float* intensity, void* f
         a.dst_bstride = (long long)4 * dst.rows * dst.ld;
         a.dst_rows = dst.rows;
         a.dst_ld = dst.ld;
+        if (epi == TC_EPI_BABINET) {                 // E_A straight from the complex64 pupil
+            a.src64 = (const float2*)pupil;
+            a.src64_bstride = p->pupil_bstride;
+            a.src64_ld = p->pupil_ld;
+        }
         e = tc_launch(p->bf16, epi, mx, mw, mm, nn, kk, B, a, s);
         mark(gi + 2);
     };

@@ -225,8 +225,8 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
         double dh = 0.0;
         float pk = 0.f;
         if constexpr (EPI == TC_EPI_BABINET) {
-            // read-modify-write of E_A: the reads of four columns are issued before any of
-            // their arithmetic, so each thread keeps 16 loads in flight
+            // E_A from the complex64 pupil when given (exact FP32, one 8-byte load), else from
+            // its split planes; the reads of four columns are issued before any arithmetic
             if (ok && m < it.M) {
                 const int kx = m - it.M / 2;
                 const size_t plane = (size_t)a.dst_rows * a.dst_ld;
@@ -241,8 +241,9 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
                         const int ky = n - it.N / 2;
                         const int r2 = kx * kx + ky * ky;
                         keep[jj] = n < it.N && r2 >= it.mask_lo && r2 <= it.mask_hi;
-                        e[jj] = keep[jj] ? load_split<BF16>(a.dst, plane, b * a.dst_bstride + (size_t)n * a.dst_ld + m)
-                                         : make_float2(0.f, 0.f);
+                        e[jj] = !keep[jj] ? make_float2(0.f, 0.f)
+                                : a.src64 ? __ldg(a.src64 + b * a.src64_bstride + (size_t)n * a.src64_ld + m)
+                                          : load_split<BF16>(a.dst, plane, b * a.dst_bstride + (size_t)n * a.dst_ld + m);
                     }
 #pragma unroll
                     for (int jj = 0; jj < G; ++jj) {

@@ -52,6 +52,9 @@ struct TcArgs {
     double* dh_acc;                  // dark-hole sums [b] (intensity epilogue)
     float* peak;                     // running max of the intensity [b] (intensity epilogue), or NULL
     int c64_seed;                    // intensity epilogue: c64 receives mask . E * inv_peak instead of E
+    const float2* src64;             // Babinet epilogue: E_A read from this complex64 array
+    long long src64_bstride;         //   [b][rows][src64_ld] (NULL: from the split planes in dst)
+    int src64_ld;
 };
 
 // Host side (tc_gemm.cu).
