@@ -108,3 +108,19 @@ def test_airy_config_fp64_end_to_end(ctx):
     assert np.max(np.abs(idet - airy(np.hypot(xd, yd)))) < 3e-3
     c = n // 2
     np.testing.assert_allclose(ifoc[c - 32:c + 32, c - 32:c + 32], idet, atol=1e-10)
+
+
+def test_wavefront_axpy_and_its_checks(ctx):
+    """y += alpha x in both dtypes; mismatched shapes or dtypes are refused before any launch."""
+    for dt, tol in ((torch.complex64, 1e-6), (torch.complex128, 1e-15)):
+        x = torch.from_numpy(inputs.random_field((2, 64, 64), seed=1)).to(dt).cuda()
+        y0 = torch.from_numpy(inputs.random_field((2, 64, 64), seed=2)).to(dt).cuda()
+        y = coro.wavefront_axpy(ctx, -0.75, x, y0.clone())
+        ref = (y0 - 0.75 * x).cpu().numpy()
+        assert np.max(np.abs(y.cpu().numpy() - ref)) < tol * np.max(np.abs(ref))
+    with pytest.raises(RuntimeError):
+        coro.wavefront_axpy(ctx, 1.0, torch.zeros((2, 64, 64), dtype=torch.complex64, device="cuda"),
+                            torch.zeros((2, 32, 32), dtype=torch.complex64, device="cuda"))
+    with pytest.raises(RuntimeError):
+        coro.wavefront_axpy(ctx, 1.0, torch.zeros((1, 64, 64), dtype=torch.complex64, device="cuda"),
+                            torch.zeros((1, 64, 64), dtype=torch.complex128, device="cuda"))

@@ -272,3 +272,11 @@ def test_wfc_8192_grid_196_actuators(ctx):
     print(f"8192^2 wfc, 196 actuators: dark-hole sums max rel {per_err:.3e}; gradient rel L2 {err:.3e}")
     assert per_err < 1e-3
     assert err < 1e-3
+
+
+def test_wfc_rejects_negative_budget(ctx):
+    p, it = small_setup()
+    with pytest.raises(RuntimeError):
+        wfc.WfcPlan(ctx, wavelengths=[550e-9], n_fresnel=p.n_f, diam_m=p.diam_m, npix=p.npix, z_m=p.z_m,
+                    n_act=p.n_act, pitch_m=p.pitch, fwhm_m=p.pitch, lyot_frac=p.lyot.lyot_frac,
+                    m_det=p.lyot.m_det, items=[it], precision=coro.MFT_3XTF32, max_resident=-1)
