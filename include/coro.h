@@ -129,8 +129,11 @@ typedef enum {
                              * i.e. scalar / lambda_b times dL/dphi of a phase exp(i phi) applied
                              * there (scalar = 4 pi: dL/dh per metre of a reflecting surface
                              * at normal incidence). Field unchanged. ref: device, the
-                             * wavefront's dtype, [batch][n][n]; store: device float
-                             * [batch][n][n]. Same placement rules as CHECKPOINT.           */
+                             * wavefront's dtype, [batch][n][n], or NULL for a unit reference
+                             * (E = 1: the tap after the conjugate of a known transmission
+                             * recomputes that plane instead of reading a checkpoint);
+                             * store: device float [batch][n][n]. Same placement rules as
+                             * CHECKPOINT.                                                    */
 } coro_element_kind;
 
 #define CORO_ELF_OPAQUE_INSIDE 1  /* CORO_EL_CIRCLE: block r <= radius instead of passing it */
@@ -426,8 +429,8 @@ coro_status coro_lyot_plan_gradient(coro_plan plan, const void* pupil, const dou
  * sum normalised by the peak of the zero-height system (computed once, held fixed).
  * coro_wfc_plan_evaluate: heights device float [2][n_act][n_act] (metres of surface, DM1 then
  * DM2); loss (host) and per_item (host [batch]) optional; grad device float [2][n_act][n_act]
- * = dL/dheights, or NULL for the forward only. Synchronises the stream. The plan holds four
- * resident x n_fresnel^2 complex64 fields (checkpoints E0, E1, work, adjoint).
+ * = dL/dheights, or NULL for the forward only. Synchronises the stream. The plan holds three
+ * resident x n_fresnel^2 complex64 fields (checkpoint E1, work, adjoint).
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
     int batch;                    /* wavelengths                                           */
@@ -442,7 +445,7 @@ typedef struct {
     int m_det;
     const coro_lyot_item* items;  /* host [batch], one Lyot item per wavelength            */
     int precision;                /* CORO_MFT_3XTF32 or CORO_MFT_3XBF16                    */
-    int max_resident;             /* wavelengths held in HBM at once (4 x 8 n_fresnel^2    */
+    int max_resident;             /* wavelengths held in HBM at once (3 x 8 n_fresnel^2    */
                                   /* bytes each); 0 = as many as fit in 70 % of the free   */
                                   /* device memory. The band runs in chunks of that many,  */
                                   /* with the same results (per-item sums in item order).  */

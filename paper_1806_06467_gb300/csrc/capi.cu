@@ -495,7 +495,7 @@ coro_status compile_element(DevBlocks& db, const coro_element* el, bool dbl, int
             break;
         }
         case CORO_EL_PHASE_GRAD: {
-            if (!el->store || !el->ref) { set_error("phase gradient: store and ref must be set"); return CORO_EINVAL; }
+            if (!el->store) { set_error("phase gradient: store must be set"); return CORO_EINVAL; }
             for (int b = 0; b < batch; ++b) split_f32(2.0 * el->scalar / lam[b], &fpar[4 * b], &fpar[4 * b + 1]);
             out->kind = DK_PHASE_GRAD;
             out->dst = el->store;

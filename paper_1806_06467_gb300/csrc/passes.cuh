@@ -32,7 +32,7 @@ enum DevElemKind : int {
     DK_STORE = 10,     // checkpoint: copy the field to dst[b * map_bstride + y * n + x], the field
                        // itself unchanged; flags bit0: the copy is taken times (-1)^(x+y)
     DK_PHASE_GRAD = 11 // float dst[...] = fpar[4b] * Im(v conj(ref)), ref = tab (complex, same
-                       // layout as dst); flags bit0 as DK_STORE. Field unchanged.
+                       // layout as dst; NULL = 1); flags bit0 as DK_STORE. Field unchanged.
 };
 
 // Zernike evaluation table: OPD = sum_{m=0}^{ZM-1} A_m(rho^2) Re(z^m) + B_m(rho^2) Im(z^m),
@@ -281,7 +281,7 @@ __device__ __forceinline__ void apply_elems_n(C (&v)[S], int x0, int y, int b, i
                 const bool chk = e.flags & 1;
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    const C r = __ldg(rf + s * XS);
+                    const C r = e.tab ? __ldg(rf + s * XS) : mk<C>(1, 0);   // no reference: 1
                     R im = v[s].y * r.x - v[s].x * r.y;                 // Im(v conj(r))
                     if (chk && ((x0 + s * XS + y) & 1)) im = -im;
                     __stcs(d + s * XS, (float)(wgt * im));
@@ -476,7 +476,8 @@ __device__ __forceinline__ void apply_elems_pair(pk::CP (&v)[16], int x0, int ya
                 const bool chk = e.flags & 1;
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
-                    const float2 ra = __ldg(rf + s * XS), rb = __ldg(rf + N + s * XS);
+                    const float2 ra = e.tab ? __ldg(rf + s * XS) : make_float2(1.f, 0.f);
+                    const float2 rb = e.tab ? __ldg(rf + N + s * XS) : make_float2(1.f, 0.f);
                     float vra, vrb, via, vib;
                     pk::unpack(v[s].re, vra, vrb);
                     pk::unpack(v[s].im, via, vib);

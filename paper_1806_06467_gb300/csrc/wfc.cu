@@ -12,15 +12,19 @@
 //   dL/dh = sum_lambda (4 pi / lambda) G_infl^T (dL/dphi) G_infl.
 // The wavelength sum is folded into one weighted map per DM before the DM correlation.
 // Each chain runs as one fused Fresnel plan (five row / column passes for the two hops):
-// forward  init . aperture . phi1 . [checkpoint E0] -> AS(+z) -> [checkpoint E1] . phi2 -> AS(-z)
-// adjoint  G3 -> AS(+z) -> exp(-i phi2) . [dL/dphi2 tap vs E1] -> AS(-z) -> [dL/dphi1 tap vs E0]
-// with checkpoints and taps written by the row passes themselves (no separate copies). The
-// dphi2 tap uses 2 Im(G2 conj(E2)) = 2 Im(G1 conj(E1)) with G1 = exp(-i phi2) G2, so it sits
-// after the conjugate phase and needs only E1. Each tap writes one weighted map per
-// wavelength; the DM correlation reads them per wavelength and a last kernel sums over them.
+// forward  init . aperture . phi1 -> AS(+z) -> [checkpoint E1] . phi2 -> AS(-z)
+// adjoint  G3 -> AS(+z) -> exp(-i phi2) . [dL/dphi2 tap vs E1] -> AS(-z)
+//          -> aperture . exp(-i phi1) . [dL/dphi1 tap vs 1]
+// with the checkpoint and the taps written by the row passes themselves (no separate copies).
+// The dphi2 tap uses 2 Im(G2 conj(E2)) = 2 Im(G1 conj(E1)) with G1 = exp(-i phi2) G2, so it
+// sits after the conjugate phase and needs only E1; E0 = A exp(i phi1) is known in closed
+// form, so 2 Im(G0 conj(E0)) = 2 Im(A exp(-i phi1) G0) is a tap against a unit reference
+// after the aperture and the conjugate DM1 phase, and E0 is never stored. Each tap writes one
+// weighted map per wavelength; the DM correlation reads them per wavelength and a last
+// kernel sums over them.
 //
-// HBM budget: the four full-grid fields per wavelength (checkpoints E0, E1, the Lyot pupil /
-// tap maps, the adjoint field) are 32 N^2 bytes each, 2 GiB per wavelength at N = 8192. The
+// HBM budget: the three full-grid fields per wavelength (checkpoint E1, the Lyot pupil / tap
+// maps, the adjoint field) are 24 N^2 bytes, 1.5 GiB per wavelength at N = 8192. The
 // plan keeps at most `resident` wavelengths in memory and runs the band in chunks of that
 // many (one set of fused plans and one Lyot plan per chunk, all on the same buffers); the
 // gradient sums the chunks' contributions in order.
@@ -62,8 +66,8 @@ struct WfcPlan : coro_plan_s {
     int resident = 0;                           // wavelengths whose fields fit at once
     std::vector<Chunk> chunks;
     std::vector<void*> bufs;
-    float2 *e0 = nullptr, *e1 = nullptr, *w = nullptr, *g = nullptr;
-    float *opd1 = nullptr, *opd2 = nullptr, *opd2n = nullptr, *zero_h = nullptr;
+    float2 *e1 = nullptr, *w = nullptr, *g = nullptr;
+    float *opd1 = nullptr, *opd1n = nullptr, *opd2 = nullptr, *opd2n = nullptr, *zero_h = nullptr;
     float* part = nullptr;                      // [2][resident][n_act][n_act] per-wavelength dL/dh
     std::vector<double> peak;
     int kind() const override { return 3; }
@@ -103,6 +107,7 @@ coro_status dm_maps(WfcPlan* p, const float* heights) {
     const double dx = d.diam_m / d.npix;
     coro_status st;
     if ((st = coro_dm_opd(c, heights, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, 2.0, p->opd1)) != CORO_OK) return st;
+    if ((st = coro_dm_opd(c, heights, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, -2.0, p->opd1n)) != CORO_OK) return st;
     if ((st = coro_dm_opd(c, heights + na * na, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, 2.0, p->opd2)) != CORO_OK) return st;
     return coro_dm_opd(c, heights + na * na, 1, na, d.act_pitch_m, d.act_fwhm_m, nf, dx, -2.0, p->opd2n);
 }
@@ -125,14 +130,13 @@ coro_status make_chunk(WfcPlan* p, Chunk& ch) {
     coro_status st = coro_lyot_plan_create(p->ctx, &ld, &ch.lyot);
     if (st != CORO_OK) return st;
     if ((st = coro_lyot_plan_set_pupil_layout(ch.lyot, nf, (long long)nf * nf)) != CORO_OK) return st;
-    coro_element fe[5]{};
+    coro_element fe[4]{};
     fe[0].kind = CORO_EL_APERTURE;
     fe[0].radius = 0.5 * d.diam_m;
     fe[1] = opd_elem(p->opd1);
-    fe[2] = checkpoint_elem(0, p->e0);
-    fe[3] = checkpoint_elem(1, p->e1);
-    fe[4] = opd_elem(p->opd2);
-    fe[4].plane = 1;
+    fe[2] = checkpoint_elem(1, p->e1);
+    fe[3] = opd_elem(p->opd2);
+    fe[3].plane = 1;
     coro_fresnel_desc fd{};
     fd.dtype = CORO_C64;
     fd.batch = ch.nb;
@@ -141,7 +145,7 @@ coro_status make_chunk(WfcPlan* p, Chunk& ch) {
     fd.wavelength = p->lam.data() + ch.b0;
     fd.n_planes = 3;
     fd.distance = z;
-    fd.n_elements = 5;
+    fd.n_elements = 4;
     fd.elements = fe;
     fd.flags = CORO_PLAN_INIT_UNIFORM;
     if ((st = coro_fresnel_plan_create(p->ctx, &fd, &ch.fwd)) != CORO_OK) return st;
@@ -149,7 +153,7 @@ coro_status make_chunk(WfcPlan* p, Chunk& ch) {
     const size_t npx = (size_t)d.n_fresnel * d.n_fresnel;
     float* dphi2 = reinterpret_cast<float*>(p->w);
     float* dphi1 = dphi2 + (size_t)ch.nb * npx;
-    coro_element ae[3]{};
+    coro_element ae[5]{};
     ae[0] = opd_elem(p->opd2n);
     ae[0].plane = 1;
     ae[1].kind = CORO_EL_PHASE_GRAD;                 // (4 pi / lambda) 2 Im(G1 conj(E1))
@@ -157,11 +161,15 @@ coro_status make_chunk(WfcPlan* p, Chunk& ch) {
     ae[1].scalar = 4.0 * M_PI;
     ae[1].ref = p->e1;
     ae[1].store = dphi2;
-    ae[2] = ae[1];                                   // (4 pi / lambda) 2 Im(G0 conj(E0))
+    ae[2] = fe[0];                                   // A exp(-i phi1) G0 ...
     ae[2].plane = 2;
-    ae[2].ref = p->e0;
-    ae[2].store = dphi1;
-    fd.n_elements = 3;
+    ae[3] = opd_elem(p->opd1n);
+    ae[3].plane = 2;
+    ae[4] = ae[1];                                   // ... (4 pi / lambda) 2 Im(A exp(-i phi1) G0)
+    ae[4].plane = 2;
+    ae[4].ref = nullptr;
+    ae[4].store = dphi1;
+    fd.n_elements = 5;
     fd.elements = ae;
     fd.flags = 0;
     if ((st = coro_fresnel_plan_create(p->ctx, &fd, &ch.adj)) != CORO_OK) return st;
@@ -206,7 +214,7 @@ extern "C" coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* d
     p->d.wavelength = p->lam.data();
     p->d.items = p->items.data();
     const int nf = d->n_fresnel;
-    const size_t item_bytes = (size_t)4 * nf * nf * sizeof(float2);       // E0, E1, w, g
+    const size_t item_bytes = (size_t)3 * nf * nf * sizeof(float2);       // E1, w, g
     // wavelengths resident at once: the caller's bound, else what fits in 70 % of the free
     // memory next to a generous allowance for the Lyot plans' own buffers
     int res = d->max_resident > 0 ? d->max_resident : d->batch;
@@ -222,12 +230,12 @@ extern "C" coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* d
     const int R = p->resident;
     coro_status st = CORO_OK;
     const size_t fbytes = (size_t)R * nf * nf * sizeof(float2), mbytes = (size_t)nf * nf * sizeof(float);
-    p->e0 = (float2*)p->alloc(fbytes, &st);
-    p->e1 = p->e0 ? (float2*)p->alloc(fbytes, &st) : nullptr;
+    p->e1 = (float2*)p->alloc(fbytes, &st);
     p->w = p->e1 ? (float2*)p->alloc(fbytes, &st) : nullptr;
     p->g = p->w ? (float2*)p->alloc(fbytes, &st) : nullptr;
     p->opd1 = p->g ? (float*)p->alloc(mbytes, &st) : nullptr;
-    p->opd2 = p->opd1 ? (float*)p->alloc(mbytes, &st) : nullptr;
+    p->opd1n = p->opd1 ? (float*)p->alloc(mbytes, &st) : nullptr;
+    p->opd2 = p->opd1n ? (float*)p->alloc(mbytes, &st) : nullptr;
     p->opd2n = p->opd2 ? (float*)p->alloc(mbytes, &st) : nullptr;
     p->zero_h = p->opd2n ? (float*)p->alloc((size_t)2 * d->n_act * d->n_act * sizeof(float), &st) : nullptr;
     p->part = p->zero_h ? (float*)p->alloc((size_t)2 * R * d->n_act * d->n_act * sizeof(float), &st) : nullptr;
@@ -295,7 +303,7 @@ extern "C" coro_status coro_wfc_plan_evaluate(coro_plan plan, const float* heigh
     for (size_t k = 0; k < p->chunks.size() && st == CORO_OK; ++k) {
         Chunk& ch = p->chunks[k];
         const int nb = ch.nb;
-        // E0, E1 checkpoints and E3 (in w)
+        // E1 checkpoint and E3 (in w)
         if ((st = coro_fresnel_plan_execute(ch.fwd, p->w, nullptr)) != CORO_OK) break;
         if (!grad) {
             st = coro_lyot_plan_execute(ch.lyot, window(p, p->w), p->peak.data() + ch.b0, nullptr, nullptr,

@@ -423,6 +423,23 @@ def test_phase_grad_tap(ctx, n, dtype):
                 assert err < 1e-5, (rv, k, b, err)             # the map is written in float
 
 
+def test_phase_grad_tap_unit_reference(ctx):
+    """With no reference field the tap writes (scalar / lambda) 2 Im(field), here after an
+    angular-spectrum hop (the last plane of the plan, fftshift sign pending)."""
+    n, lam, dx, z = 512, 600e-9, 2e-5, 0.03
+    f0 = inputs.random_field((1, n, n), seed=31)
+    x = to_dev(f0, torch.complex64)
+    out = torch.zeros((1, n, n), dtype=torch.float32, device="cuda")
+    els = [coro.element(coro.EL_PHASE_GRAD, plane=1, scalar=2.0, store=out)]
+    plan = coro.FresnelPlan(ctx, n=n, batch=1, pixelscale=dx, wavelength=lam, distances=[z], elements=els)
+    plan.execute(x)
+    g = propagation.angular_spectrum(f0[0], dx, lam, z)
+    want = 2.0 / lam * 2 * np.imag(g)
+    got = out.cpu().numpy()[0]
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-5
+    assert rel_l2(x.cpu().numpy()[0], g) < 1e-5                # the field itself passes unchanged
+
+
 def test_checkpoint_after_direct_hop_and_apply(ctx):
     """A checkpoint at the focal plane of a direct hop (natural layout, new pixel scale), on
     two wavelengths; coro_apply_element with a checkpoint copies the field."""

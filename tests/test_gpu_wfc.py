@@ -230,7 +230,7 @@ def test_wfc_chunked_band_matches_resident(ctx):
 @pytest.mark.slow
 def test_wfc_8192_grid_196_actuators(ctx):
     """The N = 8192 case of Sec. 1.2: 196 x 196 actuators at seven pixels per actuator (a
-    1372-pixel pupil), two wavelengths run one per chunk (2 GiB of fields resident), against
+    1372-pixel pupil), two wavelengths run one per chunk (1.5 GiB of fields resident), against
     the FP64 oracle: per-wavelength dark-hole sums and the summed gradient (adjoint)."""
     nf, na, npix, D, z = 8192, 196, 1372, 0.0784, 0.3
     pitch = D / na
