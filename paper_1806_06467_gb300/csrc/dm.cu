@@ -185,20 +185,34 @@ dm_correlate_u(const float* __restrict__ w, DmGeom g, int len, int span, const f
         row[i] = (x >= 0 && x < g.n) ? __ldg(wr + x) : 0.f;
     }
     __syncwarp();
-    for (int q = 0; q < g.na; ++q) {
-        const int off = xs_tab[q] - xs0;
-        const int kend = min(len, span - off);
-        const float* gq = gx + (size_t)q * len;
-        float s0 = 0.f, s1 = 0.f;
-        int k = lane;
-        for (; k + 32 < kend; k += 64) {
-            s0 = fmaf(row[off + k], __ldg(gq + k), s0);
-            s1 = fmaf(row[off + k + 32], __ldg(gq + k + 32), s1);
+    // 32 columns q at a time: every lane sums its strided share of each column's window
+    // (p[j] for q = q0 + j), then a transposing butterfly (16 + 8 + 4 + 2 + 1 shuffles)
+    // leaves lane j with the total of column q0 + j
+    for (int q0 = 0; q0 < g.na; q0 += 32) {
+        float p[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int q = q0 + j;
+            float acc = 0.f;
+            if (q < g.na) {
+                const int off = xs_tab[q] - xs0;
+                const int kend = min(len, span - off);
+                const float* gq = gx + (size_t)q * len;
+                for (int k = lane; k < kend; k += 32) acc = fmaf(row[off + k], __ldg(gq + k), acc);
+            }
+            p[j] = acc;
         }
-        if (k < kend) s0 = fmaf(row[off + k], __ldg(gq + k), s0);
-        float sum = s0 + s1;
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-        if (lane == 0) ub[q] = sum;
+#pragma unroll
+        for (int wdt = 16; wdt >= 1; wdt >>= 1) {
+            const bool upper = lane & wdt;
+#pragma unroll
+            for (int j = 0; j < wdt; ++j) {
+                const float send = upper ? p[j] : p[j + wdt];
+                const float keep = upper ? p[j + wdt] : p[j];
+                p[j] = keep + __shfl_xor_sync(0xffffffffu, send, wdt);
+            }
+        }
+        if (q0 + lane < g.na) ub[q0 + lane] = p[0];
     }
 }
 
