@@ -569,6 +569,45 @@ def relay_mixed_bench(ctx, device, steps: int, n: int = 2800, npix: int = 700) -
             "workload": f"six-plane relay (5 hops) at N = {n} (npix {npix}), complex64, mixed-radix passes"}
 
 
+def coronagraph_fp64(ctx, device, steps: int = 3) -> dict:
+    """One PSF of the Lyot system through the FP64 calls on complex128 fields (MFT, spot,
+    inverse MFT, Babinet axpy, Lyot stop, MFT to the detector): the path that meets the 1e-11
+    dark-hole bar, timed for comparison with the split-precision plan."""
+    import numpy as np
+    import torch
+
+    from paper_1806_06467_gb300 import coro, inputs
+    w = inputs.LyotWorkload()
+    npix = float(w.npix)
+    e_a = torch.ones((1, w.n, w.n), dtype=torch.complex128, device=device)
+    coro.apply_element(ctx, e_a, 1.0 / npix, w.wavelength_m, coro.element(coro.EL_APERTURE, radius=0.5))
+    coro.apply_element(ctx, e_a, 1.0 / npix, w.wavelength_m,
+                       coro.element(coro.EL_ZERNIKE, radius=0.5, coeffs=w.zernike(), j_first=w.zernike_first))
+    spot = coro.element(coro.EL_CIRCLE, radius=w.spot_radius_lamd)
+    stop = coro.element(coro.EL_CIRCLE, radius=0.5 * w.lyot_frac)
+
+    def psf():
+        e_b = coro.propagate_mft(ctx, e_a, npix, -1, w.m_occ, [w.du_occ])
+        coro.apply_element(ctx, e_b, w.du_occ, w.wavelength_m, spot)
+        e_s = coro.propagate_mft(ctx, e_b, npix, +1, w.n, [w.du_occ])
+        coro.wavefront_axpy(ctx, -1.0, e_a, e_s)          # IMFT(spot . E_B) - E_A = -E_C (E_A kept)
+        coro.apply_element(ctx, e_s, 1.0 / npix, w.wavelength_m, stop)
+        return coro.propagate_mft(ctx, e_s, npix, -1, w.m_det, [w.du_det])   # -E_det: same PSF
+
+    psf()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(device)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        psf()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"value": 1e3 / ms, "unit": "PSFs/s", "ms_per_psf": ms, "precision": "FP64 (complex128)",
+            "workload": "Lyot system of the broadband batch at its centre wavelength, one PSF per call sequence"}
+
+
 def coronagraph_plain(device, steps: int, n_lambda: int = 21, n_probe: int = 8) -> dict:
     """Plain per-wavelength FP32 GPU form: torch.matmul (cuBLAS cgemm, complex64) MFT chain per
     wavelength over the 8 probe pupils, bases precomputed; same sizes as the batched plan."""
@@ -793,6 +832,7 @@ def main():
         extras["spc_system"] = spc_system_bench(ctx, device, max(3, args.steps // 2))
         extras["wfc_gradient"] = wfc_bench(ctx, device, max(3, args.steps // 4))
         extras["relay_mixed_radix"] = relay_mixed_bench(ctx, device, max(3, args.steps // 2))
+        extras["coronagraph_fp64"] = coronagraph_fp64(ctx, device)
     if rank == 0 and not args.no_plain:
         extras["plain_gpu"] = plain_gpu(n, maps_np, w, max(3, args.steps // 4), 2, device)
         extras["plain_gpu"]["speedup_of_coro"] = value / world / extras["plain_gpu"]["value"]
