@@ -379,13 +379,17 @@ typedef struct {
     double lyot_frac;     /* Lyot stop radius / pupil radius                                 */
     int m_det;            /* detector samples per axis                                       */
     const coro_lyot_item* items;  /* host [batch], copied                                    */
-    int precision;        /* CORO_MFT_3XTF32 or CORO_MFT_3XBF16                              */
+    int precision;        /* CORO_MFT_3XTF32 or CORO_MFT_3XBF16; or CORO_MFT_FP64: the same  */
+                          /* chain item by item on complex128 pupils/fields with FP64 MFTs  */
+                          /* (exact to FP64 rounding; execute, execute_n and peak only --    */
+                          /* execute_range, gradient and set_pupil_layout return            */
+                          /* CORO_ENOTIMPL; flops reports 0 tensor flops)                    */
 } coro_lyot_desc;
 
 coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc* desc, coro_plan* out);
-/* pupil: device complex64 [batch][n][n] (E_A). peak: host [batch] normalisation (NULL = 1).
- * intensity: device float [batch][m_det][m_det] or NULL. field: device complex64
- * [batch][m_det][m_det] (unnormalised E_det) or NULL. dh: host [batch] dark-hole sums or NULL
+/* pupil: device complex64 [batch][n][n] (E_A; complex128 for CORO_MFT_FP64). peak: host [batch]
+ * normalisation (NULL = 1). intensity: device float [batch][m_det][m_det] or NULL. field: device
+ * complex64 (complex128 for CORO_MFT_FP64) [batch][m_det][m_det] (unnormalised E_det) or NULL. dh: host [batch] dark-hole sums or NULL
  * (when given, the stream is synchronised). */
 coro_status coro_lyot_plan_execute(coro_plan plan, const void* pupil, const double* peak, float* intensity,
                                    void* field, double* dh);

@@ -129,6 +129,12 @@ inline cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t s) {
 
 // Twiddle table for n (built lazily on the context's stream).
 const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st);
+// The Lyot plan at reference precision (lyot64.cu): complex128 fields, FP64 MFTs, item by item.
+coro_status lyot64_create(coro_ctx ctx, const coro_lyot_desc* d, coro_plan* out);
+coro_status lyot64_peak(coro_plan plan, const void* pupil, double* peak_out);
+int lyot64_batch(coro_plan plan);
+coro_status lyot64_execute(coro_plan plan, const void* pupil, const double* peak, float* intensity, void* field,
+                           double* dh);
 
 
 // Stream-ordered copy of a host array into a fresh device block (freed with free_async).

@@ -90,8 +90,8 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
     clear_error();
     if (!ctx || !d || !out || !d->items) { set_error("coro_lyot_plan_create: NULL argument"); return CORO_EINVAL; }
     *out = nullptr;
-    if (d->precision != CORO_MFT_3XTF32 && d->precision != CORO_MFT_3XBF16) {
-        set_error("coro_lyot_plan_create: precision must be CORO_MFT_3XTF32 or CORO_MFT_3XBF16");
+    if (d->precision != CORO_MFT_3XTF32 && d->precision != CORO_MFT_3XBF16 && d->precision != CORO_MFT_FP64) {
+        set_error("coro_lyot_plan_create: precision must be CORO_MFT_3XTF32, CORO_MFT_3XBF16 or CORO_MFT_FP64");
         return CORO_EINVAL;
     }
     if (d->batch < 1 || d->batch > 65535) { set_error("coro_lyot_plan_create: batch %d", d->batch); return CORO_ESIZE; }
@@ -110,6 +110,7 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
         }
         if (it.m_occ > m_occ_max) m_occ_max = it.m_occ;
     }
+    if (d->precision == CORO_MFT_FP64) return lyot64_create(ctx, d, out);
     DeviceGuard g(ctx->device);
     auto p = std::unique_ptr<LyotPlan>(new (std::nothrow) LyotPlan);
     if (!p) { set_error("out of host memory"); return CORO_ENOMEM; }
@@ -309,9 +310,15 @@ cudaError_t run_stages(LyotPlan* p, const void* pupil, float* intensity, void* f
 
 }  // namespace
 
+namespace {
+// Items of a split-precision (kind 2) or FP64 (kind 4) Lyot plan.
+int lyot_batch(coro_plan plan) { return plan->kind() == 4 ? coro::lyot64_batch(plan) : static_cast<LyotPlan*>(plan)->batch; }
+}  // namespace
+
 extern "C" coro_status coro_lyot_plan_execute_range(coro_plan plan, const void* pupil, const double* peak,
                                                     float* intensity, void* field, int first, int count) {
     clear_error();
+    if (plan && plan->kind() == 4) { set_error("coro_lyot_plan_execute_range: not available at CORO_MFT_FP64"); return CORO_ENOTIMPL; }
     if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_execute_range: not a Lyot plan"); return CORO_EINVAL; }
     if (!pupil || first < 0 || count < 0 || first + count > 6) {
         set_error("coro_lyot_plan_execute_range: pupil NULL or stage range [%d, %d) outside [0, 6)", first, first + count);
@@ -331,13 +338,14 @@ extern "C" coro_status coro_lyot_plan_execute_range(coro_plan plan, const void* 
 extern "C" coro_status coro_lyot_plan_execute(coro_plan plan, const void* pupil, const double* peak, float* intensity,
                                               void* field, double* dh) {
     clear_error();
-    if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_execute: not a Lyot plan"); return CORO_EINVAL; }
+    if (!plan || (plan->kind() != 2 && plan->kind() != 4)) { set_error("coro_lyot_plan_execute: not a Lyot plan"); return CORO_EINVAL; }
     if (!pupil) { set_error("coro_lyot_plan_execute: pupil is NULL"); return CORO_EINVAL; }
-    auto* p = static_cast<LyotPlan*>(plan);
-    const int B = p->batch;
+    const int B = lyot_batch(plan);
     if (peak)
         for (int b = 0; b < B; ++b)
             if (!(peak[b] > 0)) { set_error("coro_lyot_plan_execute: peak[%d] must be > 0", b); return CORO_EINVAL; }
+    if (plan->kind() == 4) return lyot64_execute(plan, pupil, peak, intensity, field, dh);
+    auto* p = static_cast<LyotPlan*>(plan);
     DeviceGuard g(p->ctx->device);
     cudaStream_t s = p->ctx->stream;
     cudaError_t e = upload_det_items(p, peak);           // outside any graph: plain stream copy
@@ -359,8 +367,16 @@ extern "C" coro_status coro_lyot_plan_execute(coro_plan plan, const void* pupil,
 extern "C" coro_status coro_lyot_plan_execute_n(coro_plan plan, const void* pupil, const double* peak, float* intensity,
                                                 void* field, int times) {
     clear_error();
-    if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_execute_n: not a Lyot plan"); return CORO_EINVAL; }
+    if (!plan || (plan->kind() != 2 && plan->kind() != 4)) { set_error("coro_lyot_plan_execute_n: not a Lyot plan"); return CORO_EINVAL; }
     if (!pupil || times < 1) { set_error("coro_lyot_plan_execute_n: pupil NULL or times < 1"); return CORO_EINVAL; }
+    if (plan->kind() == 4) {
+        if (peak)
+            for (int b = 0; b < lyot_batch(plan); ++b)
+                if (!(peak[b] > 0)) { set_error("coro_lyot_plan_execute_n: peak[%d] must be > 0", b); return CORO_EINVAL; }
+        coro_status st = CORO_OK;
+        for (int k = 0; k < times && st == CORO_OK; ++k) st = lyot64_execute(plan, pupil, peak, intensity, field, nullptr);
+        return st;
+    }
     auto* p = static_cast<LyotPlan*>(plan);
     if (peak)
         for (int b = 0; b < p->batch; ++b)
@@ -378,6 +394,11 @@ extern "C" coro_status coro_lyot_plan_execute_n(coro_plan plan, const void* pupi
 
 extern "C" coro_status coro_lyot_plan_flops(coro_plan plan, double* useful, double* issued) {
     clear_error();
+    if (plan && plan->kind() == 4) {                       // no tensor-core work
+        if (useful) *useful = 0.0;
+        if (issued) *issued = 0.0;
+        return CORO_OK;
+    }
     if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_flops: not a Lyot plan"); return CORO_EINVAL; }
     auto* p = static_cast<LyotPlan*>(plan);
     const int B = p->batch, n = p->n, md = p->m_det, mo = p->m_occ_max;
@@ -393,6 +414,7 @@ extern "C" coro_status coro_lyot_plan_flops(coro_plan plan, double* useful, doub
 
 extern "C" coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, double* peak_out) {
     clear_error();
+    if (plan && plan->kind() == 4 && pupil && peak_out) return lyot64_peak(plan, pupil, peak_out);
     if (!plan || plan->kind() != 2 || !pupil || !peak_out) { set_error("coro_lyot_plan_peak: bad argument"); return CORO_EINVAL; }
     auto* p = static_cast<LyotPlan*>(plan);
     const int B = p->batch, n = p->n;
@@ -412,6 +434,10 @@ extern "C" coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, do
 
 extern "C" coro_status coro_lyot_plan_set_pupil_layout(coro_plan plan, int ld, long long bstride) {
     clear_error();
+    if (plan && plan->kind() == 4) {
+        set_error("coro_lyot_plan_set_pupil_layout: CORO_MFT_FP64 plans take contiguous [batch][n][n] pupils");
+        return CORO_ENOTIMPL;
+    }
     if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_set_pupil_layout: not a Lyot plan"); return CORO_EINVAL; }
     auto* p = static_cast<LyotPlan*>(plan);
     if (ld < p->n || bstride < (long long)ld * (p->n - 1) + p->n) {
@@ -451,6 +477,7 @@ coro_status prepare_gradient(LyotPlan* p) {
 extern "C" coro_status coro_lyot_plan_gradient(coro_plan plan, const void* pupil, const double* peak, double* dh_out,
                                                void* grad, int grad_ld, long long grad_bstride) {
     clear_error();
+    if (plan && plan->kind() == 4) { set_error("coro_lyot_plan_gradient: not available at CORO_MFT_FP64"); return CORO_ENOTIMPL; }
     if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_gradient: not a Lyot plan"); return CORO_EINVAL; }
     auto* p = static_cast<LyotPlan*>(plan);
     const int B = p->batch, n = p->n, md = p->m_det, mo = p->m_occ_max;

@@ -142,6 +142,63 @@ def test_lyot_fp64_chain_meets_darkhole_target(ctx):
     assert err <= DH_TARGET
 
 
+def test_lyot_plan_fp64_small_uneven_batch(ctx):
+    """The plan at CORO_MFT_FP64 (complex128 pupils and fields): per-item peaks, intensities,
+    the E_det field and dark-hole sums against the oracle on an uneven batch."""
+    n, npix, m_det, lyot = 128, 120, 96, 0.8
+    items = [dict(m_occ=40, du_occ=0.25, spot_radius=3.0, du_det=0.5, dh_in=4.0, dh_out=16.0),
+             dict(m_occ=37, du_occ=0.27, spot_radius=3.0, du_det=0.45, dh_in=4.0, dh_out=16.0),
+             dict(m_occ=45, du_occ=0.22, spot_radius=3.5, du_det=0.55, dh_in=4.5, dh_out=18.0)]
+    pupils = np.stack([zernike_pupil(n, npix, 550e-9, s, rms=20e-9) for s in range(3)])
+    x = torch.from_numpy(pupils).cuda()
+    plan = coro.LyotPlan(ctx, n=n, npix=npix, lyot_frac=lyot, m_det=m_det, items=items, precision=coro.MFT_FP64)
+    peak = plan.peak(x)
+    inten = torch.empty((3, m_det, m_det), dtype=torch.float32, device="cuda")
+    field = torch.empty((3, m_det, m_det), dtype=torch.complex128, device="cuda")
+    dh = plan.execute(x, peak=peak, intensity=inten, field=field)
+    got, got_f = inten.cpu().numpy(), field.cpu().numpy()
+    for b, it in enumerate(items):
+        ref_i, ref_s, ref_peak = oracle_psf(pupils[b], n, npix, it, lyot, m_det)
+        p = coronagraph.LyotParams(n=n, npix=npix, m_occ=it["m_occ"], du_occ=it["du_occ"],
+                                   spot_radius=it["spot_radius"], lyot_frac=lyot, m_det=m_det, du_det=it["du_det"])
+        ref_f = coronagraph.lyot_fields(pupils[b], p)["det"]
+        assert abs(peak[b] / ref_peak - 1) < 1e-12
+        mask = coronagraph.dark_hole_mask(m_det, it["du_det"], it["dh_in"], it["dh_out"]) > 0
+        i64 = np.abs(got_f[b]) ** 2 / peak[b]                  # the FP64 result; the float32
+        err = np.max(np.abs(i64[mask] - ref_i[mask]))          # intensity adds its own rounding
+        print(f"FP64 plan item {b}: max |dI| in dark hole {err:.3e}, S {dh[b]:.9e} vs {ref_s:.9e}")
+        assert err <= DH_TARGET
+        assert np.all(np.abs(got[b] - ref_i) <= 2.0 ** -23 * ref_i + 1e-13)
+        assert np.max(np.abs(got_f[b] - ref_f)) < 1e-10 * np.sqrt(ref_peak)
+        assert abs(dh[b] - ref_s) <= 1e-9 * ref_s
+    with pytest.raises(coro.CoroError):
+        plan.gradient(x, peak)
+    dh_default = plan.execute(x)                               # peak NULL = 1: unnormalised sums
+    np.testing.assert_allclose(dh_default, dh * peak, rtol=1e-12)
+
+
+def test_lyot_plan_fp64_full_size_meets_darkhole_target(ctx):
+    """The full-size Lyot system through the plan at CORO_MFT_FP64: |dI| <= 1e-11 in the dark
+    hole, the bar the split-precision plan misses."""
+    w = inputs.LyotWorkload()
+    pupil = zernike_pupil(w.n, w.npix, w.wavelength_m, w.seed)
+    x = torch.from_numpy(pupil).cuda().unsqueeze(0)
+    it = dict(m_occ=w.m_occ, du_occ=w.du_occ, spot_radius=w.spot_radius_lamd, du_det=w.du_det,
+              dh_in=w.dh_inner, dh_out=w.dh_outer)
+    plan = coro.LyotPlan(ctx, n=w.n, npix=w.npix, lyot_frac=w.lyot_frac, m_det=w.m_det, items=[it],
+                         precision=coro.MFT_FP64)
+    peak = plan.peak(x)
+    field = torch.empty((1, w.m_det, w.m_det), dtype=torch.complex128, device="cuda")
+    dh = plan.execute(x, peak=peak, field=field)
+    ref_i, ref_s, ref_peak = oracle_psf(pupil, w.n, w.npix, it, w.lyot_frac, w.m_det)
+    assert abs(peak[0] / ref_peak - 1) < 1e-12
+    mask = coronagraph.dark_hole_mask(w.m_det, w.du_det, w.dh_inner, w.dh_outer) > 0
+    err = np.max(np.abs(np.abs(field.cpu().numpy()[0][mask]) ** 2 / peak[0] - ref_i[mask]))
+    print(f"FP64 plan: max |dI| in the dark hole {err:.3e}, S {dh[0]:.9e} vs {ref_s:.9e}")
+    assert err <= DH_TARGET
+    assert abs(dh[0] - ref_s) <= 1e-9 * ref_s
+
+
 def test_lyot_graph_replay_matches_eager(ctx):
     """a10: the graph-replayed execute gives bitwise the eager result, follows new peak values
     (copied outside the graph) and re-captures when the output buffer changes."""
