@@ -262,8 +262,10 @@ coro_status coro_fresnel_plan_execute(coro_plan plan, void* field, double* pixel
 coro_status coro_fresnel_plan_execute_n(coro_plan plan, void* field, int times);
 /* Number of kernels one execute launches (for launch accounting). */
 coro_status coro_plan_launch_count(coro_plan plan, int* out);
-/* Run passes [first, first + count) of the plan only (for per-launch timing); running every
- * range in order is identical to coro_fresnel_plan_execute. */
+/* Run passes [first, first + count) of the plan only (for per-launch timing); ranges always
+ * run every pass in place on the natural layout, so running every range in order matches
+ * coro_fresnel_plan_execute exactly for a plan on the natural layout and up to FP32 rounding
+ * order for one on the alternating layout (coro_fresnel_plan_set_layout). */
 coro_status coro_fresnel_plan_execute_range(coro_plan plan, void* field, int first, int count);
 /* Describe pass i: *is_row (1 = row pass, 0 = column pass) and *bytes, the algorithmic HBM
  * traffic of the launch (field read unless generated, field write, OPD/amplitude maps read). */
@@ -282,6 +284,8 @@ coro_status coro_fresnel_plan_pass_info(coro_plan plan, int i, int* is_row, doub
  * *lines = columns per group for a column pass, 0 for a row pass. Either output pointer may
  * be NULL. Plain host query; no device work. */
 coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent, int* lines);
+/* (*persistent 6: mixed-radix kernels for n not a power of two; 7: the packed-pair kernels of
+ * the alternating layout, below.) */
 /* Override the tuned kernel choice of every pass of a complex64 plan.
  *   row_variant: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row
  *                pairs (2 and 3: N = 1024 ... 4096).
@@ -291,6 +295,19 @@ coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent
  * Values the plan's N does not offer are rejected with CORO_EINVAL and nothing changes.
  * Every choice gives the same result up to FP32 rounding order (used to test each kernel). */
 coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, int col_lines);
+/* (set_pass_kernel also returns the plan to the natural layout.)
+ * Plane layout between passes (complex64 plans, n = 1024, 2048, 4096). Natural (0): every
+ * pass transforms the field in place, column passes reading and writing strided column
+ * pairs. Alternating (1): a column pass followed by a row pass writes its result transposed
+ * ([b][x][y], contiguous rows) into a plane the plan owns (batch x n x n complex64, allocated
+ * here, freed on return to 0 or with the plan), and the row pass reads it back column-wise
+ * and writes the field's rows; each pass then has one strided side. Results agree up to FP32
+ * rounding order. At creation the plan times both and keeps the faster (natural when
+ * CORO_AUTOTUNE=0) unless the environment sets CORO_LAYOUT=0 (natural) or CORO_LAYOUT=1
+ * (alternating). CORO_ENOTIMPL: the plan has no column pass followed by a row pass at a
+ * supported size. */
+coro_status coro_fresnel_plan_set_layout(coro_plan plan, int transposed);
+coro_status coro_fresnel_plan_layout(coro_plan plan, int* transposed);
 /* a10: replay plan execution as one CUDA graph (enable = 1) or launch kernel by kernel (0,
  * the default). With graphs on, the first execute with a given set of device pointers
  * (field; or pupil, intensity and field) runs eagerly and captures its launch sequence on a

@@ -118,6 +118,8 @@ _SIGS = {
     "coro_fresnel_plan_pass_info": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]),
     "coro_fresnel_plan_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "coro_fresnel_plan_set_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.c_int]),
+    "coro_fresnel_plan_set_layout": (ct.c_int, [_P, ct.c_int]),
+    "coro_fresnel_plan_layout": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "coro_selftest_wait_timeout": (ct.c_int, [_P, ct.c_int]),
     "coro_plan_set_timing": (ct.c_int, [_P, ct.c_int]),
     "coro_plan_unit_times": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_float)]),
@@ -547,7 +549,7 @@ class FresnelPlan:
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_kernel(self.handle, i, ct.byref(p), ct.byref(w)))
         row, _ = self.pass_info(i)
         kind = "row_pass" if row else "col_pass"
-        name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide", "", "_mixed")[p.value]
+        name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide", "", "_mixed", "_pair_t")[p.value]
         return f"{name}<{self.n}>" if row else f"{name}<{self.n},{w.value}>"
 
     def set_pass_kernel(self, row_variant: int, col_lines: int) -> None:
@@ -556,6 +558,18 @@ class FresnelPlan:
         lines per block, -1 persistent TMA, -2 units, -3 packed column pairs, -4 wide
         four-column groups, 0 default)."""
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_set_pass_kernel(self.handle, row_variant, col_lines))
+
+    def set_layout(self, transposed: bool) -> None:
+        """Natural (False) or alternating (True) plane layout between passes
+        (coro_fresnel_plan_set_layout)."""
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_set_layout(self.handle, 1 if transposed else 0))
+
+    @property
+    def layout(self) -> bool:
+        """True when the plan runs on the alternating layout."""
+        t = ct.c_int()
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_layout(self.handle, ct.byref(t)))
+        return bool(t.value)
 
     @property
     def launch_count(self) -> int:

@@ -540,9 +540,11 @@ struct Op {
 };
 
 // ev (optional, ops.size() + 1 events): recorded before the first pass and after each.
+// tbuf: the plane that column passes with lines -6 write transposed and the row passes of
+// variant 4 read back (batch x n x n samples); NULL when the ops hold neither.
 template <typename C>
 coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, void* field,
-                    const cudaEvent_t* ev = nullptr) {
+                    const cudaEvent_t* ev = nullptr, void* tbuf = nullptr) {
     coro_status st = CORO_OK;
     const C* tw = (const C*)get_twiddles(ctx, n, sizeof(C) == sizeof(double2), &st);
     if (!tw) return st;
@@ -554,9 +556,11 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
     int i = 0;
     for (const Op& op : ops) {
         cudaError_t e;
+        const bool t_in = op.row && op.variant == 4, t_out = !op.row && op.lines == -6;
+        if ((t_in || t_out) && !tbuf) { set_error("transposed pass without its plane"); return CORO_EINVAL; }
         if (op.row) {
             RowArgs<C> a;
-            a.in = (const C*)field;
+            a.in = (const C*)(t_in ? tbuf : field);
             a.out = (C*)field;
             a.tw = tw;
             a.flags = op.row_flags;
@@ -567,7 +571,7 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
         } else {
             ColArgs<C> a;
             a.in = (const C*)field;
-            a.out = (C*)field;
+            a.out = (C*)(t_out ? tbuf : field);
             a.tw = tw;
             a.tab_x = (const C*)op.tab_x;
             a.tab_y = (const C*)op.tab_y;
@@ -583,9 +587,9 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
 }
 
 coro_status run_ops_any(coro_ctx ctx, int dtype, int n, int batch, const std::vector<Op>& ops, void* field,
-                        const cudaEvent_t* ev = nullptr) {
-    return dtype == CORO_C64 ? run_ops<float2>(ctx, n, batch, ops, field, ev)
-                             : run_ops<double2>(ctx, n, batch, ops, field, ev);
+                        const cudaEvent_t* ev = nullptr, void* tbuf = nullptr) {
+    return dtype == CORO_C64 ? run_ops<float2>(ctx, n, batch, ops, field, ev, tbuf)
+                             : run_ops<double2>(ctx, n, batch, ops, field, ev, tbuf);
 }
 
 // ------------------------------------------------------------------------------ hop tables
@@ -805,15 +809,16 @@ bool autotune_enabled() {
 }
 
 template <typename C>
-float time_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, void* field, int reps) {
+float time_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, void* field, int reps,
+               void* tbuf = nullptr) {
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess) return 1e30f;
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 1e30f; }
     float ms = 1e30f;
-    if (run_ops<C>(ctx, n, batch, ops, field) == CORO_OK) {          // warm-up
+    if (run_ops<C>(ctx, n, batch, ops, field, nullptr, tbuf) == CORO_OK) {          // warm-up
         cudaEventRecord(a, ctx->stream);
         bool ok = true;
-        for (int r = 0; r < reps && ok; ++r) ok = run_ops<C>(ctx, n, batch, ops, field) == CORO_OK;
+        for (int r = 0; r < reps && ok; ++r) ok = run_ops<C>(ctx, n, batch, ops, field, nullptr, tbuf) == CORO_OK;
         cudaEventRecord(b, ctx->stream);
         if (ok && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
     }
@@ -871,7 +876,9 @@ struct FresnelPlan : coro_plan_s {
     coro_ctx ctx = nullptr;
     int device = 0;                  // kept so that destruction never touches the context
     int dtype = CORO_C64, n = 0, batch = 0;
-    std::vector<Op> ops;
+    std::vector<Op> ops;             // as executed
+    std::vector<Op> ops_nat;         // the same passes, every one in place on the natural layout
+    void* tbuf = nullptr;            // transposed plane of the alternating layout (owned)
     DevBlocks db;
     std::vector<double> ps_final;
     std::vector<std::string> tune_log;
@@ -888,8 +895,57 @@ struct FresnelPlan : coro_plan_s {
         timing.release();
         graph.reset();
         db.release();
+        if (tbuf) cudaFree(tbuf);
     }
 };
+
+// Alternating layout (complex64, n = 1024 ... 4096): a column pass followed by a row pass is
+// run as the packed-pair column kernel writing its result transposed into tbuf (contiguous
+// rows) and the packed-pair row kernel reading it back column-wise (TMA boxes), so that each
+// of the two passes has one strided side instead of the column pass having two. Every other
+// pass stays in place. Returns the number of such pairs.
+int transposed_ops(int dtype, int n, const std::vector<Op>& nat, std::vector<Op>* out) {
+    if (out) *out = nat;
+    if (dtype != CORO_C64 || n < 1024 || n > 4096 || (n & (n - 1))) return 0;
+    int pairs = 0;
+    for (size_t i = 0; i + 1 < nat.size(); ++i) {
+        if (nat[i].row || !nat[i + 1].row || (nat[i + 1].row_flags & RF_INIT_ONE)) continue;
+        if (out) {
+            (*out)[i].lines = -6;
+            (*out)[i + 1].variant = 4;
+        }
+        ++pairs;
+        ++i;
+    }
+    return pairs;
+}
+
+// Switch a plan between the natural (0) and the alternating (1) layout. CORO_ENOTIMPL where
+// the plan has no column pass followed by a row pass at a size the pair kernels take.
+coro_status set_layout(FresnelPlan* p, int transposed) {
+    DeviceGuard g(p->device);
+    std::vector<Op> t;
+    if (transposed) {
+        if (transposed_ops(p->dtype, p->n, p->ops_nat, &t) == 0) {
+            set_error("alternating layout: complex64 plans with n = 1024, 2048 or 4096 and a column pass followed by a row pass only");
+            return CORO_ENOTIMPL;
+        }
+        if (!p->tbuf) {
+            const cudaError_t e = cudaMalloc(&p->tbuf, (size_t)p->batch * p->n * p->n * sizeof(float2));
+            if (e != cudaSuccess) { p->tbuf = nullptr; return cuda_fail(e, "alternating layout plane"); }
+        }
+        p->ops = t;
+    } else {
+        p->ops = p->ops_nat;
+        if (p->tbuf) {
+            cudaDeviceSynchronize();
+            cudaFree(p->tbuf);
+            p->tbuf = nullptr;
+        }
+    }
+    p->graph.reset();                                   // a captured graph holds the old kernels
+    return CORO_OK;
+}
 
 }  // namespace
 
@@ -1006,10 +1062,35 @@ coro_status build_passes(FresnelPlan* plan, int n, int batch, const double* ps0,
     return CORO_OK;
 }
 
+// Layout choice: CORO_LAYOUT=0 / 1 forces the natural / alternating layout; otherwise the
+// alternating one is timed against the natural one when tuning is on and kept if faster
+// (natural without tuning).
+void choose_layout(FresnelPlan* p) {
+    if (transposed_ops(p->dtype, p->n, p->ops_nat, nullptr) == 0) return;
+    const char* v = std::getenv("CORO_LAYOUT");
+    const bool force = v && v[0] == '1';
+    if ((v && v[0] == '0') || (!force && !autotune_enabled())) return;
+    if (set_layout(p, 1) != CORO_OK) { clear_error(); return; }     // no room: natural layout
+    if (force) return;
+    coro_status st = CORO_OK;
+    const size_t bytes = (size_t)p->batch * p->n * p->n * sizeof(float2);
+    void* scratch = upload_async(p->ctx, nullptr, bytes, &st);
+    if (!scratch) { clear_error(); return; }
+    cudaMemsetAsync(scratch, 0, bytes, p->ctx->stream);
+    const float t_nat = time_ops<float2>(p->ctx, p->n, p->batch, p->ops_nat, scratch, 3);
+    const float t_alt = time_ops<float2>(p->ctx, p->n, p->batch, p->ops, scratch, 3, p->tbuf);
+    free_async(p->ctx, scratch);
+    p->tune_log.push_back("layout natural: " + std::to_string(t_nat / 3) + " ms, alternating: " +
+                          std::to_string(t_alt / 3) + " ms");
+    if (!(t_alt < t_nat)) set_layout(p, 0);
+}
+
 coro_status finish_plan(coro_ctx ctx, std::unique_ptr<FresnelPlan>& plan, coro_plan* out, const char* who) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);   // tables ready; plan owns them
     if (e == cudaSuccess) {
         autotune_ops(ctx, plan->dtype, plan->n, plan->batch, plan->ops, &plan->tune_log);
+        plan->ops_nat = plan->ops;
+        choose_layout(plan.get());
         e = cudaStreamSynchronize(ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, who);
@@ -1221,7 +1302,7 @@ extern "C" coro_status coro_fresnel_plan_execute(coro_plan plan, void* field, do
     auto* p = static_cast<FresnelPlan*>(plan);
     DeviceGuard g(p->ctx->device);
     coro_status st = run_graphed(p->ctx, p->graph, {field, (const void*)1}, [&]() {
-        return run_ops_any(p->ctx, p->dtype, p->n, p->batch, p->ops, field, p->timing.set(0));
+        return run_ops_any(p->ctx, p->dtype, p->n, p->batch, p->ops, field, p->timing.set(0), p->tbuf);
     });
     if (st == CORO_OK && pixelscale_out)
         for (int b = 0; b < p->batch; ++b) pixelscale_out[b] = p->ps_final[b];
@@ -1237,7 +1318,7 @@ extern "C" coro_status coro_fresnel_plan_execute_n(coro_plan plan, void* field, 
     return run_graphed(p->ctx, p->graph, {field, (const void*)(intptr_t)times}, [&]() {
         coro_status st = CORO_OK;
         for (int k = 0; k < times && st == CORO_OK; ++k)
-            st = run_ops_any(p->ctx, p->dtype, p->n, p->batch, p->ops, field, p->timing.set(k));
+            st = run_ops_any(p->ctx, p->dtype, p->n, p->batch, p->ops, field, p->timing.set(k), p->tbuf);
         return st;
     });
 }
@@ -1251,7 +1332,7 @@ extern "C" coro_status coro_fresnel_plan_execute_range(coro_plan plan, void* fie
         return CORO_EINVAL;
     }
     DeviceGuard g(p->ctx->device);
-    std::vector<Op> sub(p->ops.begin() + first, p->ops.begin() + first + count);
+    std::vector<Op> sub(p->ops_nat.begin() + first, p->ops_nat.begin() + first + count);   // in place
     return run_ops_any(p->ctx, p->dtype, p->n, p->batch, sub, field);
 }
 
@@ -1305,11 +1386,24 @@ extern "C" coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row
         set_error("coro_fresnel_plan_set_pass_kernel: column kernel %d not offered at n=%d", col_lines, p->n);
         return CORO_EINVAL;
     }
-    for (Op& op : p->ops) {
+    for (Op& op : p->ops_nat) {
         if (op.row) op.variant = row_variant;
         else op.lines = col_lines;
     }
-    p->graph.reset();                                   // a captured graph holds the old kernels
+    return set_layout(p, 0);                            // every pass in place with these kernels
+}
+
+extern "C" coro_status coro_fresnel_plan_set_layout(coro_plan plan, int transposed) {
+    clear_error();
+    if (!plan || plan->kind() != 1) { set_error("coro_fresnel_plan_set_layout: not a Fresnel plan"); return CORO_EINVAL; }
+    if (transposed != 0 && transposed != 1) { set_error("coro_fresnel_plan_set_layout: transposed must be 0 or 1"); return CORO_EINVAL; }
+    return set_layout(static_cast<FresnelPlan*>(plan), transposed);
+}
+
+extern "C" coro_status coro_fresnel_plan_layout(coro_plan plan, int* transposed) {
+    clear_error();
+    if (!plan || plan->kind() != 1 || !transposed) { set_error("coro_fresnel_plan_layout: bad argument"); return CORO_EINVAL; }
+    *transposed = static_cast<FresnelPlan*>(plan)->tbuf ? 1 : 0;
     return CORO_OK;
 }
 

@@ -928,7 +928,9 @@ template <int N, int U, int S> struct PColPairCfg {
     }
 };
 
-template <int N, int U, int S>
+// TOUT: the pair leaves as two contiguous rows of the transposed plane out[b][x][y] (one bulk
+// store of 2N samples) instead of two strided columns of out[b][y][x]; out must not alias in.
+template <int N, int U, int S, bool TOUT>
 __global__ void __launch_bounds__(PColPairCfg<N, U, S>::THREADS, 1)
 col_pass_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_constant__ CUtensorMap map, int groups) {
     using Cfg = PColPairCfg<N, U, S>;
@@ -997,20 +999,35 @@ col_pass_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_con
                 v[s] = CP{pk::sub2(pk::mul2(v[s].re, hr), pk::mul2(v[s].im, hi)),
                           pk::fma2(v[s].re, hi, pk::mul2(v[s].im, hr))};
         }
-        float4* out = reinterpret_cast<float4*>(region);
+        if constexpr (TOUT) {
 #pragma unroll
-        for (int s = 0; s < 16; ++s) {
-            float4 q;
-            pk::unpack(v[s].re, q.x, q.z);
-            pk::unpack(v[s].im, q.y, q.w);
-            out[t + s * Cfg::TPL] = q;
+            for (int s = 0; s < 16; ++s) {
+                float2 qa, qb;
+                pk::unpack(v[s].re, qa.x, qb.x);
+                pk::unpack(v[s].im, qa.y, qb.y);
+                region[t + s * Cfg::TPL] = qa;
+                region[N + t + s * Cfg::TPL] = qb;
+            }
+        } else {
+            float4* out = reinterpret_cast<float4*>(region);
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                float4 q;
+                pk::unpack(v[s].re, q.x, q.z);
+                pk::unpack(v[s].im, q.y, q.w);
+                out[t + s * Cfg::TPL] = q;
+            }
         }
         tc::fence_proxy_async();
         sync();
         if (leader) {
-            const int x = col, y = b * N;
+            if constexpr (TOUT) {
+                tc::bulk_store(a.out + ((size_t)b * N + col) * N, region, BYTES);
+            } else {
+                const int x = col, y = b * N;
 #pragma unroll 1
-            for (int q = 0; q < Cfg::BOXES; ++q) tc::tma_store_2d(&map, region + q * 512, x, y + q * 256);
+                for (int q = 0; q < Cfg::BOXES; ++q) tc::tma_store_2d(&map, region + q * 512, x, y + q * 256);
+            }
             tc::bulk_commit();
         }
     }
@@ -1221,9 +1238,12 @@ template <int N, int U, int S> struct PRowPairCfg {
     static constexpr size_t smem() { return ((size_t)S * GROUP + (size_t)U * REGION) * 8 + 8 * U; }
 };
 
-template <int N, int U, int S>
+// TIN: the pair arrives as two columns of the transposed plane in[b][x][y] (TMA boxes of
+// 2 x 256 through `map`, as in the column pass) instead of two contiguous rows; in must not
+// alias out. Without TIN `map` is unused.
+template <int N, int U, int S, bool TIN>
 __global__ void __launch_bounds__(PRowPairCfg<N, U, S>::THREADS, 1)
-row_pass_pair_kernel(const __grid_constant__ RowArgs<float2> a, int pairs) {
+row_pass_pair_kernel(const __grid_constant__ RowArgs<float2> a, const __grid_constant__ CUtensorMap map, int pairs) {
     using Cfg = PRowPairCfg<N, U, S>;
     using pk::CP;
     constexpr uint32_t BYTES = Cfg::GROUP * sizeof(float2);
@@ -1241,13 +1261,21 @@ row_pass_pair_kernel(const __grid_constant__ RowArgs<float2> a, int pairs) {
     auto issue_load = [&](int k) {
         const int g = blockIdx.x + k * gridDim.x;
         uint64_t* bar = &full[k % U];
+        float2* dst = stage + (k % S) * Cfg::GROUP;
         tc::mbar_arrive_expect_tx(bar, BYTES);
-        tc::bulk_load(stage + (k % S) * Cfg::GROUP, a.in + (size_t)g * Cfg::GROUP, BYTES, bar);
+        if constexpr (TIN) {
+            const int x = (2 * g) % N, y = ((2 * g) / N) * N;     // first line of the pair, item's rows
+#pragma unroll 1
+            for (int q = 0; q < N / 256; ++q) tc::tma_load_2d(dst + q * 512, &map, bar, x, y + q * 256);
+        } else {
+            tc::bulk_load(dst, a.in + (size_t)g * Cfg::GROUP, BYTES, bar);
+        }
     };
     const int mine = pairs > (int)blockIdx.x ? (pairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < U; ++i) tc::mbar_init(&full[i], 1);
         tc::fence_mbar_init();
+        if constexpr (TIN) tc::prefetch_tmap(&map);
         if (load)
             for (int k = 0; k < S && k < mine; ++k) issue_load(k);
     }
@@ -1261,10 +1289,19 @@ row_pass_pair_kernel(const __grid_constant__ RowArgs<float2> a, int pairs) {
         if (load) {
             const float2* src = stage + (k % S) * Cfg::GROUP;
             if (ok) ok = tc::mbar_wait(&full[u], j & 1, a.err, 11);
+            if constexpr (TIN) {
+                const float4* src4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
-            for (int s = 0; s < 16; ++s) {
-                const float2 qa = src[t + s * Cfg::TPL], qb = src[N + t + s * Cfg::TPL];
-                v[s] = CP{pk::pack(qa.x, qb.x), pk::pack(qa.y, qb.y)};
+                for (int s = 0; s < 16; ++s) {
+                    const float4 q = src4[t + s * Cfg::TPL];   // sample t + s*TPL: (re_A, im_A, re_B, im_B)
+                    v[s] = CP{pk::pack(q.x, q.z), pk::pack(q.y, q.w)};
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const float2 qa = src[t + s * Cfg::TPL], qb = src[N + t + s * Cfg::TPL];
+                    v[s] = CP{pk::pack(qa.x, qb.x), pk::pack(qa.y, qb.y)};
+                }
             }
         } else {
             const pk::u64 one = pk::pack(1.f, 1.f);

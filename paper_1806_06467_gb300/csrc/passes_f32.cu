@@ -16,14 +16,17 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
         case 256: return row_launch<float2, 256>(a, l);
         case 512: return row_launch<float2, 512>(a, l);
         case 1024:
+            if (l.variant == 4) return row_launch_pair<1024, 8, 4, true>(a, l);
             if (l.variant == 3) return row_launch_pair<1024, 8, 4>(a, l);
             if (l.variant == 2) return row_launch_units<float2, 1024, 8, 4>(a, l);
             return l.variant == 1 ? row_launch<float2, 1024>(a, l) : row_launch_persistent<float2, 1024>(a, l);
         case 2048:
+            if (l.variant == 4) return row_launch_pair<2048, 4, 2, true>(a, l);
             if (l.variant == 3) return row_launch_pair<2048, 4, 2>(a, l);
             if (l.variant == 2) return row_launch_units<float2, 2048, 8, 4>(a, l);
             return l.variant == 1 ? row_launch<float2, 2048>(a, l) : row_launch_persistent<float2, 2048>(a, l);
         case 4096:
+            if (l.variant == 4) return row_launch_pair<4096, 2, 1, true>(a, l);
             if (l.variant == 3) return row_launch_pair<4096, 2, 1>(a, l);
             if (l.variant == 2) return row_launch_units<float2, 4096, 4, 2>(a, l);
             return l.variant == 1 ? row_launch<float2, 4096>(a, l) : row_launch_persistent<float2, 4096>(a, l);
@@ -35,7 +38,8 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
 // lines = columns per block; 0 = default. Wider blocks give longer contiguous segments per
 // row (L * 8 bytes), narrower ones more resident blocks per SM. -1 = persistent TMA kernel,
 // -2 = unit-pipelined kernel (two columns per unit), -3 = unit-pipelined kernel on packed
-// FP32x2 column pairs, -4 = wide kernel (four columns, packed pairs, staged by TMA).
+// FP32x2 column pairs, -4 = wide kernel (four columns, packed pairs, staged by TMA), -6 = the
+// packed-pair kernel writing its result transposed to a separate plane (row variant 4 reads it).
 template <>
 cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, const PassLaunch& l) {
     using namespace detail;
@@ -48,18 +52,21 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
         case 512: return col_launch<float2, 512, 16>(a, l);
         case 1024:
             if (lines == -4) return col_launch_wide<1024>(a, l);
+            if (lines == -6) return col_launch_pair<1024, 8, 4, true>(a, l);
             if (lines == -3) return col_launch_pair<1024, 8, 4>(a, l);
             if (lines == -2) return col_launch_units<float2, 1024, 2, 8, 4>(a, l);
             if (lines == -1) return col_launch_persistent<float2, 1024, 4>(a, l);
             return lines == 8 ? col_launch<float2, 1024, 8>(a, l) : col_launch<float2, 1024, 16>(a, l);
         case 2048:
             if (lines == -4) return col_launch_wide<2048>(a, l);
+            if (lines == -6) return col_launch_pair<2048, 4, 2, true>(a, l);
             if (lines == -3) return col_launch_pair<2048, 4, 2>(a, l);
             if (lines == -2) return col_launch_units<float2, 2048, 2, 4, 2>(a, l);
             if (lines == -1) return col_launch_persistent<float2, 2048, 2>(a, l);
             return lines == 4 ? col_launch<float2, 2048, 4>(a, l) : col_launch<float2, 2048, 8>(a, l);
         case 4096:
             if (lines == -4) return col_launch_wide<4096>(a, l);
+            if (lines == -6) return col_launch_pair<4096, 2, 1, true>(a, l);
             if (lines == -3) return col_launch_pair<4096, 2, 1>(a, l);
             if (lines == -2) return col_launch_units<float2, 4096, 2, 2, 1>(a, l);
             if (lines == -1) return col_launch_persistent<float2, 4096, 2>(a, l);
@@ -99,6 +106,8 @@ int col_candidates(int n, int* out) {
 }
 
 // row variants: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row pairs
+// (4, packed row pairs read from a transposed plane, is only paired with column lines -6 and is
+// not a tuning candidate)
 int row_variant_count(int n) { return (n >= 1024 && n <= 4096) ? 4 : n == 8192 ? 2 : 1; }
 
 bool mixed_length_ok(int n, bool dbl) { return dbl ? mixed_supported<double2>(n) : mixed_supported<float2>(n); }
@@ -113,6 +122,7 @@ void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persi
     if (variant < 0) variant = row_variant_default(n);
     if (row) {                                              // mirrors launch_row_pass
         p = (!dbl && n >= 1024) ? (variant == 1 ? 0 : (variant == 2 || variant == 3) && n <= 4096 ? variant : 1) : 0;
+        if (!dbl && variant == 4 && n >= 1024 && n <= 4096) p = 7;
     } else if (dbl) {
         w = col_lines_default(n, true);                     // the double launcher ignores `lines`
     } else {                                                // mirrors launch_col_pass<float2>
@@ -124,6 +134,7 @@ void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persi
             case 8192: w = lines == 1 ? 1 : 2; break;
             default: w = 16; break;
         }
+        if (p == 6) p = 7;                                  // lines -6: transposed packed pairs
     }
     if (persistent) *persistent = p;
     if (out_lines) *out_lines = w;

@@ -1,6 +1,8 @@
 // passes_launch.cuh -- instantiation and launch of the row/column pass kernels for one
 // complex type. Included once per precision (passes_f32.cu, passes_f64.cu).
 #pragma once
+#include <cstring>
+
 #include "passes.cuh"
 #include "tc_gemm.cuh"
 
@@ -124,21 +126,22 @@ cudaError_t col_launch_units(const ColArgs<C>& a, const PassLaunch& l) {
     return cudaGetLastError();
 }
 
-template <int N, int U, int S>
+// TOUT: out-of-place, the result transposed (out[b][x][y]).
+template <int N, int U, int S, bool TOUT = false>
 cudaError_t col_launch_pair(const ColArgs<float2>& a, const PassLaunch& l) {
     using Cfg = PColPairCfg<N, U, S>;
     static unsigned done = 0;
     const size_t smem = Cfg::template smem<float2>();
-    cudaError_t e = ensure_smem(col_pass_pair_kernel<N, U, S>, smem, done);
+    cudaError_t e = ensure_smem(col_pass_pair_kernel<N, U, S, TOUT>, smem, done);
     if (e != cudaSuccess) return e;
     int sms = 0;
     if ((e = sm_count(&sms)) != cudaSuccess) return e;
-    if (a.in != a.out) return cudaErrorInvalidValue;
+    if ((a.in != a.out) != TOUT) return cudaErrorInvalidValue;
     CUtensorMap map;
     if ((e = tc_make_field_map(a.in, N, (long long)l.batch * N, 2, &map)) != cudaSuccess) return e;
     const int groups = l.batch * N / 2;
     const int grid = groups < sms ? groups : sms;
-    col_pass_pair_kernel<N, U, S><<<grid, Cfg::THREADS, smem, l.stream>>>(a, map, groups);
+    col_pass_pair_kernel<N, U, S, TOUT><<<grid, Cfg::THREADS, smem, l.stream>>>(a, map, groups);
     return cudaGetLastError();
 }
 
@@ -181,18 +184,24 @@ cudaError_t row_launch_units(const RowArgs<C>& a, const PassLaunch& l) {
     return cudaGetLastError();
 }
 
-template <int N, int U, int S>
+template <int N, int U, int S, bool TIN = false>
 cudaError_t row_launch_pair(const RowArgs<float2>& a, const PassLaunch& l) {
     using Cfg = PRowPairCfg<N, U, S>;
     static unsigned done = 0;
     const size_t smem = Cfg::smem();
-    cudaError_t e = ensure_smem(row_pass_pair_kernel<N, U, S>, smem, done);
+    cudaError_t e = ensure_smem(row_pass_pair_kernel<N, U, S, TIN>, smem, done);
     if (e != cudaSuccess) return e;
     int sms = 0;
     if ((e = sm_count(&sms)) != cudaSuccess) return e;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    if constexpr (TIN) {                    // out-of-place; input transposed (in[b][x][y])
+        if (a.in == a.out || (a.flags & RF_INIT_ONE)) return cudaErrorInvalidValue;
+        if ((e = tc_make_field_map(a.in, N, (long long)l.batch * N, 2, &map)) != cudaSuccess) return e;
+    }
     const int pairs = l.batch * N / 2;
     const int grid = pairs < sms ? pairs : sms;
-    row_pass_pair_kernel<N, U, S><<<grid, Cfg::THREADS, smem, l.stream>>>(a, pairs);
+    row_pass_pair_kernel<N, U, S, TIN><<<grid, Cfg::THREADS, smem, l.stream>>>(a, map, pairs);
     return cudaGetLastError();
 }
 
