@@ -467,7 +467,9 @@ typedef struct {
     const coro_lyot_item* items;  /* host [batch], one Lyot item per wavelength            */
     int precision;                /* CORO_MFT_3XTF32 or CORO_MFT_3XBF16                    */
     int max_resident;             /* wavelengths held in HBM at once (3 x 8 n_fresnel^2    */
-                                  /* bytes each); 0 = as many as fit in 70 % of the free   */
+                                  /* bytes each, 5 x where the Fresnel plans may take the  */
+                                  /* alternating layout: n_fresnel 1024 ... 4096); 0 = as  */
+                                  /* many as fit in 70 % of the free                       */
                                   /* device memory. The band runs in chunks of that many,  */
                                   /* with the same results (per-item sums in item order).  */
 } coro_wfc_desc;

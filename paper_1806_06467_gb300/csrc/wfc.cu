@@ -214,7 +214,9 @@ extern "C" coro_status coro_wfc_plan_create(coro_ctx ctx, const coro_wfc_desc* d
     p->d.wavelength = p->lam.data();
     p->d.items = p->items.data();
     const int nf = d->n_fresnel;
-    const size_t item_bytes = (size_t)3 * nf * nf * sizeof(float2);       // E1, w, g
+    // E1, w, g; plus the transposed planes of the forward and adjoint plans should their
+    // tuner pick the alternating layout (n_fresnel 1024 ... 4096)
+    const size_t item_bytes = (size_t)(nf >= 1024 && nf <= 4096 ? 5 : 3) * nf * nf * sizeof(float2);
     // wavelengths resident at once: the caller's bound, else what fits in 70 % of the free
     // memory next to a generous allowance for the Lyot plans' own buffers
     int res = d->max_resident > 0 ? d->max_resident : d->batch;
