@@ -755,6 +755,12 @@ def main():
 
     passes = [{"kernel": kernels[i], "us": round(1e3 * float(np.median(per_pass[:, i])), 2),
                "bytes": info[i][1]} for i in range(n_pass)]
+    # per-step spread from the event-instrumented replay (sum of the step's pass times; the
+    # value above is the uninstrumented replay)
+    per_step = per_pass.sum(axis=1)
+    step_stats = {"median_ms": float(np.median(per_step)), "mean_ms": float(per_step.mean()),
+                  "std_ms": float(per_step.std(ddof=1)) if len(per_step) > 1 else 0.0,
+                  "steps": int(len(per_step)), "source": "per-pass library events, second replay"}
 
     plan.set_timing(0)
     plan.use_graph(False)
@@ -851,6 +857,7 @@ def main():
                           "batch": 1, "parallelism": f"replicas{world}",
                           "l2": f"inputs larger than L2 ({n * n * 8 / 1e6:.0f} MB field + 2 x {n * n * 4 / 1e6:.0f} MB maps)"},
                "gpu_launches": n_pass * args.steps, "graph_replays": 1, "roofline": roofline, "passes": passes,
+               "step_stats": step_stats,
                "cpu_baseline": cpu,
                "e2e": e2e, "clocks": clk}
         out.update(extras)

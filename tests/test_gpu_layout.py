@@ -149,3 +149,23 @@ def test_alternating_layout_refused_where_unsupported(ctx):
         with pytest.raises(coro.CoroError):
             plan.set_layout(True)
         assert not plan.layout
+
+
+def test_plan_tuning_leaves_caller_buffers_alone(ctx):
+    """The plan-time tuner (kernel candidates, row variants over every pass, layouts) runs on
+    a scratch field with the checkpoint and tap elements left out: buffers those elements
+    write keep their contents until the first execute."""
+    n = 1024
+    w = inputs.RelayWorkload(n=n, npix=n // 2, seed=9)
+    maps_t = [torch.from_numpy(m.astype(np.float32)).cuda() for m in w.psd_maps()]
+    cp = torch.full((1, n, n), 7.0 + 3.0j, dtype=torch.complex64, device="cuda")
+    tap = torch.full((1, n, n), -5.0, dtype=torch.float32, device="cuda")
+    els = relay_elements(w, maps_t)
+    els = els[:3] + [coro.element(coro.EL_CHECKPOINT, plane=2, store=cp),
+                     coro.element(coro.EL_PHASE_GRAD, plane=3, store=tap, scalar=1.0)] + els[3:]
+    plan = relay_plan(ctx, w, maps_t, extra=els)
+    torch.cuda.synchronize()
+    assert bool((cp == (7.0 + 3.0j)).all()) and bool((tap == -5.0).all())
+    x = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
+    plan.execute(x)
+    assert not bool((cp == (7.0 + 3.0j)).any()) and bool(torch.isfinite(tap).all())
