@@ -109,6 +109,7 @@ __device__ __forceinline__ void mixed_stage(const C* __restrict__ src, C* __rest
                                             const C* __restrict__ lin) {
     using T = typename real_of<C>::type;
     const int nb = n / R, step = n / (ns * R);
+    const int lsh = __ffs(L) - 1;                       // L is 1, 2, 4 or 8
     constexpr int H = (R - 1) / 2 + 1;
     T cs[H], sn[H];
     if constexpr (R % 2 == 1) {
@@ -120,7 +121,7 @@ __device__ __forceinline__ void mixed_stage(const C* __restrict__ src, C* __rest
         }
     }
     for (int i = threadIdx.x; i < nb * L; i += blockDim.x) {
-        const int c = i % L, j = i / L, k = j % ns;
+        const int c = i & (L - 1), j = i >> lsh, k = j % ns;
         C u[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) u[r] = src[mpad((j + r * nb) * L + c)];
@@ -137,39 +138,71 @@ __device__ __forceinline__ void mixed_stage(const C* __restrict__ src, C* __rest
 }
 
 // The same for an odd prime radix known only at run time (R <= kMixedMaxRadix); cs / sn
-// (shared) hold cos, sin(2 pi m / R) for m = 0 ... (R-1)/2.
+// (shared) hold cos, sin(2 pi m / R) for m = 0 ... (R-1)/2. Two block-wide steps, so that
+// every thread has work even when the stage has few butterflies: (1) one task per butterfly
+// and pair b = 1 ... (R-1)/2 twiddles u_b and u_{R-b} and leaves s_b = u_b + u_{R-b} and
+// d_b = u_b - u_{R-b} in their places in src; (2) one task per butterfly and output pair
+// (a, R - a) sums them (the pair-sum DFT of odd_dft), a = 0 giving u_0 + sum_b s_b.
 template <typename C, bool INV>
-__device__ void mixed_stage_any(const C* __restrict__ src, C* __restrict__ dst, int n, int ns, int L, int R,
+__device__ void mixed_stage_any(C* __restrict__ src, C* __restrict__ dst, int n, int ns, int L, int R,
                                 const C* __restrict__ lin, const typename real_of<C>::type* cs,
                                 const typename real_of<C>::type* sn) {
     using T = typename real_of<C>::type;
     const int nb = n / R, step = n / (ns * R), H = (R - 1) / 2;
-    for (int i = threadIdx.x; i < nb * L; i += blockDim.x) {
-        const int c = i % L, j = i / L, k = j % ns;
-        C u[kMixedMaxRadix];
-        for (int r = 0; r < R; ++r) {
-            u[r] = src[mpad((j + r * nb) * L + c)];
-            if (ns > 1 && r > 0) u[r] = cmul(u[r], lin_tw<INV>(lin, r * k * step));
+    const int tasks = nb * L, lsh = __ffs(L) - 1;      // L is 1, 2, 4 or 8
+    for (int i = threadIdx.x; i < tasks * H; i += blockDim.x) {
+        const int c = i & (L - 1), jb = i >> lsh, j = jb % nb, bb = jb / nb + 1;
+        const int k = j % ns;
+        const int pb = mpad((j + bb * nb) * L + c), pc = mpad((j + (R - bb) * nb) * L + c);
+        C ub = src[pb], uc = src[pc];
+        if (ns > 1) {
+            ub = cmul(ub, lin_tw<INV>(lin, bb * k * step));
+            uc = cmul(uc, lin_tw<INV>(lin, (R - bb) * k * step));
         }
+        src[pb] = cadd(ub, uc);
+        src[pc] = csub(ub, uc);
+    }
+    __syncthreads();
+    // step (2): group 0 is a = 0; group g >= 1 holds the outputs a = 4 (g - 1) + 1 ... + 4, each
+    // loaded s_b, d_b feeding all four accumulators
+    constexpr int G = 4;
+    const int groups = 1 + (H + G - 1) / G;
+    for (int i = threadIdx.x; i < tasks * groups; i += blockDim.x) {
+        const int c = i & (L - 1), jg = i >> lsh, j = jg % nb, g = jg / nb;
+        const int k = j % ns;
         const int base = (j / ns) * ns * R + k;
-        C o0 = u[0];
-        for (int b = 1; b <= H; ++b) o0 = cadd(o0, cadd(u[b], u[R - b]));
-        dst[mpad(base * L + c)] = o0;
-        for (int a = 1; a <= H; ++a) {
-            C re = u[0], im = mk<C>(0, 0);
-            int m = 0;
-            for (int b = 1; b <= H; ++b) {
-                m += a;
-                if (m >= R) m -= R;                            // m = a b mod R
-                const C sb = cadd(u[b], u[R - b]), db = csub(u[b], u[R - b]);
-                const T cc = m <= H ? cs[m] : cs[R - m];
-                const T sg = m <= H ? sn[m] : -sn[R - m];
-                re = mk<C>(re.x + sb.x * cc, re.y + sb.y * cc);
-                im = mk<C>(im.x + db.x * sg, im.y + db.y * sg);
+        const C u0 = src[mpad(j * L + c)];
+        if (g == 0) {
+            C o0 = u0;
+            for (int bb = 1; bb <= H; ++bb) o0 = cadd(o0, src[mpad((j + bb * nb) * L + c)]);
+            dst[mpad(base * L + c)] = o0;
+            continue;
+        }
+        const int a0 = G * (g - 1) + 1;
+        C re[G], im[G];
+        int m[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) { re[q] = u0; im[q] = mk<C>(0, 0); m[q] = 0; }
+        for (int bb = 1; bb <= H; ++bb) {
+            const C sb = src[mpad((j + bb * nb) * L + c)], db = src[mpad((j + (R - bb) * nb) * L + c)];
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                m[q] += a0 + q;                                // m = a b mod R
+                if (m[q] >= R) m[q] -= R;
+                const bool lo = m[q] <= H;
+                const T cc = cs[lo ? m[q] : R - m[q]];
+                const T sg = lo ? sn[m[q]] : -sn[R - m[q]];
+                re[q] = mk<C>(re[q].x + sb.x * cc, re[q].y + sb.y * cc);
+                im[q] = mk<C>(im[q].x + db.x * sg, im[q].y + db.y * sg);
             }
-            const C mi = INV ? mk<C>(-im.y, im.x) : mk<C>(im.y, -im.x);
-            dst[mpad((base + a * ns) * L + c)] = cadd(re, mi);
-            dst[mpad((base + (R - a) * ns) * L + c)] = csub(re, mi);
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int a = a0 + q;
+            if (a > H) break;
+            const C mi = INV ? mk<C>(-im[q].y, im[q].x) : mk<C>(im[q].y, -im[q].x);
+            dst[mpad((base + a * ns) * L + c)] = cadd(re[q], mi);
+            dst[mpad((base + (R - a) * ns) * L + c)] = csub(re[q], mi);
         }
     }
 }
@@ -244,23 +277,23 @@ template <typename C>
 __global__ void __launch_bounds__(kMixedColThreads)
 col_pass_mixed_kernel(const __grid_constant__ ColArgs<C> a, const __grid_constant__ MixedPlan mp, int L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = mp.n, b = blockIdx.y, col0 = blockIdx.x * L;
+    const int n = mp.n, b = blockIdx.y, col0 = blockIdx.x * L, lsh = __ffs(L) - 1;   // L: 1, 2, 4 or 8
     C* A = reinterpret_cast<C*>(smem_raw);
     C* B = A + mixed_buf<C>(n, L);
     const size_t base = (size_t)b * n * n + col0;
-    for (int i = threadIdx.x; i < n * L; i += blockDim.x) A[mpad(i)] = a.in[base + (size_t)(i / L) * n + i % L];
+    for (int i = threadIdx.x; i < n * L; i += blockDim.x) A[mpad(i)] = a.in[base + (size_t)(i >> lsh) * n + (i & (L - 1))];
     __syncthreads();
     C* cur = A;
     if (a.flags & CF_FWD) cur = mixed_fft<C, false>(A, B, mp, L, a.tw);
     if (a.flags & CF_TABLE) {
         for (int i = threadIdx.x; i < n * L; i += blockDim.x) {
-            const C h = cmul(a.tab_x[(size_t)b * n + col0 + i % L], a.tab_y[(size_t)b * n + i / L]);
+            const C h = cmul(a.tab_x[(size_t)b * n + col0 + (i & (L - 1))], a.tab_y[(size_t)b * n + (i >> lsh)]);
             cur[mpad(i)] = cmul(cur[mpad(i)], h);
         }
         __syncthreads();
     }
     if (a.flags & CF_INV) cur = mixed_fft<C, true>(cur, cur == A ? B : A, mp, L, a.tw);
-    for (int i = threadIdx.x; i < n * L; i += blockDim.x) a.out[base + (size_t)(i / L) * n + i % L] = cur[mpad(i)];
+    for (int i = threadIdx.x; i < n * L; i += blockDim.x) a.out[base + (size_t)(i >> lsh) * n + (i & (L - 1))] = cur[mpad(i)];
 }
 
 // Columns per block: the widest of 8 / 4 / 2 / 1 that divides n and fits in shared memory.
