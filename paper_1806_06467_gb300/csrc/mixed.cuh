@@ -324,16 +324,21 @@ cudaError_t row_launch_mixed(int n, const RowArgs<C>& a, const PassLaunch& l) {
     return cudaGetLastError();
 }
 
+// lines: columns per block (0: the widest that fits, mixed_col_lines). Blocks whose two
+// buffers fit in half the shared-memory budget run 512 threads, so that two share an SM and
+// one's loads and stores overlap the other's stages; larger ones run 1024 threads alone.
 template <typename C>
-cudaError_t col_launch_mixed(int n, const ColArgs<C>& a, const PassLaunch& l) {
+cudaError_t col_launch_mixed(int n, int lines, const ColArgs<C>& a, const PassLaunch& l) {
     MixedPlan mp;
     if (!mixed_plan(n, &mp)) return cudaErrorInvalidValue;
-    const int L = mixed_col_lines<C>(n);
-    if (L == 0) return cudaErrorInvalidValue;
+    const int L = lines > 0 ? lines : mixed_col_lines<C>(n);
+    if (L <= 0 || L > 8 || (L & (L - 1)) || n % L || mixed_smem<C>(n, L) > kMixedMaxSmem) return cudaErrorInvalidValue;
+    const size_t smem = mixed_smem<C>(n, L);
+    const int threads = smem <= kMixedMaxSmem / 2 ? kMixedColThreads / 2 : kMixedColThreads;
     static unsigned done = 0;
     cudaError_t e = ensure_smem(col_pass_mixed_kernel<C>, kMixedMaxSmem, done);
     if (e != cudaSuccess) return e;
-    col_pass_mixed_kernel<C><<<dim3(n / L, l.batch), kMixedColThreads, mixed_smem<C>(n, L), l.stream>>>(a, mp, L);
+    col_pass_mixed_kernel<C><<<dim3(n / L, l.batch), threads, smem, l.stream>>>(a, mp, L);
     return cudaGetLastError();
 }
 

@@ -72,11 +72,12 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
             if (lines == -1) return col_launch_persistent<float2, 4096, 2>(a, l);
             return lines == 2 ? col_launch<float2, 4096, 2>(a, l) : col_launch<float2, 4096, 4>(a, l);
         case 8192: return lines == 1 ? col_launch<float2, 8192, 1>(a, l) : col_launch<float2, 8192, 2>(a, l);
-        default: return col_launch_mixed<float2>(n, a, l);
+        default: return col_launch_mixed<float2>(n, lines, a, l);
     }
 }
 
 int col_lines_default(int n, bool dbl) {
+    if (n & (n - 1)) return 0;                      // mixed radix: its launcher picks the width
     if (dbl) {
         switch (n) {
             case 4096: return 1;
@@ -101,7 +102,13 @@ int col_candidates(int n, int* out) {
         case 4096: out[5] = -4; out[0] = 4; out[1] = 2; out[2] = -1; out[3] = -2; out[4] = -3; return 6;
         case 2048: out[5] = -4; out[0] = 8; out[1] = 4; out[2] = -1; out[3] = -2; out[4] = -3; return 6;
         case 1024: out[5] = -4; out[0] = 16; out[1] = 8; out[2] = -1; out[3] = -2; out[4] = -3; return 6;
-        default: out[0] = 0; return 1;
+        default:                                            // mixed radix: widest fit, and half of it
+            out[0] = 0;
+            if (!mixed_supported<float2>(n)) return 1;
+            out[0] = mixed_col_lines<float2>(n);
+            if (out[0] < 2) return 1;
+            out[1] = out[0] / 2;
+            return 2;
     }
 }
 
@@ -116,7 +123,7 @@ void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persi
     int p = 0, w = 0;
     if (n & (n - 1)) {                                      // mixed-radix passes
         if (persistent) *persistent = 6;
-        if (out_lines) *out_lines = row ? 1 : (dbl ? mixed_col_lines<double2>(n) : mixed_col_lines<float2>(n));
+        if (out_lines) *out_lines = row ? 1 : dbl ? mixed_col_lines<double2>(n) : lines > 0 ? lines : mixed_col_lines<float2>(n);
         return;
     }
     if (variant < 0) variant = row_variant_default(n);

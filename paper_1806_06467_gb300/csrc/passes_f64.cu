@@ -34,7 +34,7 @@ cudaError_t launch_col_pass<double2>(int n, int lines, const ColArgs<double2>& a
         case 1024: return col_launch<double2, 1024, 4>(a, l);
         case 2048: return col_launch<double2, 2048, 2>(a, l);
         case 4096: return col_launch<double2, 4096, 1>(a, l);
-        default: return col_launch_mixed<double2>(n, a, l);
+        default: return col_launch_mixed<double2>(n, 0, a, l);
     }
 }
 

@@ -82,6 +82,18 @@ def test_relay_plan_2800(ctx):
             optics.circle_stop(n, dx, w.field_stop_frac * r)]
     ref = propagation.fresnel_chain(np.ones((n, n), complex), dx, lam, oels, list(w.distances()))
     assert rel_l2(x.cpu().numpy()[0], ref) < 1e-5
+    # both column widths the tuner chooses from: 4 columns per 1024-thread block (alone on its
+    # SM) and 2 per 512-thread block (two per SM)
+    widths = set()
+    for cl in (4, 2):
+        plan.set_pass_kernel(0, cl)
+        widths |= {plan.pass_kernel(i) for i in range(plan.launch_count) if "col_" in plan.pass_kernel(i)}
+        x.fill_(float("nan"))
+        plan.execute(x)
+        assert rel_l2(x.cpu().numpy()[0], ref) < 1e-5, cl
+    assert widths == {"col_pass_mixed<2800,4>", "col_pass_mixed<2800,2>"}
+    with pytest.raises(coro.CoroError):
+        plan.set_pass_kernel(0, 8)
 
 
 def test_direct_hop_mixed_two_wavelengths(ctx):
