@@ -779,6 +779,8 @@ def main():
             pl = plan if sidx == 0 else coro.FresnelPlan(
                 ctx, n=n, batch=1, pixelscale=w.dx, wavelength=w.wavelength_m, distances=list(w.distances()),
                 elements=relay_elements(w, dmaps), init_uniform=True)
+            if sidx:
+                pl.copy_tuning(plan)                       # both slots run the same kernels
             pl.use_graph(True)
             slots.append({"maps": dmaps, "field": fld, "plan": pl,
                           "host_maps": [torch.from_numpy(m).pin_memory() for m in maps_np],

@@ -307,6 +307,10 @@ coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, i
  * (alternating). CORO_ENOTIMPL: the plan has no column pass followed by a row pass at a
  * supported size. */
 coro_status coro_fresnel_plan_set_layout(coro_plan plan, int transposed);
+/* Give dst the kernel choices and layout the tuner made for src (plans of the same dtype, n,
+ * batch and pass sequence, e.g. a second buffer slot of one system): the two then run the
+ * same kernels. CORO_EINVAL when they differ; dst is unchanged then. */
+coro_status coro_fresnel_plan_copy_tuning(coro_plan dst, coro_plan src);
 coro_status coro_fresnel_plan_layout(coro_plan plan, int* transposed);
 /* a10: replay plan execution as one CUDA graph (enable = 1) or launch kernel by kernel (0,
  * the default). With graphs on, the first execute with a given set of device pointers

@@ -120,6 +120,7 @@ _SIGS = {
     "coro_fresnel_plan_set_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.c_int]),
     "coro_fresnel_plan_set_layout": (ct.c_int, [_P, ct.c_int]),
     "coro_fresnel_plan_layout": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
+    "coro_fresnel_plan_copy_tuning": (ct.c_int, [_P, _P]),
     "coro_selftest_wait_timeout": (ct.c_int, [_P, ct.c_int]),
     "coro_plan_set_timing": (ct.c_int, [_P, ct.c_int]),
     "coro_plan_unit_times": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_float)]),
@@ -563,6 +564,10 @@ class FresnelPlan:
         """Natural (False) or alternating (True) plane layout between passes
         (coro_fresnel_plan_set_layout)."""
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_set_layout(self.handle, 1 if transposed else 0))
+
+    def copy_tuning(self, other: "FresnelPlan") -> None:
+        """Run the kernels and layout `other`'s tuner chose (coro_fresnel_plan_copy_tuning)."""
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_copy_tuning(self.handle, other.handle))
 
     @property
     def layout(self) -> bool:

@@ -1426,6 +1426,30 @@ extern "C" coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row
     return set_layout(p, 0);                            // every pass in place with these kernels
 }
 
+extern "C" coro_status coro_fresnel_plan_copy_tuning(coro_plan dst, coro_plan src) {
+    clear_error();
+    if (!dst || !src || dst->kind() != 1 || src->kind() != 1) {
+        set_error("coro_fresnel_plan_copy_tuning: not two Fresnel plans");
+        return CORO_EINVAL;
+    }
+    auto* d = static_cast<FresnelPlan*>(dst);
+    auto* s = static_cast<const FresnelPlan*>(src);
+    bool same = d->dtype == s->dtype && d->n == s->n && d->batch == s->batch && d->ops_nat.size() == s->ops_nat.size();
+    for (size_t i = 0; same && i < d->ops_nat.size(); ++i) same = d->ops_nat[i].row == s->ops_nat[i].row;
+    if (!same) {
+        set_error("coro_fresnel_plan_copy_tuning: plans differ in dtype, size, batch or pass sequence");
+        return CORO_EINVAL;
+    }
+    for (size_t i = 0; i < d->ops_nat.size(); ++i) {
+        d->ops_nat[i].variant = s->ops_nat[i].variant;
+        d->ops_nat[i].lines = s->ops_nat[i].lines;
+    }
+    d->ops = d->ops_nat;
+    coro_status st = set_layout(d, 0);
+    if (st == CORO_OK && s->tbuf) st = set_layout(d, 1);
+    return st;
+}
+
 extern "C" coro_status coro_fresnel_plan_set_layout(coro_plan plan, int transposed) {
     clear_error();
     if (!plan || plan->kind() != 1) { set_error("coro_fresnel_plan_set_layout: not a Fresnel plan"); return CORO_EINVAL; }

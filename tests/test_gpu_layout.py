@@ -169,3 +169,31 @@ def test_plan_tuning_leaves_caller_buffers_alone(ctx):
     x = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
     plan.execute(x)
     assert not bool((cp == (7.0 + 3.0j)).any()) and bool(torch.isfinite(tap).all())
+
+
+def test_copy_tuning(ctx):
+    """A second plan of the same system takes the first one's kernels and layout; plans of
+    another size or pass sequence are refused and left unchanged."""
+    n = 1024
+    w = inputs.RelayWorkload(n=n, npix=n // 2, seed=10)
+    maps_t = [torch.from_numpy(m.astype(np.float32)).cuda() for m in w.psd_maps()]
+    a = relay_plan(ctx, w, maps_t)
+    b = relay_plan(ctx, w, maps_t)
+    a.set_pass_kernel(2, -1)                             # units rows, persistent columns
+    a.set_layout(True)
+    b.copy_tuning(a)
+    assert names(b) == names(a) and b.layout
+    x, y = (torch.empty((1, n, n), dtype=torch.complex64, device="cuda") for _ in range(2))
+    a.execute(x)
+    b.execute(y)
+    assert torch.equal(x, y)
+    a.set_layout(False)
+    b.copy_tuning(a)
+    assert names(b) == names(a) and not b.layout
+    w2 = inputs.RelayWorkload(n=2048, npix=1024, seed=10)
+    maps2 = [torch.from_numpy(m.astype(np.float32)).cuda() for m in w2.psd_maps()]
+    c = relay_plan(ctx, w2, maps2)
+    before = names(c)
+    with pytest.raises(coro.CoroError):
+        c.copy_tuning(a)
+    assert names(c) == before
