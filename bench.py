@@ -688,6 +688,7 @@ def main():
                             distances=list(w.distances()), elements=els, init_uniform=True)
     n_pass = plan.launch_count
     info = [plan.pass_info(i) for i in range(n_pass)]
+    flops = [plan.pass_flops(i) for i in range(n_pass)]
     kernels = [plan.pass_kernel(i) for i in range(n_pass)]
     field = torch.empty((1, n, n), dtype=torch.complex64, device=device)
 
@@ -728,15 +729,28 @@ def main():
     value, t_max = replica_throughput(HOPS * args.steps, total_ms, world, device)
 
     # -------- roofline of the dominant pass kind
-    kinds = {"row": [0.0, 0.0, 0, set()], "col": [0.0, 0.0, 0, set()]}
+    kinds = {"row": [0.0, 0.0, 0, set(), 0.0], "col": [0.0, 0.0, 0, set(), 0.0]}
     for i, (is_row, nbytes) in enumerate(info):
         kk = "row" if is_row else "col"
         kinds[kk][0] += per_pass[:, i].sum()
         kinds[kk][1] += nbytes * args.steps
         kinds[kk][2] += args.steps
         kinds[kk][3].add(kernels[i])
+        kinds[kk][4] += flops[i] * args.steps
+    # the passes' FP32 arithmetic against the CUDA-core peak: SMs x 128 FP32 lanes x 2 flops
+    # (one FMA) x the maximum SM clock
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+
+    def alu(kind):
+        t_k, f_k = kinds[kind][0], kinds[kind][4]
+        return {"achieved": f_k / (t_k / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": f_k / (t_k / 1e3) / 1e12 / alu_peak, "flops_per_launch": f_k / kinds[kind][2],
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz (derived)",
+                "flops": "5 N log2 N per line transform, 1 or 2 transforms per pass; elements not counted"}
     dom = max(kinds, key=lambda k: kinds[k][0])
-    t_dom, b_dom, l_dom, k_dom = kinds[dom]
+    t_dom, b_dom, l_dom, k_dom = kinds[dom][:4]
     k_name = ", ".join(sorted(k_dom))
     peak, peak_src = measured_peaks()
     achieved = b_dom / (t_dom / 1e3) / 1e9
@@ -744,14 +758,15 @@ def main():
                 "traffic": recorded_traffic(k_name) if len(k_dom) == 1 else None, "kernel": k_name,
                 "bytes_per_launch": b_dom / l_dom, "us_per_launch": 1e3 * t_dom / l_dom,
                 "time_share": t_dom / per_pass.sum(), "peak_source": f"{peak_src} hbm_gbs (copy)",
-                "timing": "library CUDA events around each pass, inside a second graph replay of the K steps"}
+                "timing": "library CUDA events around each pass, inside a second graph replay of the K steps",
+                "alu": alu(dom)}
     other = "col" if dom == "row" else "row"
     if kinds[other][2]:
-        t_o, b_o, l_o, k_o = kinds[other]
+        t_o, b_o, l_o, k_o = kinds[other][:4]
         roofline["other_kernel"] = {"kernel": ", ".join(sorted(k_o)), "achieved": b_o / (t_o / 1e3) / 1e9,
                                     "traffic": recorded_traffic(next(iter(k_o))) if len(k_o) == 1 else None,
                                     "frac": b_o / (t_o / 1e3) / 1e9 / peak, "us_per_launch": 1e3 * t_o / l_o,
-                                    "time_share": t_o / per_pass.sum()}
+                                    "time_share": t_o / per_pass.sum(), "alu": alu(other)}
 
     passes = [{"kernel": kernels[i], "us": round(1e3 * float(np.median(per_pass[:, i])), 2),
                "bytes": info[i][1]} for i in range(n_pass)]

@@ -270,6 +270,9 @@ coro_status coro_fresnel_plan_execute_range(coro_plan plan, void* field, int fir
 /* Describe pass i: *is_row (1 = row pass, 0 = column pass) and *bytes, the algorithmic HBM
  * traffic of the launch (field read unless generated, field write, OPD/amplitude maps read). */
 coro_status coro_fresnel_plan_pass_info(coro_plan plan, int i, int* is_row, double* bytes);
+/* *flops: the pass's line transforms at the conventional 5 N log2 N real flops each (N lines
+ * per item, one or two transforms per pass), elements and tables not counted. */
+coro_status coro_fresnel_plan_pass_flops(coro_plan plan, int i, double* flops);
 /* Kernel that pass i launches, as chosen when the plan was built (the complex64 plan times
  * its candidates then unless the environment sets CORO_AUTOTUNE=0). *persistent:
  *   0  one block per group of lines;

@@ -116,6 +116,7 @@ _SIGS = {
     "coro_plan_launch_count": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "coro_fresnel_plan_execute_range": (ct.c_int, [_P, _P, ct.c_int, ct.c_int]),
     "coro_fresnel_plan_pass_info": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]),
+    "coro_fresnel_plan_pass_flops": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_double)]),
     "coro_fresnel_plan_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "coro_fresnel_plan_set_pass_kernel": (ct.c_int, [_P, ct.c_int, ct.c_int]),
     "coro_fresnel_plan_set_layout": (ct.c_int, [_P, ct.c_int]),
@@ -537,6 +538,12 @@ class FresnelPlan:
     def execute_range(self, field, first: int, count: int = 1):
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_execute_range(
             self.handle, ct.c_void_p(field.data_ptr()), first, count))
+
+    def pass_flops(self, i: int) -> float:
+        """FFT arithmetic of pass i (coro_fresnel_plan_pass_flops)."""
+        f = ct.c_double()
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_flops(self.handle, i, ct.byref(f)))
+        return f.value
 
     def pass_info(self, i: int) -> tuple[bool, float]:
         """(is_row_pass, algorithmic HBM bytes) of pass i."""

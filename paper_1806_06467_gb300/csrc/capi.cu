@@ -1369,6 +1369,19 @@ extern "C" coro_status coro_fresnel_plan_execute_range(coro_plan plan, void* fie
     return run_ops_any(p->ctx, p->dtype, p->n, p->batch, sub, field);
 }
 
+extern "C" coro_status coro_fresnel_plan_pass_flops(coro_plan plan, int i, double* flops) {
+    clear_error();
+    if (!plan || plan->kind() != 1 || !flops) { set_error("coro_fresnel_plan_pass_flops: bad argument"); return CORO_EINVAL; }
+    auto* p = static_cast<FresnelPlan*>(plan);
+    if (i < 0 || i >= (int)p->ops.size()) { set_error("coro_fresnel_plan_pass_flops: pass %d of %d", i, (int)p->ops.size()); return CORO_EINVAL; }
+    const Op& op = p->ops[i];
+    const int transforms = op.row ? ((op.row_flags & RF_INV_FIRST) ? 1 : 0) + ((op.row_flags & RF_FWD_AFTER) ? 1 : 0)
+                                  : ((op.col_flags & CF_FWD) ? 1 : 0) + ((op.col_flags & CF_INV) ? 1 : 0);
+    const double n = p->n;
+    *flops = transforms * 5.0 * n * std::log2(n) * n * p->batch;
+    return CORO_OK;
+}
+
 extern "C" coro_status coro_fresnel_plan_pass_info(coro_plan plan, int i, int* is_row, double* bytes) {
     clear_error();
     if (!plan || plan->kind() != 1 || !is_row || !bytes) { set_error("coro_fresnel_plan_pass_info: bad argument"); return CORO_EINVAL; }

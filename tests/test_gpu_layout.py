@@ -197,3 +197,16 @@ def test_copy_tuning(ctx):
     with pytest.raises(coro.CoroError):
         c.copy_tuning(a)
     assert names(c) == before
+
+
+def test_pass_flops(ctx):
+    """FFT arithmetic per pass: two line transforms in every column pass and interior row pass,
+    one in the first (uniform start, forward only) and the last (inverse only) row pass."""
+    n = 1024
+    w = inputs.RelayWorkload(n=n, npix=n // 2, seed=11)
+    maps_t = [torch.from_numpy(m.astype(np.float32)).cuda() for m in w.psd_maps()]
+    plan = relay_plan(ctx, w, maps_t)
+    one = 5.0 * n * np.log2(n) * n
+    f = [plan.pass_flops(i) for i in range(plan.launch_count)]
+    assert f[0] == one and f[-1] == one
+    assert all(x == 2 * one for x in f[1:-1])
