@@ -4,6 +4,8 @@
 // 4 x 4 block of complex outputs at stride 16 (conflict-free shared reads, coalesced stores).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "../../include/coro.h"
 #include "mft_gemm.cuh"
 
@@ -79,13 +81,18 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(const GemmDesc g) {
     }
 }
 
-// FP64 complex GEMM: 64 x 64 output tile, 8-deep k slices, each thread 4 x 4 outputs.
+// FP64 complex GEMM: 64 x 64 output tile, 8-deep k slices, each thread 4 x 4 outputs. With
+// splits > 1 (split K: the MFT's products have few output tiles and a long K, and FP64 FMAs
+// are scarce, so every SM needs blocks) block z = b * splits + s covers k in
+// [s kc, (s + 1) kc) and writes its unscaled partial sum to part[s][b][m][n]; zreduce_kernel
+// adds the partials in split order.
 constexpr int ZBK = 8;
 
-__global__ void __launch_bounds__(256) zgemm_simt_kernel(const ZGemmDesc g) {
+__global__ void __launch_bounds__(256) zgemm_simt_kernel(const ZGemmDesc g, int splits, int kc, double2* part) {
     __shared__ double2 As[ZBK][BM];
     __shared__ double2 Bs[ZBK][BN];
-    const int b = blockIdx.z;
+    const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
+    const int k_lo = sp * kc, k_hi = min(g.K, k_lo + kc);
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const double2* A = g.A + b * g.sA;
@@ -96,7 +103,7 @@ __global__ void __launch_bounds__(256) zgemm_simt_kernel(const ZGemmDesc g) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
 
-    for (int k0 = 0; k0 < g.K; k0 += ZBK) {
+    for (int k0 = k_lo; k0 < k_hi; k0 += ZBK) {
         // 512 samples of each tile, 2 per thread
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -105,13 +112,13 @@ __global__ void __launch_bounds__(256) zgemm_simt_kernel(const ZGemmDesc g) {
             if (g.a_trans) { mm = idx % BM; kk = idx / BM; } else { kk = idx % ZBK; mm = idx / ZBK; }
             const int gm = m0 + mm, gk = k0 + kk;
             double2 v = make_double2(0.0, 0.0);
-            if (gm < g.M && gk < g.K) v = g.a_trans ? A[(size_t)gk * g.lda + gm] : A[(size_t)gm * g.lda + gk];
+            if (gm < g.M && gk < k_hi) v = g.a_trans ? A[(size_t)gk * g.lda + gm] : A[(size_t)gm * g.lda + gk];
             As[kk][mm] = v;
             int nn;
             if (g.b_trans) { kk = idx % ZBK; nn = idx / ZBK; } else { nn = idx % BN; kk = idx / BN; }
             const int gn = n0 + nn, gk2 = k0 + kk;
             double2 w = make_double2(0.0, 0.0);
-            if (gn < g.N && gk2 < g.K) w = g.b_trans ? B[(size_t)gn * g.ldb + gk2] : B[(size_t)gk2 * g.ldb + gn];
+            if (gn < g.N && gk2 < k_hi) w = g.b_trans ? B[(size_t)gn * g.ldb + gk2] : B[(size_t)gk2 * g.ldb + gn];
             Bs[kk][nn] = w;
         }
         __syncthreads();
@@ -134,8 +141,10 @@ __global__ void __launch_bounds__(256) zgemm_simt_kernel(const ZGemmDesc g) {
         }
         __syncthreads();
     }
-    const double s = g.scale_per_item ? g.scale_per_item[b] : g.alpha;
-    double2* C = g.C + b * g.sC;
+    const bool direct = splits == 1;
+    const double s = !direct ? 1.0 : g.scale_per_item ? g.scale_per_item[b] : g.alpha;
+    double2* C = direct ? g.C + b * g.sC : part + ((size_t)sp * gridDim.z / splits + b) * g.M * g.N;
+    const int ldc = direct ? g.ldc : g.N;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int gm = m0 + ty + 16 * i;
@@ -143,8 +152,26 @@ __global__ void __launch_bounds__(256) zgemm_simt_kernel(const ZGemmDesc g) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int gn = n0 + tx + 16 * j;
-            if (gn < g.N) C[(size_t)gm * g.ldc + gn] = make_double2(acc[i][j].x * s, acc[i][j].y * s);
+            if (gn < g.N) C[(size_t)gm * ldc + gn] = make_double2(acc[i][j].x * s, acc[i][j].y * s);
         }
+    }
+}
+
+// C[b][m][n] = scale_b * sum_s part[s][b][m][n], the partials added in split order.
+__global__ void zreduce_kernel(const ZGemmDesc g, int batch, int splits, const double2* __restrict__ part) {
+    const size_t mn = (size_t)g.M * g.N, total = mn * batch;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / mn);
+        const size_t r = i - (size_t)b * mn;
+        const int m = (int)(r / g.N), n = (int)(r - (size_t)m * g.N);
+        double2 acc = part[i];
+        for (int sp = 1; sp < splits; ++sp) {
+            const double2 v = part[(size_t)sp * total + i];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        const double sc = g.scale_per_item ? g.scale_per_item[b] : g.alpha;
+        g.C[b * g.sC + (size_t)m * g.ldc + n] = make_double2(acc.x * sc, acc.y * sc);
     }
 }
 
@@ -152,8 +179,29 @@ __global__ void __launch_bounds__(256) zgemm_simt_kernel(const ZGemmDesc g) {
 
 cudaError_t launch_zgemm(const ZGemmDesc& g, int batch, cudaStream_t stream) {
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch);
-    zgemm_simt_kernel<<<grid, 256, 0, stream>>>(g);
-    return cudaGetLastError();
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // two blocks fit per SM: split K so that the blocks fill those slots (at least 32 of K each)
+    const long long tiles = (long long)grid.x * grid.y * batch, slots = 2LL * sms;
+    int splits = tiles >= slots ? 1 : (int)(slots / tiles);
+    splits = std::max(1, std::min(splits, g.K / 32));
+    const int kc = ((g.K + splits - 1) / splits + ZBK - 1) / ZBK * ZBK;
+    splits = (g.K + kc - 1) / kc;
+    if (splits == 1) {
+        zgemm_simt_kernel<<<grid, 256, 0, stream>>>(g, 1, g.K, nullptr);
+        return cudaGetLastError();
+    }
+    const size_t total = (size_t)g.M * g.N * batch;
+    double2* part = nullptr;
+    if ((e = cudaMallocAsync(&part, total * splits * sizeof(double2), stream)) != cudaSuccess) return e;
+    grid.z = batch * splits;
+    zgemm_simt_kernel<<<grid, 256, 0, stream>>>(g, splits, kc, part);
+    zreduce_kernel<<<(int)std::min<size_t>((total + 255) / 256, 4096), 256, 0, stream>>>(g, batch, splits, part);
+    e = cudaGetLastError();
+    const cudaError_t f = cudaFreeAsync(part, stream);
+    return e != cudaSuccess ? e : f;
 }
 
 cudaError_t launch_cgemm(const GemmDesc& g, int batch, int precision, cudaStream_t stream) {
