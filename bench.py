@@ -863,6 +863,8 @@ def main():
         extras["spc_system"] = spc_system_bench(ctx, device, max(3, args.steps // 2))
         extras["wfc_gradient"] = wfc_bench(ctx, device, max(3, args.steps // 4))
         extras["relay_mixed_radix"] = relay_mixed_bench(ctx, device, max(3, args.steps // 2))
+        # App. B's pupil (npix 1025) padded 4x: N = 4100 = 4 x 5^2 x 41, a radix-41 stage
+        extras["relay_mixed_radix_4100"] = relay_mixed_bench(ctx, device, 3, n=4100, npix=1025)
         extras["coronagraph_fp64"] = coronagraph_fp64(ctx, device)
     if rank == 0 and not args.no_plain:
         extras["plain_gpu"] = plain_gpu(n, maps_np, w, max(3, args.steps // 4), 2, device)
