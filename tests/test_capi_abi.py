@@ -50,6 +50,29 @@ def test_host_side_argument_checks(dll):
     assert dll.coro_plan_destroy(None) == coro.OK
 
 
+def test_plan_entry_points_reject_null_plans(dll):
+    """Every plan query and setter checks its handle on the host and fails with CORO_EINVAL
+    and a message, without touching a device."""
+    from paper_1806_06467_gb300 import coro
+    i, d = ct.c_int(), ct.c_double()
+    calls = [
+        lambda: dll.coro_fresnel_plan_set_layout(None, 1),
+        lambda: dll.coro_fresnel_plan_layout(None, ct.byref(i)),
+        lambda: dll.coro_fresnel_plan_copy_tuning(None, None),
+        lambda: dll.coro_fresnel_plan_pass_flops(None, 0, ct.byref(d)),
+        lambda: dll.coro_fresnel_plan_pass_info(None, 0, ct.byref(i), ct.byref(d)),
+        lambda: dll.coro_fresnel_plan_pass_kernel(None, 0, ct.byref(i), ct.byref(i)),
+        lambda: dll.coro_fresnel_plan_set_pass_kernel(None, 0, 0),
+        lambda: dll.coro_lyot_plan_execute(None, None, None, None, None, None),
+        lambda: dll.coro_lyot_plan_peak(None, None, None),
+        lambda: dll.coro_lyot_plan_gradient(None, None, None, None, None, 0, 0),
+        lambda: dll.coro_wfc_plan_resident(None, ct.byref(i), ct.byref(i)),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == coro.EINVAL, k
+        assert dll.coro_last_error(), k
+
+
 def test_no_device_reports_ecuda(dll):
     import torch
     if torch.cuda.is_available():
