@@ -407,7 +407,8 @@ typedef struct {
                           /* chain item by item on complex128 pupils/fields with FP64 MFTs  */
                           /* (exact to FP64 rounding; execute, execute_n and peak only --    */
                           /* execute_range, gradient and set_pupil_layout return            */
-                          /* CORO_ENOTIMPL; flops reports 0 tensor flops)                    */
+                          /* CORO_ENOTIMPL; flops reports 0 tensor flops; executes are not   */
+                          /* replayed as graphs)                                             */
 } coro_lyot_desc;
 
 coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc* desc, coro_plan* out);
