@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--impl", default="coro", choices=["coro", "reference"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pass-kernels", default=None, metavar="ROW,COL",
+                    help="run the relay on these kernels (coro_fresnel_plan_set_pass_kernel) instead of the "
+                         "tuner's pick, e.g. for a profiler capture, where the tuner times serialised launches")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-coronagraph", action="store_true")
@@ -694,6 +697,9 @@ def main():
     w, maps_np, maps, els = relay_setup(n, seed=rank, device=device)
     plan = coro.FresnelPlan(ctx, n=n, batch=1, pixelscale=w.dx, wavelength=w.wavelength_m,
                             distances=list(w.distances()), elements=els, init_uniform=True)
+    if args.pass_kernels:
+        rv, cl = (int(v) for v in args.pass_kernels.split(","))
+        plan.set_pass_kernel(rv, cl)
     n_pass = plan.launch_count
     info = [plan.pass_info(i) for i in range(n_pass)]
     flops = [plan.pass_flops(i) for i in range(n_pass)]
