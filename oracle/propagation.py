@@ -1,7 +1,8 @@
 """Fresnel and Fraunhofer propagators in FP64 (oracle; test infrastructure only).
 
 * Centred DFT: F[k] = sum_j f[j] exp(-2 pi i (j - N/2)(k - N/2) / N), inverse with 1/N per
-  axis. Written as fftshift(fft(ifftshift(.))) -- a library FFT used as a step.
+  axis, one axis after the other through the textbook radix-2 FFT of ``oracle.fft`` (direct
+  sums on the odd factor of N).
 * Angular spectrum (Sec. 1.1, Lawrence Eqs. 82-89 cited, paraxial transfer function):
   E(z) = IDFT2[ H . DFT2[E] ], H = exp(-i pi lambda z (fx^2 + fy^2)), piston dropped.
 * Direct Fresnel (Sec. 1.1, with the quadratic phase factor of Eq. 2 read as
@@ -16,19 +17,18 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import optics
+from . import fft, optics
 
 
 def centred_dft2(e: np.ndarray) -> np.ndarray:
-    """Centred 2-D DFT over the last two axes (no normalisation)."""
-    ax = (-2, -1)
-    return np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(e, axes=ax), axes=ax), axes=ax)
+    """Centred 2-D DFT over the last two axes (no normalisation): rows, then columns."""
+    return fft.centred_dft(fft.centred_dft(e, -1, -1), -2, -1)
 
 
 def centred_idft2(e: np.ndarray) -> np.ndarray:
-    """Centred 2-D inverse DFT over the last two axes (1/N^2 normalisation)."""
-    ax = (-2, -1)
-    return np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(e, axes=ax), axes=ax), axes=ax)
+    """Centred 2-D inverse DFT over the last two axes (1/N per axis)."""
+    n0, n1 = e.shape[-2], e.shape[-1]
+    return fft.centred_dft(fft.centred_dft(e, -1, +1), -2, +1) / (n0 * n1)
 
 
 def freqs(n: int, dx: float) -> np.ndarray:

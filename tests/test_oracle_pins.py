@@ -327,3 +327,109 @@ def test_aperture_geometry():
     area = a.sum() * dx * dx
     expect = np.pi * (0.25 - 0.15 ** 2) - 4 * 0.01 * (0.5 - 0.15)
     assert abs(area / expect - 1) < 0.02
+
+
+# ----------------------------------------------------------------------------- detector masks and normalisation
+
+def lattice_count(r2: int) -> int:
+    """Gauss circle count #{(i, j) in Z^2 : i^2 + j^2 <= r2}, row by row with integer square roots."""
+    r = math.isqrt(r2)
+    return sum(2 * math.isqrt(r2 - i * i) + 1 for i in range(-r, r + 1))
+
+
+def test_dark_hole_sum_counts_the_annulus():
+    """At 0.25 lambda/D per pixel the 6-20 lambda/D annulus is 24 <= |(i', j')| <= 80 pixels, both
+    bounds inclusive (reading S7): a unit intensity sums to the lattice-point count, and r^2 as
+    the intensity to the integer sum of i'^2 + j'^2 over those points."""
+    m, du = 512, 0.25
+    s = coronagraph.dark_hole_sum(np.ones((m, m)), du, 6.0, 20.0)
+    assert s == lattice_count(80 * 80) - lattice_count(24 * 24 - 1)
+    assert abs(s / (math.pi * (80 ** 2 - 24 ** 2)) - 1) < 1e-3      # the annulus area in pixels
+    k = np.arange(m) - m // 2
+    r2 = (k[None, :] ** 2 + k[:, None] ** 2).astype(float)
+    brute = sum(i * i + j * j for i in range(-80, 81) for j in range(-80, 81)
+                if 576 <= i * i + j * j <= 6400)
+    assert coronagraph.dark_hole_sum(r2, du, 6.0, 20.0) == brute
+
+
+def test_lyot_stop_radius_is_half_frac_of_d():
+    """lyot_frac is a fraction of the pupil DIAMETER's half: at npix = 128 and frac = 0.75 the
+    stop passes |(i', j')| <= 48 pixels."""
+    stop = coronagraph.lyot_stop(160, 128, 0.75)
+    assert stop.sum() == lattice_count(48 * 48)
+    assert stop[80, 80 + 48] == 1 and stop[80, 80 + 49] == 0
+
+
+@pytest.mark.parametrize("lyot_frac,r_px", [(1.0, 32), (0.75, 24)])
+def test_peak_intensity_of_clear_disk(lyot_frac, r_px):
+    """Without the occulter the on-axis detector field is s * (sum of the lit pupil samples), every
+    phase factor being 1 at U = 0, and no pixel can exceed it: peak = (dU/npix * N_lit)^2."""
+    n, npix = 80, 64
+    p = coronagraph.LyotParams(n=n, npix=npix, m_occ=32, du_occ=0.25, spot_radius=2.0,
+                               lyot_frac=lyot_frac, m_det=48, du_det=0.5)
+    e = coronagraph.pupil_field(n, npix, 550e-9, None)
+    n_lit = lattice_count(r_px * r_px)
+    assert abs(coronagraph.peak_intensity(e, p) / (0.5 / npix * n_lit) ** 2 - 1) < 1e-13
+
+
+# ----------------------------------------------------------------------------- Zernike OPD maps
+
+# Noll (1976) Table 1, unit-RMS forms written out (rho = r/R, theta from +x towards +y)
+NOLL_CLOSED = {
+    4: lambda r, t: math.sqrt(3) * (2 * r ** 2 - 1),
+    5: lambda r, t: math.sqrt(6) * r ** 2 * np.sin(2 * t),
+    6: lambda r, t: math.sqrt(6) * r ** 2 * np.cos(2 * t),
+    7: lambda r, t: math.sqrt(8) * (3 * r ** 3 - 2 * r) * np.sin(t),
+    8: lambda r, t: math.sqrt(8) * (3 * r ** 3 - 2 * r) * np.cos(t),
+    11: lambda r, t: math.sqrt(5) * (6 * r ** 4 - 6 * r ** 2 + 1),
+}
+
+
+@pytest.mark.parametrize("j", sorted(NOLL_CLOSED))
+def test_zernike_opd_single_term_closed_form(j):
+    """One coefficient: c Z_j(r/R, theta) inside r <= R (R = 0.37 m on a 1 cm grid, so rho is not
+    a grid ratio), exactly zero outside."""
+    n, dx, radius, c = 96, 0.01, 0.37, 3e-9
+    opd = optics.zernike_opd(n, dx, radius, np.array([c]), j)
+    for (iy, ix) in [(48, 48), (48, 70), (20, 55), (60, 31), (75, 70), (48, 48 + 37)]:
+        x, y = (ix - 48) * dx, (iy - 48) * dx
+        r = math.hypot(x, y)
+        expect = c * NOLL_CLOSED[j](r / radius, math.atan2(y, x)) if r * r <= radius * radius else 0.0
+        assert abs(opd[iy, ix] - expect) < 1e-12 * c, (iy, ix)
+    k = np.arange(n) - 48
+    outside = (k[None, :] ** 2 + k[:, None] ** 2) * dx * dx > radius * radius
+    assert np.all(opd[outside] == 0.0)
+
+
+def test_zernike_opd_composes_consecutive_terms():
+    """Coefficients c_0.. belong to Noll indices j_first, j_first + 1, ...: the map is their sum."""
+    n, dx, radius = 64, 0.02, 0.55
+    cs = np.array([1e-9, -2e-9, 0.5e-9])
+    opd = optics.zernike_opd(n, dx, radius, cs, 5)
+    x, y = optics.grid(n, dx)
+    r, t = np.hypot(x, y) / radius, np.arctan2(y, x)
+    expect = sum(c * NOLL_CLOSED[5 + i](r, t) for i, c in enumerate(cs))
+    expect[r > 1] = 0.0
+    np.testing.assert_allclose(opd, expect, rtol=0, atol=1e-20)
+
+
+def test_focal_mask_spot_count():
+    """The occulting spot covers rho <= 5 lambda/D inclusive: at 0.25 lambda/D per pixel, the
+    lattice points within 20 pixels."""
+    spot = coronagraph.focal_mask(64, 0.25, 5.0)
+    assert spot.sum() == lattice_count(400)
+    assert spot[32, 52] == 1 and spot[32, 53] == 0
+
+
+def test_fresnel_chain_composes_hops():
+    """Transfer functions multiply: bare planes z1 then z2 equal one hop z1 + z2; an element
+    applied at a plane acts on the field that arrives there."""
+    n, dx, lam = 64, 2e-4, 600e-9
+    f = inputs.random_field((n, n), seed=21)
+    two = propagation.fresnel_chain(f, dx, lam, [None, None, None], [0.7, 1.1])
+    one = propagation.angular_spectrum(f, dx, lam, 1.8)
+    np.testing.assert_allclose(two, one, atol=1e-12)
+    a = optics.circular_aperture(n, dx, 20 * dx).astype(complex)
+    chained = propagation.fresnel_chain(f, dx, lam, [None, a, None], [0.7, 1.1])
+    manual = propagation.angular_spectrum(a * propagation.angular_spectrum(f, dx, lam, 0.7), dx, lam, 1.1)
+    np.testing.assert_allclose(chained, manual, atol=1e-12)
