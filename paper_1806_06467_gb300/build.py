@@ -16,7 +16,7 @@ SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcoro.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "passes_f32.cu", "passes_f64.cu", "mft.cu", "cgemm_simt.cu", "tc_gemm.cu", "noalloc.cu", "lyot.cu", "lyot64.cu", "dm.cu", "wfc.cu"]
+SOURCES = ["capi.cu", "passes_f32.cu", "passes_f64.cu", "mft.cu", "cgemm_simt.cu", "tc_gemm.cu", "tcx_gemm.cu", "noalloc.cu", "lyot.cu", "lyot64.cu", "dm.cu", "wfc.cu"]
 
 
 def nvcc() -> str:

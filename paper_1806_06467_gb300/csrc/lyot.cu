@@ -14,12 +14,14 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <memory>
 #include <vector>
 
 #include "capi_common.h"
 #include "tc_gemm.cuh"
+#include "tcx_gemm.cuh"
 
 using namespace coro;
 
@@ -33,6 +35,8 @@ struct Buf {
 struct LyotPlan : coro_plan_s {
     coro_ctx ctx = nullptr;
     bool bf16 = false;
+    bool ext = false;                  // CORO_MFT_EXT: sliced BF16 operands (tcx_gemm.cu)
+    int tile_n = TCX_TILE_N_WIDE;      // CORO_MFT_EXT output tile width (complex columns)
     int batch = 0, n = 0, m_det = 0, m_occ_max = 0;
     double npix = 0;
     std::vector<coro_lyot_item> items;
@@ -52,6 +56,7 @@ struct LyotPlan : coro_plan_s {
     int* keep_lyot = nullptr;          // [batch] Lyot-stop radius^2 (pupil pixels)
     double* dh = nullptr;              // [batch]
     float* peak = nullptr;             // [batch]
+    double* peak64 = nullptr;          // [batch] (CORO_MFT_EXT)
     int device = 0;                    // kept so that destruction never touches the context
     int kind() const override { return 2; }
     int launches() const override { return 7; }
@@ -72,17 +77,43 @@ struct LyotPlan : coro_plan_s {
         if (e != cudaSuccess) { *st = cuda_fail(e, "cudaMemsetAsync"); return nullptr; }
         return p;
     }
-    bool make(TcOperand& op, int nb, int rows, int cols, coro_status* st) {
+    // An operand of the plan's GEMM family; basis = a W-type operand (the MFT bases).
+    bool make(TcOperand& op, int nb, int rows, int cols, coro_status* st, bool basis = false) {
         op.batch = nb;
         op.rows = rows;
         op.cols = cols;
-        op.ld = tc_ld(cols, bf16);
-        op.base = alloc((size_t)4 * nb * rows * op.ld * tc_elem_size(bf16), st);
+        if (ext) {
+            op.ld = tcx_ld(cols);
+            op.base = alloc((size_t)(basis ? TCX_W_PLANES : TCX_X_PLANES) * nb * rows * op.ld * 2, st);
+        } else {
+            op.ld = tc_ld(cols, bf16);
+            op.base = alloc((size_t)4 * nb * rows * op.ld * tc_elem_size(bf16), st);
+        }
         return op.base != nullptr;
     }
+    cudaError_t map(const TcOperand& op, bool basis, CUtensorMap* m) const {
+        if (ext) return basis ? tcx_make_w_map(op, m, tile_n) : tcx_make_x_map(op, m);
+        return tc_make_operand_map(op, bf16, m);
+    }
+    cudaError_t basis(double c, int sign, const TcOperand& dst, int item, int rows, int cols) const {
+        return ext ? tcx_basis_one(c, sign, dst, item, rows, cols, ctx->stream)
+                   : tc_basis_one(bf16, c, sign, dst, item, rows, cols, ctx->stream);
+    }
+    cudaError_t split(const float2* src, long long bstride, int ld, const TcOperand& dst, const int* keep = nullptr) const {
+        return ext ? tcx_split(src, bstride, ld, dst, ctx->stream, keep)
+                   : tc_split(bf16, src, bstride, ld, dst, ctx->stream, keep);
+    }
+    cudaError_t launch(int epi, const CUtensorMap& mx, const CUtensorMap& mw, int mm, int nn, int kk, const TcArgs& a) const {
+        return ext ? tcx_launch(epi, mx, mw, mm, nn, batch, a, ctx->stream, tile_n)
+                   : tc_launch(bf16, epi, mx, mw, mm, nn, kk, batch, a, ctx->stream);
+    }
+    // elements per item of an X-type operand (for the epilogues' batch strides)
+    long long xstride(const TcOperand& op) const { return (long long)(ext ? TCX_X_PLANES : 4) * op.rows * op.ld; }
 };
 
 int clamp_thr(long long v) { return v > 0x3fffffffLL ? 0x3fffffff : (int)v; }
+
+coro_status tune_tile(LyotPlan* p);
 
 }  // namespace
 
@@ -90,8 +121,9 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
     clear_error();
     if (!ctx || !d || !out || !d->items) { set_error("coro_lyot_plan_create: NULL argument"); return CORO_EINVAL; }
     *out = nullptr;
-    if (d->precision != CORO_MFT_3XTF32 && d->precision != CORO_MFT_3XBF16 && d->precision != CORO_MFT_FP64) {
-        set_error("coro_lyot_plan_create: precision must be CORO_MFT_3XTF32, CORO_MFT_3XBF16 or CORO_MFT_FP64");
+    if (d->precision != CORO_MFT_3XTF32 && d->precision != CORO_MFT_3XBF16 && d->precision != CORO_MFT_EXT &&
+        d->precision != CORO_MFT_FP64) {
+        set_error("coro_lyot_plan_create: precision must be CORO_MFT_3XTF32, CORO_MFT_3XBF16, CORO_MFT_EXT or CORO_MFT_FP64");
         return CORO_EINVAL;
     }
     if (d->batch < 1 || d->batch > 65535) { set_error("coro_lyot_plan_create: batch %d", d->batch); return CORO_ESIZE; }
@@ -117,6 +149,7 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
     p->ctx = ctx;
     p->device = ctx->device;
     p->bf16 = d->precision == CORO_MFT_3XBF16;
+    p->ext = d->precision == CORO_MFT_EXT;
     p->batch = d->batch;
     p->n = d->n;
     p->npix = d->npix;
@@ -139,22 +172,22 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
     coro_status st = CORO_OK;
     const int no = (int)occ_id.size(), nd = (int)det_id.size();
     if (!p->make(p->XA, B, n, n, &st) || !p->make(p->Z1, B, m_occ_max, n, &st) || !p->make(p->XB, B, m_occ_max, m_occ_max, &st) ||
-        !p->make(p->Z3, B, n, m_occ_max, &st) || !p->make(p->Z5, B, md, n, &st) || !p->make(p->W1, no, m_occ_max, n, &st) ||
-        !p->make(p->W2, no, n, m_occ_max, &st) || !p->make(p->W3, nd, md, n, &st))
+        !p->make(p->Z3, B, n, m_occ_max, &st) || !p->make(p->Z5, B, md, n, &st) || !p->make(p->W1, no, m_occ_max, n, &st, true) ||
+        !p->make(p->W2, no, n, m_occ_max, &st, true) || !p->make(p->W3, nd, md, n, &st, true))
         return st;
     cudaError_t e = cudaSuccess;
     // A_occ[u][j] = exp(-2 pi i u' j' du/npix), B^T[j][u] = exp(+2 pi i j' u' du/npix), A_det likewise
     for (auto& kv : occ_id) {
         const double c = kv.first.second / d->npix;
         const int m = kv.first.first;
-        if (e == cudaSuccess) e = tc_basis_one(p->bf16, c, -1, p->W1, kv.second, m, n, ctx->stream);
-        if (e == cudaSuccess) e = tc_basis_one(p->bf16, c, +1, p->W2, kv.second, n, m, ctx->stream);
+        if (e == cudaSuccess) e = p->basis(c, -1, p->W1, kv.second, m, n);
+        if (e == cudaSuccess) e = p->basis(c, +1, p->W2, kv.second, n, m);
     }
     for (auto& kv : det_id)
-        if (e == cudaSuccess) e = tc_basis_one(p->bf16, kv.first / d->npix, -1, p->W3, kv.second, md, n, ctx->stream);
+        if (e == cudaSuccess) e = p->basis(kv.first / d->npix, -1, p->W3, kv.second, md, n);
     TcOperand* ops[8] = {&p->XA, &p->Z1, &p->XB, &p->Z3, &p->Z5, &p->W1, &p->W2, &p->W3};
     CUtensorMap* maps[8] = {&p->mXA, &p->mZ1, &p->mXB, &p->mZ3, &p->mZ5, &p->mW1, &p->mW2, &p->mW3};
-    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = tc_make_operand_map(*ops[i], p->bf16, maps[i]);
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = p->map(*ops[i], i >= 5, maps[i]);
     if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_create: bases / tensor maps");
 
     // per-GEMM item tables
@@ -184,6 +217,8 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
         h[6 * B + b] = TcItem{md, n, md, b, di[b], 0, all, 1.0f, 1.0f};
         h[7 * B + b] = TcItem{n, n, md, b, di[b], 0, lyot_thr, s_det, 1.0f};
         h[8 * B + b] = TcItem{n, n, mo, b, oi[b], 0, all, s_occ, 1.0f};
+        for (int g : {1, 3, 8}) h[g * B + b].scale64 = it.du_occ / d->npix;
+        for (int g : {5, 7}) h[g * B + b].scale64 = it.du_det / d->npix;
         // known zeros of the X operands (tc_gemm skips the K slices and tiles they cover):
         // X_B is the spot disk; Z3's columns are X_B's rows, so a band of the spot's width;
         // E_D is the Lyot-stop disk; Z5's columns are E_D's rows, a band of the stop's width
@@ -208,11 +243,16 @@ extern "C" coro_status coro_lyot_plan_create(coro_ctx ctx, const coro_lyot_desc*
     p->keep_lyot = p->dev_items ? (int*)p->alloc(B * sizeof(int), &st) : nullptr;
     p->dh = p->keep_lyot ? (double*)p->alloc(B * sizeof(double), &st) : nullptr;
     p->peak = p->dh ? (float*)p->alloc(B * sizeof(float), &st) : nullptr;
-    if (!p->peak) return st;
+    p->peak64 = p->peak ? (double*)p->alloc(B * sizeof(double), &st) : nullptr;
+    if (!p->peak64) return st;
     e = cudaMemcpyAsync(p->dev_items, p->host_items.data(), p->host_items.size() * sizeof(TcItem), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->keep_lyot, keep.data(), B * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_create");
+    if (p->ext && !(std::getenv("CORO_AUTOTUNE") && std::getenv("CORO_AUTOTUNE")[0] == '0')) {
+        const coro_status ts = tune_tile(p.get());
+        if (ts != CORO_OK) return ts;
+    }
     *out = p.release();
     return CORO_OK;
 }
@@ -225,7 +265,10 @@ cudaError_t upload_det_items(LyotPlan* p, const double* peak_host) {
     cudaStream_t s = p->ctx->stream;
     if (peak_host) {
         std::vector<TcItem> g6(p->host_items.begin() + 5 * B, p->host_items.begin() + 6 * B);
-        for (int b = 0; b < B; ++b) g6[b].inv_peak = (float)(1.0 / peak_host[b]);
+        for (int b = 0; b < B; ++b) {
+            g6[b].inv_peak = (float)(1.0 / peak_host[b]);
+            g6[b].inv_peak64 = 1.0 / peak_host[b];
+        }
         return cudaMemcpyAsync(p->dev_items + 5 * B, g6.data(), B * sizeof(TcItem), cudaMemcpyHostToDevice, s);
     }
     return cudaMemcpyAsync(p->dev_items + 5 * B, p->host_items.data() + 5 * B, B * sizeof(TcItem), cudaMemcpyHostToDevice, s);
@@ -240,13 +283,14 @@ cudaError_t detector_gemms(LyotPlan* p, float* intensity, void* field, bool trac
     a.err = p->ctx->err;
     a.items = p->dev_items + 4 * B;
     a.dst = p->Z5.base;
-    a.dst_bstride = (long long)4 * p->Z5.rows * p->Z5.ld;
+    a.dst_bstride = p->xstride(p->Z5);
     a.dst_rows = p->Z5.rows;
     a.dst_ld = p->Z5.ld;
-    cudaError_t e = tc_launch(p->bf16, TC_EPI_SPLITT, p->mXA, p->mW3, n, md, n, B, a, s);
+    cudaError_t e = p->launch(TC_EPI_SPLITT, p->mXA, p->mW3, n, md, n, a);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p->dh, 0, B * sizeof(double), s);
     if (e == cudaSuccess && track_peak) e = cudaMemsetAsync(p->peak, 0, B * sizeof(float), s);
+    if (e == cudaSuccess && track_peak) e = cudaMemsetAsync(p->peak64, 0, B * sizeof(double), s);
     if (e != cudaSuccess) return e;
     TcArgs b6{};
     b6.err = p->ctx->err;
@@ -261,7 +305,8 @@ cudaError_t detector_gemms(LyotPlan* p, float* intensity, void* field, bool trac
     b6.c64_ld = md;
     b6.dh_acc = p->dh;
     b6.peak = track_peak ? p->peak : nullptr;
-    return tc_launch(p->bf16, TC_EPI_INTENSITY, p->mZ5, p->mW3, md, md, n, B, b6, s);
+    b6.peak64 = track_peak ? p->peak64 : nullptr;
+    return p->launch(TC_EPI_INTENSITY, p->mZ5, p->mW3, md, md, n, b6);
 }
 
 }  // namespace
@@ -286,7 +331,7 @@ cudaError_t run_stages(LyotPlan* p, const void* pupil, float* intensity, void* f
         a.err = p->ctx->err;
         a.items = p->dev_items + gi * B;
         a.dst = dst.base;
-        a.dst_bstride = (long long)4 * dst.rows * dst.ld;
+        a.dst_bstride = p->xstride(dst);
         a.dst_rows = dst.rows;
         a.dst_ld = dst.ld;
         if (epi == TC_EPI_BABINET) {                 // E_A straight from the complex64 pupil
@@ -294,10 +339,10 @@ cudaError_t run_stages(LyotPlan* p, const void* pupil, float* intensity, void* f
             a.src64_bstride = p->pupil_bstride;
             a.src64_ld = p->pupil_ld;
         }
-        e = tc_launch(p->bf16, epi, mx, mw, mm, nn, kk, B, a, s);
+        e = p->launch(epi, mx, mw, mm, nn, kk, a);
         mark(gi + 2);
     };
-    if (first <= 0 && last >= 0) e = tc_split(p->bf16, (const float2*)pupil, p->pupil_bstride, p->pupil_ld, p->XA, s);
+    if (first <= 0 && last >= 0) e = p->split((const float2*)pupil, p->pupil_bstride, p->pupil_ld, p->XA);
     mark(1);
     gemm(0, TC_EPI_SPLITT, p->mXA, p->mW1, p->Z1, n, mo, n);     // G1
     gemm(1, TC_EPI_SPLITT, p->mZ1, p->mW1, p->XB, mo, mo, n);    // G2 (x spot)
@@ -309,6 +354,84 @@ cudaError_t run_stages(LyotPlan* p, const void* pupil, float* intensity, void* f
 }
 
 }  // namespace
+
+namespace {
+
+// Re-encode the basis maps for the plan's tile width (their boxes have tile_n rows).
+cudaError_t remap_bases(LyotPlan* p) {
+    cudaError_t e = p->map(p->W1, true, &p->mW1);
+    if (e == cudaSuccess) e = p->map(p->W2, true, &p->mW2);
+    if (e == cudaSuccess) e = p->map(p->W3, true, &p->mW3);
+    if (e == cudaSuccess && p->grad_ready) e = p->map(p->W4, true, &p->mW4);
+    return e;
+}
+
+// Plan-time choice of the extended GEMM's tile width: the GEMM stages (1-5) of one execute on
+// the plan's own (zero) operands, timed with events for each width; the faster is kept. The
+// GEMMs' cost depends on the geometry only (tile counts, support-aware K ranges), not on the
+// values. Results do not depend on the choice beyond FP32 rounding order.
+coro_status tune_tile(LyotPlan* p) {
+    cudaStream_t s = p->ctx->stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    float best = 1e30f;
+    int best_tile = TCX_TILE_N_WIDE;
+    for (int tile : {TCX_TILE_N_WIDE, TCX_TILE_N_NARROW}) {
+        if (e != cudaSuccess) break;
+        p->tile_n = tile;
+        e = remap_bases(p);
+        if (e == cudaSuccess) e = run_stages(p, nullptr, nullptr, nullptr, 1, 5);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(a, s);
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = run_stages(p, nullptr, nullptr, nullptr, 1, 5);
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && ms < best) { best = ms; best_tile = tile; }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    p->tile_n = best_tile;
+    if (e == cudaSuccess) e = remap_bases(p);
+    return e == cudaSuccess ? CORO_OK : cuda_fail(e, "coro_lyot_plan_create: GEMM tile tuning");
+}
+
+}  // namespace
+
+extern "C" coro_status coro_lyot_plan_gemm_tile(coro_plan plan, int* tile_m, int* tile_n) {
+    clear_error();
+    if (!plan || (plan->kind() != 2 && plan->kind() != 4)) { set_error("coro_lyot_plan_gemm_tile: not a Lyot plan"); return CORO_EINVAL; }
+    int m = 0, n = 0;                                    // FP64 plans: CUDA-core GEMMs, no tensor tile
+    if (plan->kind() == 2) {
+        auto* p = static_cast<LyotPlan*>(plan);
+        m = 128;
+        n = p->ext ? p->tile_n : 128;
+    }
+    if (tile_m) *tile_m = m;
+    if (tile_n) *tile_n = n;
+    return CORO_OK;
+}
+
+extern "C" coro_status coro_lyot_plan_set_gemm_tile(coro_plan plan, int tile_n) {
+    clear_error();
+    if (!plan || plan->kind() != 2) { set_error("coro_lyot_plan_set_gemm_tile: not a tensor-core Lyot plan"); return CORO_EINVAL; }
+    auto* p = static_cast<LyotPlan*>(plan);
+    if (!p->ext) {
+        if (tile_n == 128) return CORO_OK;
+        set_error("coro_lyot_plan_set_gemm_tile: the 3xTF32 / 3xBF16 GEMM has one tile width, 128");
+        return CORO_EINVAL;
+    }
+    if (tile_n != TCX_TILE_N_WIDE && tile_n != TCX_TILE_N_NARROW) {
+        set_error("coro_lyot_plan_set_gemm_tile: tile width %d (CORO_MFT_EXT offers 64 and 32)", tile_n);
+        return CORO_EINVAL;
+    }
+    DeviceGuard g(p->ctx->device);
+    p->graph.reset();                                    // captured launches used the old maps
+    p->tile_n = tile_n;
+    const cudaError_t e = remap_bases(p);
+    return e == cudaSuccess ? CORO_OK : cuda_fail(e, "coro_lyot_plan_set_gemm_tile");
+}
 
 namespace {
 // Items of a split-precision (kind 2) or FP64 (kind 4) Lyot plan.
@@ -405,8 +528,10 @@ extern "C" coro_status coro_lyot_plan_flops(coro_plan plan, double* useful, doub
     const int epi[6] = {TC_EPI_SPLITT, TC_EPI_SPLITT, TC_EPI_SPLITT, TC_EPI_BABINET, TC_EPI_SPLITT, TC_EPI_INTENSITY};
     const int mm[6] = {n, mo, mo, n, n, md}, nn[6] = {mo, mo, n, n, md, md};
     double u = 0, is = 0;
-    for (int g = 0; g < 6; ++g)
-        tc_count_flops(p->bf16, epi[g], p->host_items.data() + (size_t)g * B, B, mm[g], nn[g], &u, &is);
+    for (int g = 0; g < 6; ++g) {
+        if (p->ext) tcx_count_flops(epi[g], p->host_items.data() + (size_t)g * B, B, mm[g], nn[g], &u, &is, p->tile_n);
+        else tc_count_flops(p->bf16, epi[g], p->host_items.data() + (size_t)g * B, B, mm[g], nn[g], &u, &is);
+    }
     if (useful) *useful = u;
     if (issued) *issued = is;
     return CORO_OK;
@@ -421,14 +546,16 @@ extern "C" coro_status coro_lyot_plan_peak(coro_plan plan, const void* pupil, do
     DeviceGuard g(p->ctx->device);
     cudaStream_t s = p->ctx->stream;
     // occulter removed: E_D = E_A . Lyot stop, then the detector MFT
-    cudaError_t e = tc_split(p->bf16, (const float2*)pupil, p->pupil_bstride, p->pupil_ld, p->XA, s, p->keep_lyot);
+    cudaError_t e = p->split((const float2*)pupil, p->pupil_bstride, p->pupil_ld, p->XA, p->keep_lyot);
     if (e == cudaSuccess) e = upload_det_items(p, nullptr);
     if (e == cudaSuccess) e = detector_gemms(p, nullptr, nullptr, true);
     std::vector<float> pk(B);
+    std::vector<double> pk64(B);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pk.data(), p->peak, B * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pk64.data(), p->peak64, B * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_peak");
-    for (int b = 0; b < B; ++b) peak_out[b] = pk[b];
+    for (int b = 0; b < B; ++b) peak_out[b] = p->ext ? pk64[b] : pk[b];
     return CORO_OK;
 }
 
@@ -456,17 +583,17 @@ coro_status prepare_gradient(LyotPlan* p) {
     coro_status st = CORO_OK;
     const int B = p->batch, n = p->n, md = p->m_det;
     const int nd = (int)p->det_bases.size();
-    if (!p->make(p->XS, B, md, md, &st) || !p->make(p->Z4, B, n, md, &st) || !p->make(p->W4, nd, n, md, &st))
+    if (!p->make(p->XS, B, md, md, &st) || !p->make(p->Z4, B, n, md, &st) || !p->make(p->W4, nd, n, md, &st, true))
         return st;
     p->seed = (float2*)p->alloc((size_t)B * md * md * sizeof(float2), &st);
     if (!p->seed) return st;
     cudaError_t e = cudaSuccess;
     // W4[j][u] = exp(+2 pi i j' u' du_det / npix): the detector MFT's conjugate transpose
     for (auto& db : p->det_bases)
-        if (e == cudaSuccess) e = tc_basis_one(p->bf16, db.first / p->npix, +1, p->W4, db.second, n, md, p->ctx->stream);
-    if (e == cudaSuccess) e = tc_make_operand_map(p->XS, p->bf16, &p->mXS);
-    if (e == cudaSuccess) e = tc_make_operand_map(p->Z4, p->bf16, &p->mZ4);
-    if (e == cudaSuccess) e = tc_make_operand_map(p->W4, p->bf16, &p->mW4);
+        if (e == cudaSuccess) e = p->basis(db.first / p->npix, +1, p->W4, db.second, n, md);
+    if (e == cudaSuccess) e = p->map(p->XS, false, &p->mXS);
+    if (e == cudaSuccess) e = p->map(p->Z4, false, &p->mZ4);
+    if (e == cudaSuccess) e = p->map(p->W4, true, &p->mW4);
     if (e != cudaSuccess) return cuda_fail(e, "coro_lyot_plan_gradient: set-up");
     p->grad_ready = true;
     return CORO_OK;
@@ -498,17 +625,17 @@ extern "C" coro_status coro_lyot_plan_gradient(coro_plan plan, const void* pupil
     if (e == cudaSuccess) e = detector_gemms(p, nullptr, nullptr, false, p->seed);
     if (e == cudaSuccess && dh_out) e = cudaMemcpyAsync(dh_out, p->dh, B * sizeof(double), cudaMemcpyDeviceToHost, s);
     // adjoint: G_D = IMFT_det(seed); G_C = Lyot . G_D; G_A = G_C - IMFT_occ(spot . MFT_occ(G_C))
-    if (e == cudaSuccess) e = tc_split(p->bf16, p->seed, (long long)md * md, md, p->XS, s);
+    if (e == cudaSuccess) e = p->split(p->seed, (long long)md * md, md, p->XS);
     auto gemm = [&](int gi, int epi, const CUtensorMap& mx, const CUtensorMap& mw, const TcOperand& dst, int mm, int nn, int kk) {
         if (e != cudaSuccess) return;
         TcArgs a{};
         a.err = p->ctx->err;
         a.items = p->dev_items + gi * B;
         a.dst = dst.base;
-        a.dst_bstride = (long long)4 * dst.rows * dst.ld;
+        a.dst_bstride = p->xstride(dst);
         a.dst_rows = dst.rows;
         a.dst_ld = dst.ld;
-        e = tc_launch(p->bf16, epi, mx, mw, mm, nn, kk, B, a, s);
+        e = p->launch(epi, mx, mw, mm, nn, kk, a);
     };
     gemm(6, TC_EPI_SPLITT, p->mXS, p->mW4, p->Z4, md, n, md);    // H1
     gemm(7, TC_EPI_SPLITT, p->mZ4, p->mW4, p->XA, n, n, md);     // H2 (x Lyot) -> G_C in XA
@@ -516,7 +643,9 @@ extern "C" coro_status coro_lyot_plan_gradient(coro_plan plan, const void* pupil
     gemm(1, TC_EPI_SPLITT, p->mZ1, p->mW1, p->XB, mo, mo, n);    // G2 (x spot)
     gemm(2, TC_EPI_SPLITT, p->mXB, p->mW2, p->Z3, mo, n, mo);    // G3
     gemm(8, TC_EPI_BABINET, p->mZ3, p->mW2, p->XA, n, n, mo);    // G4, no stop -> G_A in XA
-    if (e == cudaSuccess) e = tc_merge(p->bf16, p->XA, (float2*)grad, grad_bstride, grad_ld, s);
+    if (e == cudaSuccess)
+        e = p->ext ? tcx_merge(p->XA, (float2*)grad, grad_bstride, grad_ld, s)
+                   : tc_merge(p->bf16, p->XA, (float2*)grad, grad_bstride, grad_ld, s);
     if (e == cudaSuccess && dh_out) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? CORO_OK : cuda_fail(e, "coro_lyot_plan_gradient");
 }

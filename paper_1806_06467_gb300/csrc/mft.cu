@@ -17,6 +17,7 @@
 #include "fft_engine.cuh"
 #include "mft_gemm.cuh"
 #include "tc_gemm.cuh"
+#include "tcx_gemm.cuh"
 
 using namespace coro;
 
@@ -113,6 +114,71 @@ coro_status mft_tensor_core(coro_ctx ctx, const coro_wavefront* in, int directio
     return CORO_OK;
 }
 
+// Extended-precision tensor-core MFT (CORO_MFT_EXT): the same two GEMMs on sliced BF16
+// operands (tcx_gemm.cu), the bases sliced straight from their FP64 values.
+coro_status mft_ext(coro_ctx ctx, const coro_wavefront* in, int direction, int m, const std::vector<double>& c,
+                    coro_wavefront* out) {
+    coro_status st = CORO_OK;
+    const int batch = in->batch;
+    const int nin = in->n, nout = m;
+    const int ld = tcx_ld(nin);
+    const size_t x_bytes = (size_t)TCX_X_PLANES * batch * nin * ld * 2;
+    const size_t w_bytes = (size_t)TCX_W_PLANES * batch * nout * ld * 2;
+    const size_t z_bytes = (size_t)TCX_X_PLANES * batch * nout * ld * 2;
+    auto align = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
+    unsigned char* work = (unsigned char*)coro::ctx_work(ctx, align(x_bytes) + align(w_bytes) + align(z_bytes), &st);
+    if (!work) return st;
+    TcOperand X{work, batch, nin, nin, ld};
+    TcOperand W{work + align(x_bytes), batch, nout, nin, ld};
+    TcOperand Z{work + align(x_bytes) + align(w_bytes), batch, nout, nin, ld};
+    std::vector<TcItem> it1(batch), it2(batch);
+    for (int b = 0; b < batch; ++b) {
+        it1[b] = TcItem{nin, nout, nin, b, b, 0, 0x7fffffff, 1.0f, 1.0f};
+        it2[b] = TcItem{nout, nout, nin, b, b, 0, 0x7fffffff, (float)c[b], 1.0f};
+        it2[b].scale64 = c[b];
+    }
+    void* i1 = coro::upload_async(ctx, it1.data(), batch * sizeof(TcItem), &st);
+    void* i2 = i1 ? coro::upload_async(ctx, it2.data(), batch * sizeof(TcItem), &st) : nullptr;
+    cudaError_t e = (i1 && i2) ? cudaSuccess : cudaErrorMemoryAllocation;
+    // the first GEMM writes Z's nin valid columns only; its padding up to ld must read as zeros
+    if (e == cudaSuccess) e = cudaMemsetAsync(Z.base, 0, z_bytes, ctx->stream);
+    CUtensorMap mx, mw, mz;
+    if (e == cudaSuccess) e = tcx_split((const float2*)in->data, (long long)nin * nin, nin, X, ctx->stream);
+    for (int b = 0; b < batch && e == cudaSuccess; ++b)
+        e = tcx_basis_one(c[b], direction < 0 ? -1 : 1, W, b, nout, nin, ctx->stream);
+    if (e == cudaSuccess) e = tcx_make_x_map(X, &mx);
+    if (e == cudaSuccess) e = tcx_make_w_map(W, &mw);
+    if (e == cudaSuccess) e = tcx_make_x_map(Z, &mz);
+    if (e == cudaSuccess) {
+        TcArgs a{};
+        a.items = (const TcItem*)i1;
+        a.err = ctx->err;
+        a.dst = Z.base;
+        a.dst_bstride = (long long)TCX_X_PLANES * nout * ld;
+        a.dst_rows = nout;
+        a.dst_ld = ld;
+        e = tcx_launch(TC_EPI_SPLITT, mx, mw, nin, nout, batch, a, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        TcArgs a{};
+        a.items = (const TcItem*)i2;
+        a.err = ctx->err;
+        a.dst = out->data;
+        a.dst_bstride = (long long)nout * nout;
+        a.dst_rows = nout;
+        a.dst_ld = nout;
+        e = tcx_launch(TC_EPI_C64T, mz, mw, nout, nout, batch, a, ctx->stream);
+    }
+    coro::free_async(ctx, i1);
+    coro::free_async(ctx, i2);
+    if (e == cudaErrorNotSupported) {
+        coro::set_error("coro_propagate_mft: tensor maps unavailable (driver entry point missing)");
+        return CORO_ENOTIMPL;
+    }
+    if (e != cudaSuccess) return coro::cuda_fail(e, "extended-precision tensor-core MFT");
+    return CORO_OK;
+}
+
 // CUDA-core MFT: complex64 with FP32 arithmetic or complex128 with FP64 arithmetic.
 template <typename C>
 coro_status mft_cuda_cores(coro_ctx ctx, const coro_wavefront* in, int direction, int m, const std::vector<double>& c,
@@ -194,7 +260,8 @@ extern "C" coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in
     if (in->dtype != out->dtype) { coro::set_error("coro_propagate_mft: in and out dtypes differ"); return CORO_EINVAL; }
     const bool dbl = in->dtype == CORO_C128;
     if (dbl ? precision != CORO_MFT_FP64
-            : (precision != CORO_MFT_FP32 && precision != CORO_MFT_3XTF32 && precision != CORO_MFT_3XBF16)) {
+            : (precision != CORO_MFT_FP32 && precision != CORO_MFT_3XTF32 && precision != CORO_MFT_3XBF16 &&
+                 precision != CORO_MFT_EXT)) {
         coro::set_error("coro_propagate_mft: precision %d does not apply to %s fields", precision,
                         dbl ? "complex128 (use CORO_MFT_FP64)" : "complex64");
         return CORO_EINVAL;
@@ -206,6 +273,7 @@ extern "C" coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in
         c[b] = du[b] / npix;
     }
     coro::DeviceGuard g(ctx->device);
+    if (precision == CORO_MFT_EXT) return mft_ext(ctx, in, direction, m, c, out);
     if (precision == CORO_MFT_3XTF32 || precision == CORO_MFT_3XBF16)
         return mft_tensor_core(ctx, in, direction, m, c, precision == CORO_MFT_3XBF16, out);
     return dbl ? mft_cuda_cores<double2>(ctx, in, direction, m, c, out) : mft_cuda_cores<float2>(ctx, in, direction, m, c, out);

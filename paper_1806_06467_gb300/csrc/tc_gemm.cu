@@ -64,41 +64,6 @@ __device__ __forceinline__ float2 load_split(const void* base, size_t plane, siz
     }
 }
 
-__host__ __device__ inline int isqrt_floor(long long v) {
-    long long w = (long long)sqrt((double)v);
-    while (w * w > v) --w;
-    while ((w + 1) * (w + 1) <= v) ++w;
-    return (int)w;
-}
-
-// Distance from c to the nearest of the integers lo..hi (0 if c lies inside).
-__host__ __device__ inline int dist_to_range(int c, int lo, int hi) { return c < lo ? lo - c : c > hi ? c - hi : 0; }
-
-// K slices [kb0, kb0 + kblocks) a tile (rows m0.., columns n0..) has to run: those that can
-// hold non-zeros of X's known support, none when a masking epilogue zeroes every output of
-// the tile. Shared by the kernel and the host-side flop count.
-__host__ __device__ inline void tile_k_range(const TcItem& it, int m0, int n0, int KE, bool masked, int& kb0,
-                                             int& kblocks) {
-    const int mhi = (m0 + BM < it.M ? m0 + BM : it.M) - 1, nhi = (n0 + BN < it.N ? n0 + BN : it.N) - 1;
-    if (masked && (it.mask_lo > 0 || it.mask_hi < 0x7fffffff)) {
-        const long long dx0 = dist_to_range(it.M / 2, m0, mhi), dy0 = dist_to_range(it.N / 2, n0, nhi);
-        const long long dx1 = (it.M / 2 - m0 > mhi - it.M / 2) ? it.M / 2 - m0 : mhi - it.M / 2;
-        const long long dy1 = (it.N / 2 - n0 > nhi - it.N / 2) ? it.N / 2 - n0 : nhi - it.N / 2;
-        const long long r2min = dx0 * dx0 + dy0 * dy0, r2max = dx1 * dx1 + dy1 * dy1;
-        if (r2min > it.mask_hi || r2max < it.mask_lo) { kb0 = 0; kblocks = 0; return; }
-    }
-    if (it.kr2 < 0) return;
-    const long long dm = dist_to_range(it.M / 2, m0, mhi);
-    const long long rem = (long long)it.kr2 - (long long)it.kdy * dm * dm;
-    if (rem < 0) { kb0 = 0; kblocks = 0; return; }
-    const int w = isqrt_floor(rem);
-    const int klo = it.K / 2 - w < 0 ? 0 : it.K / 2 - w;
-    const int khi = it.K / 2 + w > it.K - 1 ? it.K - 1 : it.K / 2 + w;
-    if (khi < klo) { kb0 = 0; kblocks = 0; return; }
-    kb0 = klo / KE;
-    kblocks = khi / KE - kb0 + 1;
-}
-
 template <bool BF16, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw, const TcArgs a) {
@@ -118,7 +83,7 @@ tc_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int KE = BF16 ? 32 : 16;               // real elements per 64-byte K slice
     int kb0 = 0, kblocks = (it.K + KE - 1) / KE;
-    tile_k_range(it, m0, n0, KE, EPI == TC_EPI_SPLITT || EPI == TC_EPI_BABINET, kb0, kblocks);
+    tile_k_range<BM, BN>(it, m0, n0, KE, EPI == TC_EPI_SPLITT || EPI == TC_EPI_BABINET, kb0, kblocks);
     const int nchunks = (kblocks + kChunk - 1) / kChunk;
 
     if (threadIdx.x == 0) {
@@ -393,6 +358,9 @@ cudaError_t launch_t(const CUtensorMap& mx, const CUtensorMap& mw, int max_m, in
 
 }  // namespace
 
+// The driver's tensor-map encoder, shared with tcx_gemm.cu.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
 void tc_count_flops(bool bf16, int epi, const TcItem* items, int batch, int max_m, int max_n, double* useful,
                     double* issued) {
     const int KE = bf16 ? 32 : 16;
@@ -402,7 +370,7 @@ void tc_count_flops(bool bf16, int epi, const TcItem* items, int batch, int max_
         for (int m0 = 0; m0 < max_m && m0 < it.M; m0 += BM)
             for (int n0 = 0; n0 < max_n && n0 < it.N; n0 += BN) {
                 int kb0 = 0, kblocks = (it.K + KE - 1) / KE;
-                tile_k_range(it, m0, n0, KE, masked, kb0, kblocks);
+                tile_k_range<BM, BN>(it, m0, n0, KE, masked, kb0, kblocks);
                 if (kblocks <= 0) continue;
                 const int rows = (m0 + BM < it.M ? BM : it.M - m0), cols = (n0 + BN < it.N ? BN : it.N - n0);
                 int klo = 0, khi = it.K - 1;                  // elements inside the support

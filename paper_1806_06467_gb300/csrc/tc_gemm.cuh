@@ -18,6 +18,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 namespace coro {
 
 enum TcEpi : int {
@@ -38,6 +40,9 @@ struct TcItem {
     // a disk, 0: a band of columns); kr2 < 0: no known zeros. Each tile then runs only the K
     // slices that can hold non-zeros (none if its rows hold none); the result is unchanged.
     int kr2 = -1, kdy = 0;
+    // The extended-precision GEMM (tcx_gemm.cu) scales and normalises in FP64-class arithmetic
+    // (two-float products): its scale and 1/peak are taken from these, not from the floats.
+    double scale64 = 1.0, inv_peak64 = 1.0;
 };
 
 struct TcArgs {
@@ -55,7 +60,45 @@ struct TcArgs {
     const float2* src64;             // Babinet epilogue: E_A read from this complex64 array
     long long src64_bstride;         //   [b][rows][src64_ld] (NULL: from the split planes in dst)
     int src64_ld;
+    double* peak64;                  // extended-precision intensity epilogue: running max [b] (or NULL)
 };
+
+__host__ __device__ inline int isqrt_floor(long long v) {
+    long long w = (long long)sqrt((double)v);
+    while (w * w > v) --w;
+    while ((w + 1) * (w + 1) <= v) ++w;
+    return (int)w;
+}
+
+// Distance from c to the nearest of the integers lo..hi (0 if c lies inside).
+__host__ __device__ inline int dist_to_range(int c, int lo, int hi) { return c < lo ? lo - c : c > hi ? c - hi : 0; }
+
+// K slices of KE elements [kb0, kb0 + kblocks) a BM x BN tile (rows m0.., columns n0..) has to run: those that can
+// hold non-zeros of X's known support, none when a masking epilogue zeroes every output of
+// the tile. Shared by the kernel and the host-side flop count.
+template <int BM, int BN>
+__host__ __device__ inline void tile_k_range(const TcItem& it, int m0, int n0, int KE, bool masked, int& kb0,
+                                             int& kblocks) {
+    const int mhi = (m0 + BM < it.M ? m0 + BM : it.M) - 1, nhi = (n0 + BN < it.N ? n0 + BN : it.N) - 1;
+    if (masked && (it.mask_lo > 0 || it.mask_hi < 0x7fffffff)) {
+        const long long dx0 = dist_to_range(it.M / 2, m0, mhi), dy0 = dist_to_range(it.N / 2, n0, nhi);
+        const long long dx1 = (it.M / 2 - m0 > mhi - it.M / 2) ? it.M / 2 - m0 : mhi - it.M / 2;
+        const long long dy1 = (it.N / 2 - n0 > nhi - it.N / 2) ? it.N / 2 - n0 : nhi - it.N / 2;
+        const long long r2min = dx0 * dx0 + dy0 * dy0, r2max = dx1 * dx1 + dy1 * dy1;
+        if (r2min > it.mask_hi || r2max < it.mask_lo) { kb0 = 0; kblocks = 0; return; }
+    }
+    if (it.kr2 < 0) return;
+    const long long dm = dist_to_range(it.M / 2, m0, mhi);
+    const long long rem = (long long)it.kr2 - (long long)it.kdy * dm * dm;
+    if (rem < 0) { kb0 = 0; kblocks = 0; return; }
+    const int w = isqrt_floor(rem);
+    const int klo = it.K / 2 - w < 0 ? 0 : it.K / 2 - w;
+    const int khi = it.K / 2 + w > it.K - 1 ? it.K - 1 : it.K / 2 + w;
+    if (khi < klo) { kb0 = 0; kblocks = 0; return; }
+    kb0 = klo / KE;
+    kblocks = khi / KE - kb0 + 1;
+}
+
 
 // Host side (tc_gemm.cu).
 struct TcOperand {                   // a planar split operand in global memory
