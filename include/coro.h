@@ -288,13 +288,15 @@ coro_status coro_fresnel_plan_pass_flops(coro_plan plan, int i, double* flops);
  * be NULL. Plain host query; no device work. */
 coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent, int* lines);
 /* (*persistent 6: mixed-radix kernels for n not a power of two; 7: the packed-pair kernels of
- * the alternating layout, below.) */
+ * the alternating layout, below; 8: quad kernel, four-column strips (whole 32-byte sectors)
+ * as two packed pairs, streamed by TMA in quarter strips, exchanges in swizzled shared
+ * memory of exactly N slots per pair.) */
 /* Override the tuned kernel choice of every pass of a complex64 plan.
  *   row_variant: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row
  *                pairs (2 and 3: N = 1024 ... 4096).
  *   col_lines:   columns per block (a width the plan's N supports), -1 persistent TMA,
- *                -2 unit-pipelined, -3 packed column pairs, -4 wide (-2 to -4: N = 1024 ...
- *                4096), 0 default.
+ *                -2 unit-pipelined, -3 packed column pairs, -4 wide, -7 quad (-2 to -7:
+ *                N = 1024 ... 4096), 0 default.
  * Values the plan's N does not offer are rejected with CORO_EINVAL and nothing changes.
  * Every choice gives the same result up to FP32 rounding order (used to test each kernel). */
 coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, int col_lines);
@@ -343,7 +345,7 @@ coro_status coro_plan_destroy(coro_plan plan);
  *     X_j = (j - n/2)/npix (units of D), U_u = (u - m/2) du (units of lambda/D), s = du/npix.
  * direction +1 (focal plane -> pupil): input pitch du (lambda/D), output pitch 1/npix (D),
  *     exponent +2 pi i, same s.
- * in: [batch][n_in][n_in]; out: [batch][m][m], both C64 (precisions FP32 / 3XTF32 / 3XBF16) or
+ * in: [batch][n_in][n_in]; out: [batch][m][m], both C64 (precisions FP32 / 3XTF32 / 3XBF16 / EXT) or
  * both C128 (precision FP64). du: host [batch] (lambda/D per pixel of the focal-plane side).
  * npix: pupil pixels across D. precision: coro_mft_prec.
  * Work buffers are taken from the context (allocated on first use, grown as needed).
@@ -352,7 +354,12 @@ typedef enum {
     CORO_MFT_FP32 = 0,    /* FP32 CUDA-core complex GEMM                                     */
     CORO_MFT_3XTF32 = 1,  /* split TF32 tensor-core GEMM (hi*hi + hi*lo + lo*hi), FP32 acc   */
     CORO_MFT_3XBF16 = 2,  /* split BF16 tensor-core GEMM, FP32 accumulate                    */
-    CORO_MFT_FP64 = 3     /* complex128 fields, FP64 CUDA-core GEMM (reference precision)    */
+    CORO_MFT_FP64 = 3,    /* complex128 fields, FP64 CUDA-core GEMM (reference precision)    */
+    CORO_MFT_EXT = 4      /* extended precision on the BF16 tensor cores: each operand value  */
+                          /* as four 8-bit slices of a power-of-two scale shared by 32       */
+                          /* consecutive K elements (32 bits), ten slice products summed     */
+                          /* exactly per 32-element group, two-float accumulation across     */
+                          /* groups and in the epilogues; complex64 in and out               */
 } coro_mft_prec;
 
 coro_status coro_propagate_mft(coro_ctx ctx, const coro_wavefront* in, double npix, int direction,
@@ -403,7 +410,8 @@ typedef struct {
     double lyot_frac;     /* Lyot stop radius / pupil radius                                 */
     int m_det;            /* detector samples per axis                                       */
     const coro_lyot_item* items;  /* host [batch], copied                                    */
-    int precision;        /* CORO_MFT_3XTF32 or CORO_MFT_3XBF16; or CORO_MFT_FP64: the same  */
+    int precision;        /* CORO_MFT_3XTF32, CORO_MFT_3XBF16 or CORO_MFT_EXT (complex64     */
+                          /* pupils; EXT keeps the peak and 1/peak in FP64); or CORO_MFT_FP64: the same  */
                           /* chain item by item on complex128 pupils/fields with FP64 MFTs  */
                           /* (exact to FP64 rounding; execute, execute_n and peak only --    */
                           /* execute_range, gradient and set_pupil_layout return            */
@@ -436,6 +444,15 @@ coro_status coro_lyot_plan_execute_range(coro_plan plan, const void* pupil, cons
  * only the K ranges and tiles those leave non-zero); *issued = the same over every 128 x 128
  * tile and K slice the kernels run (padding included). Either pointer may be NULL. Host only. */
 coro_status coro_lyot_plan_flops(coro_plan plan, double* useful, double* issued);
+/* Tensor-core GEMM output tile of the plan (rows x complex columns): 128 x 128 for 3XTF32 /
+ * 3XBF16; 128 x 64 or 128 x 32 for EXT, chosen when the plan is created by timing the plan's
+ * GEMM stages at both widths (unless the environment sets CORO_AUTOTUNE=0, which keeps 64);
+ * 0 x 0 for FP64 plans (CUDA-core GEMMs). Either pointer may be NULL. Host query. */
+coro_status coro_lyot_plan_gemm_tile(coro_plan plan, int* tile_m, int* tile_n);
+/* Override the tile width: 64 or 32 for EXT plans, 128 (the only one) for 3XTF32 / 3XBF16;
+ * other values return CORO_EINVAL and change nothing. Results agree across widths to FP32
+ * rounding order. Drops a captured graph. */
+coro_status coro_lyot_plan_set_gemm_tile(coro_plan plan, int tile_n);
 
 /* Pupil argument layout for execute / peak / gradient: item b, row i, column j of E_A at
  * pupil[b * bstride + i * ld + j] (default ld = n, bstride = n * n), so the pupil can be the
@@ -473,7 +490,7 @@ typedef struct {
     double lyot_frac;
     int m_det;
     const coro_lyot_item* items;  /* host [batch], one Lyot item per wavelength            */
-    int precision;                /* CORO_MFT_3XTF32 or CORO_MFT_3XBF16                    */
+    int precision;                /* CORO_MFT_3XTF32, CORO_MFT_3XBF16 or CORO_MFT_EXT      */
     int max_resident;             /* wavelengths held in HBM at once (3 x 8 n_fresnel^2    */
                                   /* bytes each, 5 x where the Fresnel plans may take the  */
                                   /* alternating layout: n_fresnel 1024 ... 4096); 0 = as  */
@@ -511,10 +528,13 @@ coro_status coro_darkhole_sum(coro_ctx ctx, const coro_wavefront* wf, const doub
  * to CORO_NOALLOC_MAX_BATCH items, 32 KiB) is one fixed device array inside the library,
  * held by every GPU that loads it until the process exits. No cudaMalloc/cudaFree or other
  * allocating routine is called.
- *   - Runs on the calling thread's current device and on `stream` (a cudaStream_t, NULL =
- *     legacy default stream); synchronises that stream to return the host values.
+ *   - Runs on the calling thread's current device and on `stream` (a cudaStream_t of that
+ *     device, NULL = legacy default stream); synchronises that stream to return the host
+ *     values. A field in another device's memory is rejected with CORO_EINVAL.
  *   - The first call on a device looks up the array's device address (once per device, with
- *     that device current); make that first call before any stream capture.
+ *     that device current) and keeps it for the life of the process; make that first call
+ *     before any stream capture. Resetting the device (cudaDeviceReset, or tearing down its
+ *     primary context) after that first call is not supported.
  *   - Every call shares the one array: calls that overlap on the GPU (other threads, other
  *     streams) race and must be serialised by the caller. Each call clears the accumulators
  *     it uses before the reduction.

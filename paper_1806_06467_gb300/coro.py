@@ -24,7 +24,7 @@ EL_APERTURE, EL_CIRCLE, EL_LENS, EL_OPD_MAP, EL_ZERNIKE, EL_SINE, EL_SCALAR, EL_
 ELF_OPAQUE_INSIDE, ELF_MAP_BATCHED = 1, 2
 FRESNEL_AS, FRESNEL_DIRECT = 0, 1
 PLAN_INIT_UNIFORM = 1
-MFT_FP32, MFT_3XTF32, MFT_3XBF16, MFT_FP64 = 0, 1, 2, 3
+MFT_FP32, MFT_3XTF32, MFT_3XBF16, MFT_FP64, MFT_EXT = 0, 1, 2, 3, 4
 
 
 class CoroError(RuntimeError):
@@ -97,6 +97,8 @@ _SIGS = {
     "coro_lyot_plan_peak": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double)]),
     "coro_lyot_plan_execute_range": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), _P, _P, ct.c_int, ct.c_int]),
     "coro_lyot_plan_flops": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
+    "coro_lyot_plan_gemm_tile": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "coro_lyot_plan_set_gemm_tile": (ct.c_int, [_P, ct.c_int]),
     "coro_version": (ct.c_int, []),
     "coro_last_error": (ct.c_char_p, []),
     "coro_ctx_create": (ct.c_int, [ct.c_int, _P, ct.POINTER(_P)]),
@@ -297,7 +299,7 @@ def wavefront_axpy(ctx: Context, alpha: float, x, y):
 
 def propagate_mft(ctx: Context, field, npix: float, direction: int, m: int, du, precision: int | None = None,
                   out=None):
-    """precision: MFT_FP32 / MFT_3XTF32 / MFT_3XBF16 for complex64 fields, MFT_FP64 for complex128
+    """precision: MFT_FP32 / MFT_3XTF32 / MFT_3XBF16 / MFT_EXT for complex64 fields, MFT_FP64 for complex128
     (the default follows the field's dtype: FP32 CUDA cores or FP64)."""
     import torch
     if precision is None:
@@ -335,19 +337,21 @@ def darkhole_sum(ctx: Context, field, du, r_in: float, r_out: float, norm=None) 
 
 def darkhole_sum_noalloc(field, du, r_in: float, r_out: float, norm=None, stream=None) -> np.ndarray:
     """coro_darkhole_sum_noalloc: same sums as darkhole_sum, with no device allocation (for
-    callers that must not allocate while they run). Uses the current device and torch's current
-    stream unless one is given; calls that overlap on the GPU race (one shared scratch array)."""
+    callers that must not allocate while they run). Runs with the field's device current, on
+    torch's current stream of that device unless one is given; calls that overlap on the GPU
+    race (one shared scratch array)."""
     import torch
     lib = Library.get()
     w = WF(field)
     b = w.s.batch
     du_arr = _dbl(np.broadcast_to(np.asarray(du, float), (b,)))
     nrm = None if norm is None else _dbl(np.broadcast_to(np.asarray(norm, float), (b,)))
-    if stream is None:
-        stream = torch.cuda.current_stream(field.device)
     out = (ct.c_double * b)()
-    lib.check(lib.coro_darkhole_sum_noalloc(ct.byref(w.s), du_arr, r_in, r_out, nrm,
-                                            ct.c_void_p(stream.cuda_stream), out))
+    with torch.cuda.device(field.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(field.device)
+        lib.check(lib.coro_darkhole_sum_noalloc(ct.byref(w.s), du_arr, r_in, r_out, nrm,
+                                                ct.c_void_p(stream.cuda_stream), out))
     return np.array(out[:])
 
 
@@ -438,6 +442,16 @@ class LyotPlan:
             self.handle, ct.c_void_p(pupil.data_ptr()), pk,
             None if intensity is None else ct.c_void_p(intensity.data_ptr()),
             None if field is None else ct.c_void_p(field.data_ptr()), first, count))
+
+    def gemm_tile(self) -> tuple[int, int]:
+        """(rows, complex columns) of the tensor-core GEMM tile the plan runs."""
+        m, n = ct.c_int(), ct.c_int()
+        self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_gemm_tile(self.handle, ct.byref(m), ct.byref(n)))
+        return m.value, n.value
+
+    def set_gemm_tile(self, tile_n: int) -> None:
+        """Override the tuned tile width (EXT: 64 or 32)."""
+        self.ctx.lib.check(self.ctx.lib.coro_lyot_plan_set_gemm_tile(self.handle, tile_n))
 
     def flops(self) -> tuple[float, float]:
         """(useful, issued) tensor flops of one execute (coro_lyot_plan_flops)."""
@@ -557,14 +571,14 @@ class FresnelPlan:
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_kernel(self.handle, i, ct.byref(p), ct.byref(w)))
         row, _ = self.pass_info(i)
         kind = "row_pass" if row else "col_pass"
-        name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide", "", "_mixed", "_pair_t")[p.value]
+        name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide", "", "_mixed", "_pair_t", "_quad")[p.value]
         return f"{name}<{self.n}>" if row else f"{name}<{self.n},{w.value}>"
 
     def set_pass_kernel(self, row_variant: int, col_lines: int) -> None:
         """Override the tuned kernels (row: 0 persistent, 1 per-group, 2 units, 3 packed row
         pairs; column:
         lines per block, -1 persistent TMA, -2 units, -3 packed column pairs, -4 wide
-        four-column groups, 0 default)."""
+        four-column groups, -7 quad four-column strips, 0 default)."""
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_set_pass_kernel(self.handle, row_variant, col_lines))
 
     def set_layout(self, transposed: bool) -> None:

@@ -90,6 +90,20 @@ extern "C" coro_status coro_darkhole_sum_noalloc(const coro_wavefront* wf, const
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return coro::cuda_fail(e, "coro_darkhole_sum_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= 64) { coro::set_error("coro_darkhole_sum_noalloc: device %d out of range", dev); return CORO_EINVAL; }
+    {
+        // the kernel runs on the current device with that device's scratch: the field must live there
+        cudaPointerAttributes pa{};
+        e = cudaPointerGetAttributes(&pa, wf->data);
+        if (e != cudaSuccess) return coro::cuda_fail(e, "coro_darkhole_sum_noalloc: cudaPointerGetAttributes");
+        if (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered) {
+            coro::set_error("coro_darkhole_sum_noalloc: the field is not in device memory");
+            return CORO_EINVAL;
+        }
+        if (pa.type == cudaMemoryTypeDevice && pa.device != dev) {
+            coro::set_error("coro_darkhole_sum_noalloc: the field is on device %d but device %d is current", pa.device, dev);
+            return CORO_EINVAL;
+        }
+    }
     NoallocItem* ptr = nullptr;
     {
         // set-up, once per device, with that device current: the host-side name g_scratch
