@@ -154,15 +154,23 @@ __device__ __forceinline__ void load_tw(const float2* p, u64& wr, u64& wi) {
     wi = pack(w.y, w.y);
 }
 
+// Shared-memory slot of line position p. Default: pad16 (N + N/16 slots). SWZ: exactly N slots,
+// the 16-byte slot's index within its group of 8 XORed with bits 4-6 of p. Every access pattern
+// of the passes below (16 consecutive positions per thread, stride-16 positions per thread,
+// t + s N/16) then puts any 8 consecutive threads of a warp on 8 different 16-byte bank
+// groups, the same conflict-free property the padding gives, without the 1/16 extra space.
+template <bool SWZ> __device__ __forceinline__ int xslot(int p) { return SWZ ? (p ^ ((p >> 4) & 7)) : pad16(p); }
+
 // One Stockham pass with span NS over a line pair (see line_fft_pass in fft_engine.cuh).
 // HALF: the exchange goes through a buffer of N/2 (padded) entries in two rounds. Every pass
 // but the last has R = 16, and the 16 positions a thread writes lie in one block of 16 NS
 // positions, inside the first half of the line exactly when t < N/32; the positions a thread
 // reads back, t + s N/16, lie in the first half exactly when s < 8. So round one lets the
 // threads t < N/32 write and everyone read slots 0..7, round two the others and slots 8..15.
-template <int N, bool INV, int NS, bool HALF, typename Sync>
+template <int N, bool INV, int NS, bool HALF, typename Sync, bool SWZ = false>
 __device__ __forceinline__ void line_fft_pass2(CP (&v)[16], CP* buf, int t, const float2* __restrict__ tw,
                                                const Sync& sync) {
+    static_assert(!(SWZ && HALF), "the swizzled layout has no half-size form");
     constexpr int TPL = N / 16;
     constexpr int REM = N / NS;
     constexpr int R = REM >= 16 ? 16 : REM;
@@ -206,7 +214,10 @@ __device__ __forceinline__ void line_fft_pass2(CP (&v)[16], CP* buf, int t, cons
         // positions base + r NS (minus `shift`); for NS a multiple of 16, or NS = 1, the
         // padded addresses advance by a compile-time stride
         auto write = [&](int shift) {
-            if constexpr (NS % 16 == 0 || NS == 1) {
+            if constexpr (SWZ) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) buf[xslot<true>(base - shift + r * NS)] = v[r];
+            } else if constexpr (NS % 16 == 0 || NS == 1) {
                 constexpr int PS = NS == 1 ? 1 : NS + NS / 16;
                 CP* p = buf + pad16(base - shift);
 #pragma unroll
@@ -217,7 +228,15 @@ __device__ __forceinline__ void line_fft_pass2(CP (&v)[16], CP* buf, int t, cons
             }
         };
         auto read = [&](CP (&dst)[16], int s0, int s1, int shift) {
-            if constexpr (TPL % 16 == 0) {
+            if constexpr (SWZ && TPL % 128 == 0) {
+                // t + s TPL: the multiple of TPL leaves bits 4-6 alone, so the slots advance by TPL
+                const CP* p = buf + xslot<true>(t + s0 * TPL - shift);
+#pragma unroll
+                for (int s = s0; s < s1; ++s) dst[s] = p[(s - s0) * TPL];
+            } else if constexpr (SWZ) {
+#pragma unroll
+                for (int s = s0; s < s1; ++s) dst[s] = buf[xslot<true>(t + s * TPL - shift)];
+            } else if constexpr (TPL % 16 == 0) {
                 const CP* p = buf + pad16(t + s0 * TPL - shift);
 #pragma unroll
                 for (int s = s0; s < s1; ++s) dst[s] = p[(s - s0) * (TPL + TPL / 16)];
@@ -245,16 +264,16 @@ __device__ __forceinline__ void line_fft_pass2(CP (&v)[16], CP* buf, int t, cons
 #pragma unroll
             for (int s = 0; s < 16; ++s) v[s] = w[s];
         }
-        line_fft_pass2<N, INV, NS * 16, HALF>(v, buf, t, tw, sync);
+        line_fft_pass2<N, INV, NS * 16, HALF, Sync, SWZ>(v, buf, t, tw, sync);
     }
 }
 
 // Full N-point DFT of a line pair held by the TPL threads that share `sync`. buf holds
-// N + N/16 padded entries, or N/2 + N/32 with HALF.
-template <int N, bool INV, bool HALF = false, typename Sync>
+// N + N/16 padded entries, N/2 + N/32 with HALF, or exactly N with SWZ.
+template <int N, bool INV, bool HALF = false, typename Sync, bool SWZ = false>
 __device__ __forceinline__ void line_fft2(CP (&v)[16], CP* buf, int t, const float2* __restrict__ tw,
                                           const Sync& sync) {
-    line_fft_pass2<N, INV, 1, HALF>(v, buf, t, tw, sync);
+    line_fft_pass2<N, INV, 1, HALF, Sync, SWZ>(v, buf, t, tw, sync);
 }
 
 }  // namespace pk

@@ -1034,6 +1034,124 @@ col_pass_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_con
     if (leader) tc::bulk_wait<0>();
 }
 
+// Quad column pass: four adjacent columns per strip, so that every row segment the strip reads
+// or writes is one whole 32-byte sector (two-column strips stream at about half the copy
+// bandwidth of four-column ones). Two units of N/16 threads, unit u transforming the packed
+// column pair (2u, 2u + 1) of the strip (fft_pair.cuh), both in one block that owns the SM.
+// Room: the exchanges use the swizzled layout of exactly N pair slots (64 KB per unit at
+// 4096), and the strip arrives by TMA in quarters (4 columns x N/4 rows, 32 KB at 4096)
+// through three staging slots: 2 x 64 + 3 x 32 = 224 KB. A unit pulls its rows of each
+// quarter into registers as the quarter lands (rows t + s N/16, s = 4q .. 4q + 3), the block
+// releases the slot and the next quarters (of this strip, then the next) load while the
+// transforms run. Results go out as 4-column TMA boxes from the two regions, read as one
+// [N][4] array once both units have left their last exchange.
+template <int N> struct QColCfg {
+    static constexpr int TPL = LineGeom<N>::TPL;
+    static constexpr int THREADS = 2 * TPL;
+    static constexpr int QROWS = N / 4;                // rows per quarter strip
+    static constexpr int SLOTS = 3;
+    static constexpr int SLOT = 4 * QROWS;             // float2 per staging slot
+    static constexpr int REGION = 2 * N;               // float2: N pair slots of 16 bytes
+    static constexpr int QBOXES = QROWS / 256;         // TMA boxes (4 x 256) per quarter
+    static constexpr int OBOXES = N / 256;
+    static_assert(QROWS % 256 == 0, "quarter strips of whole 256-row boxes");
+    static constexpr size_t smem() { return ((size_t)SLOTS * SLOT + 2 * (size_t)REGION) * sizeof(float2) + 64; }
+};
+
+template <int N>
+__global__ void __launch_bounds__(QColCfg<N>::THREADS, 1)
+col_pass_quad_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_constant__ CUtensorMap map, int strips) {
+    using Cfg = QColCfg<N>;
+    using pk::CP;
+    constexpr int SPI = N / 4;                         // strips per item
+    constexpr uint32_t QBYTES = Cfg::SLOT * sizeof(float2);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    float2* regions = stage + Cfg::SLOTS * Cfg::SLOT;  // unit 0, then unit 1; together [N][4]
+    uint64_t* full = reinterpret_cast<uint64_t*>(regions + 2 * Cfg::REGION);
+    const int u = threadIdx.x / Cfg::TPL;
+    const int t = threadIdx.x % Cfg::TPL;
+    CP* xl = reinterpret_cast<CP*>(regions + u * Cfg::REGION);
+    const SyncNamed sync{1 + u, Cfg::TPL};
+    const float2* tw = a.tw;
+    const int mine = strips > (int)blockIdx.x ? (strips - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int loads = 4 * mine;                        // quarter loads of this block, in order
+
+    auto issue_load = [&](int i) {                     // quarter i % 4 of this block's strip i / 4
+        const int g = blockIdx.x + (i >> 2) * gridDim.x;
+        const int x = (g % SPI) * 4, y = (g / SPI) * N + (i & 3) * Cfg::QROWS;
+        float2* dst = stage + (i % Cfg::SLOTS) * Cfg::SLOT;
+        uint64_t* bar = &full[i % Cfg::SLOTS];
+        tc::mbar_arrive_expect_tx(bar, QBYTES);
+#pragma unroll 1
+        for (int q = 0; q < Cfg::QBOXES; ++q) tc::tma_load_2d(dst + q * 1024, &map, bar, x, y + q * 256);
+    };
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < Cfg::SLOTS; ++i) tc::mbar_init(&full[i], 1);
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&map);
+        for (int i = 0; i < Cfg::SLOTS && i < loads; ++i) issue_load(i);
+    }
+    __syncthreads();
+    bool ok = true;
+    for (int k = 0; k < mine; ++k) {
+        const int g = blockIdx.x + k * gridDim.x;
+        const int b = g / SPI, x0 = (g % SPI) * 4, col = x0 + 2 * u;
+        // the previous strip's stores have read the regions before anything writes them again
+        if (threadIdx.x == 0) tc::bulk_wait_read<0>();
+        CP v[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = 4 * k + q;
+            if (ok) ok = tc::mbar_wait(&full[i % Cfg::SLOTS], (i / Cfg::SLOTS) & 1, a.err, 15);
+            const float4* src = reinterpret_cast<const float4*>(stage + (i % Cfg::SLOTS) * Cfg::SLOT);
+#pragma unroll
+            for (int s = 4 * q; s < 4 * q + 4; ++s) {
+                const int r = t + s * Cfg::TPL - q * Cfg::QROWS;      // row within the quarter
+                const float4 c = src[r * 2 + u];                        // (re_A, im_A, re_B, im_B)
+                v[s] = CP{pk::pack(c.x, c.z), pk::pack(c.y, c.w)};
+            }
+            __syncthreads();                                            // both units have read the slot
+            if (threadIdx.x == 0 && i + Cfg::SLOTS < loads) issue_load(i + Cfg::SLOTS);
+        }
+        if (a.flags & CF_FWD) pk::line_fft2<N, false, false, SyncNamed, true>(v, xl, t, tw, sync);
+        if (a.flags & CF_TABLE) {
+            const float2* ty = a.tab_y + (size_t)b * N;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const float2 h = ty[t + s * Cfg::TPL];
+                v[s] = pk::cmul_b<false>(v[s], pk::pack(h.x, h.x), pk::pack(h.y, h.y));
+            }
+        }
+        if (a.flags & CF_INV) pk::line_fft2<N, true, false, SyncNamed, true>(v, xl, t, tw, sync);
+        if (a.flags & CF_TABLE) {
+            const float2 ha = a.tab_x[(size_t)b * N + col], hb = a.tab_x[(size_t)b * N + col + 1];
+            const pk::u64 hr = pk::pack(ha.x, hb.x), hi = pk::pack(ha.y, hb.y);
+#pragma unroll
+            for (int s = 0; s < 16; ++s)
+                v[s] = CP{pk::sub2(pk::mul2(v[s].re, hr), pk::mul2(v[s].im, hi)),
+                          pk::fma2(v[s].re, hi, pk::mul2(v[s].im, hr))};
+        }
+        __syncthreads();                               // both units are out of their exchanges
+        float4* out = reinterpret_cast<float4*>(regions);                 // [N][4] float2
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            float4 q;
+            pk::unpack(v[s].re, q.x, q.z);
+            pk::unpack(v[s].im, q.y, q.w);
+            out[(t + s * Cfg::TPL) * 2 + u] = q;
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll 1
+            for (int q = 0; q < Cfg::OBOXES; ++q) tc::tma_store_2d(&map, regions + q * 1024, x0, b * N + q * 256);
+            tc::bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) tc::bulk_wait<0>();
+}
+
 // Wide column pass: four adjacent columns per group, so that every row segment read or
 // written is one full 32-byte sector (two-column strips reach about half the copy bandwidth
 // of four-column ones). One resident block per SM of two pair-units (N/16 threads each,

@@ -39,7 +39,8 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
 // row (L * 8 bytes), narrower ones more resident blocks per SM. -1 = persistent TMA kernel,
 // -2 = unit-pipelined kernel (two columns per unit), -3 = unit-pipelined kernel on packed
 // FP32x2 column pairs, -4 = wide kernel (four columns, packed pairs, staged by TMA), -6 = the
-// packed-pair kernel writing its result transposed to a separate plane (row variant 4 reads it).
+// packed-pair kernel writing its result transposed to a separate plane (row variant 4 reads it),
+// -7 = quad kernel (four columns as two packed pairs, whole-sector strips, swizzled exchanges).
 template <>
 cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, const PassLaunch& l) {
     using namespace detail;
@@ -51,6 +52,7 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
         case 256: return col_launch<float2, 256, 16>(a, l);
         case 512: return col_launch<float2, 512, 16>(a, l);
         case 1024:
+            if (lines == -7) return col_launch_quad<1024>(a, l);
             if (lines == -4) return col_launch_wide<1024>(a, l);
             if (lines == -6) return col_launch_pair<1024, 8, 4, true>(a, l);
             if (lines == -3) return col_launch_pair<1024, 8, 4>(a, l);
@@ -58,6 +60,7 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
             if (lines == -1) return col_launch_persistent<float2, 1024, 4>(a, l);
             return lines == 8 ? col_launch<float2, 1024, 8>(a, l) : col_launch<float2, 1024, 16>(a, l);
         case 2048:
+            if (lines == -7) return col_launch_quad<2048>(a, l);
             if (lines == -4) return col_launch_wide<2048>(a, l);
             if (lines == -6) return col_launch_pair<2048, 4, 2, true>(a, l);
             if (lines == -3) return col_launch_pair<2048, 4, 2>(a, l);
@@ -65,6 +68,7 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
             if (lines == -1) return col_launch_persistent<float2, 2048, 2>(a, l);
             return lines == 4 ? col_launch<float2, 2048, 4>(a, l) : col_launch<float2, 2048, 8>(a, l);
         case 4096:
+            if (lines == -7) return col_launch_quad<4096>(a, l);
             if (lines == -4) return col_launch_wide<4096>(a, l);
             if (lines == -6) return col_launch_pair<4096, 2, 1, true>(a, l);
             if (lines == -3) return col_launch_pair<4096, 2, 1>(a, l);
@@ -99,9 +103,9 @@ int row_variant_default(int n) { return (n >= 1024 && n <= 4096) ? 3 : 0; }
 int col_candidates(int n, int* out) {
     switch (n) {
         case 8192: out[0] = 2; out[1] = 1; return 2;
-        case 4096: out[5] = -4; out[0] = 4; out[1] = 2; out[2] = -1; out[3] = -2; out[4] = -3; return 6;
-        case 2048: out[5] = -4; out[0] = 8; out[1] = 4; out[2] = -1; out[3] = -2; out[4] = -3; return 6;
-        case 1024: out[5] = -4; out[0] = 16; out[1] = 8; out[2] = -1; out[3] = -2; out[4] = -3; return 6;
+        case 4096: out[5] = -4; out[6] = -7; out[0] = 4; out[1] = 2; out[2] = -1; out[3] = -2; out[4] = -3; return 7;
+        case 2048: out[5] = -4; out[6] = -7; out[0] = 8; out[1] = 4; out[2] = -1; out[3] = -2; out[4] = -3; return 7;
+        case 1024: out[5] = -4; out[6] = -7; out[0] = 16; out[1] = 8; out[2] = -1; out[3] = -2; out[4] = -3; return 7;
         default:                                            // mixed radix: widest fit, and half of it
             out[0] = 0;
             if (!mixed_supported<float2>(n)) return 1;
@@ -135,13 +139,14 @@ void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persi
     } else {                                                // mirrors launch_col_pass<float2>
         if (lines == 0) lines = col_lines_default(n, false);
         switch (n) {
-            case 1024: p = lines < 0 ? -lines : 0; w = p == 1 || p == 4 ? 4 : p ? 2 : (lines == 8 ? 8 : 16); break;
-            case 2048: p = lines < 0 ? -lines : 0; w = p == 4 ? 4 : p ? 2 : (lines == 4 ? 4 : 8); break;
-            case 4096: p = lines < 0 ? -lines : 0; w = p == 4 ? 4 : p ? 2 : (lines == 2 ? 2 : 4); break;
+            case 1024: p = lines < 0 ? -lines : 0; w = p == 1 || p == 4 || p == 7 ? 4 : p ? 2 : (lines == 8 ? 8 : 16); break;
+            case 2048: p = lines < 0 ? -lines : 0; w = p == 4 || p == 7 ? 4 : p ? 2 : (lines == 4 ? 4 : 8); break;
+            case 4096: p = lines < 0 ? -lines : 0; w = p == 4 || p == 7 ? 4 : p ? 2 : (lines == 2 ? 2 : 4); break;
             case 8192: w = lines == 1 ? 1 : 2; break;
             default: w = 16; break;
         }
         if (p == 6) p = 7;                                  // lines -6: transposed packed pairs
+        else if (p == 7) p = 8;                             // lines -7: quad strips
     }
     if (persistent) *persistent = p;
     if (out_lines) *out_lines = w;

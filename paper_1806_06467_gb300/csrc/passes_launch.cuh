@@ -146,6 +146,30 @@ cudaError_t col_launch_pair(const ColArgs<float2>& a, const PassLaunch& l) {
 }
 
 template <int N>
+cudaError_t col_launch_quad(const ColArgs<float2>& a, const PassLaunch& l) {
+    using Cfg = QColCfg<N>;
+    static unsigned done = 0;
+    const size_t smem = Cfg::smem();
+    cudaError_t e = ensure_smem(col_pass_quad_kernel<N>, smem, done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = sm_count(&sms)) != cudaSuccess) return e;
+    if (a.in != a.out) return cudaErrorInvalidValue;   // one tensor map serves loads and stores
+    CUtensorMap map;
+    if ((e = tc_make_field_map(a.in, N, (long long)l.batch * N, 4, &map)) != cudaSuccess) return e;
+    static int occ = 0;
+    if (occ == 0) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, col_pass_quad_kernel<N>, Cfg::THREADS, smem)) != cudaSuccess)
+            return e;
+        if (occ < 1) occ = 1;
+    }
+    const int strips = l.batch * N / 4;
+    const int grid = strips < sms * occ ? strips : sms * occ;
+    col_pass_quad_kernel<N><<<grid, Cfg::THREADS, smem, l.stream>>>(a, map, strips);
+    return cudaGetLastError();
+}
+
+template <int N>
 cudaError_t col_launch_wide(const ColArgs<float2>& a, const PassLaunch& l) {
     using Cfg = WColCfg<N>;
     static unsigned done = 0;

@@ -278,9 +278,9 @@ def test_relay_graph_replay_matches_eager(ctx):
 
 KERNEL_CHOICES = {
     # n: (row variants, column kernels) the complex64 plan offers
-    1024: ([0, 1, 2, 3], [16, 8, -1, -2, -3, -4]),
-    2048: ([0, 1, 2, 3], [8, 4, -1, -2, -3, -4]),
-    4096: ([0, 1, 2, 3], [4, 2, -1, -2, -3, -4]),
+    1024: ([0, 1, 2, 3], [16, 8, -1, -2, -3, -4, -7]),
+    2048: ([0, 1, 2, 3], [8, 4, -1, -2, -3, -4, -7]),
+    4096: ([0, 1, 2, 3], [4, 2, -1, -2, -3, -4, -7]),
 }
 
 
@@ -315,7 +315,7 @@ def _relay_all_kernels(ctx, n, npix, seed):
 @pytest.mark.parametrize("n", [1024, 2048])
 def test_relay_every_pass_kernel(ctx, n):
     """Every row and column kernel the plan can pick (per-group, persistent, unit-pipelined,
-    packed pairs, wide) gives the oracle's relay to 1e-5 relative L2."""
+    packed pairs, wide, quad) gives the oracle's relay to 1e-5 relative L2."""
     seen = _relay_all_kernels(ctx, n, n // 2, seed=2)
     assert any("_units" in k for k in seen) and any("_persistent" in k for k in seen)
 
@@ -325,7 +325,7 @@ def test_relay_every_pass_kernel_4096(ctx):
     """The same at 4096^2, the benchmarked size (one oracle run, nine kernel pairs)."""
     seen = _relay_all_kernels(ctx, 4096, 1024, seed=0)
     assert "row_pass_units<4096>" in seen and "col_pass_units<4096,2>" in seen and "col_pass_pair<4096,2>" in seen
-    assert "col_pass_wide<4096,4>" in seen and "row_pass_pair<4096>" in seen
+    assert "col_pass_wide<4096,4>" in seen and "row_pass_pair<4096>" in seen and "col_pass_quad<4096,4>" in seen
 
 
 def relay_oracle_planes(w, maps_np):
@@ -489,10 +489,10 @@ def test_mixed_plan_direct_then_as(ctx):
         assert rel_l2(got[b], e) < 1e-5
 
 
-@pytest.mark.parametrize("col", [0, -1])
+@pytest.mark.parametrize("col", [0, -1, -7])
 def test_direct_hop_column_kernels_2048(ctx, col):
     """A direct (single-transform) hop followed by an angular-spectrum hop at 2048^2 on two
-    wavelengths, with the default column kernel and with the persistent one (their
+    wavelengths, with the default column kernel, the persistent one and the quad one (their
     forward-only form for the direct hop)."""
     n, npix = 2048, 512
     dx = 1.0 / npix
