@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--bf16", action="store_true", help="also time the 3xBF16 coronagraph plan")
     ap.add_argument("--psf-lambdas", type=int, default=21, help="wavelengths in the coronagraph batch")
     ap.add_argument("--psf-probes", type=int, default=8, help="DM probe states in the coronagraph batch")
+    ap.add_argument("--coronagraph-only", default=None, choices=["tf32", "bf16", "ext"],
+                    help="time only the broadband Lyot batch at this precision (for profiler captures)")
     return ap.parse_args()
 
 
@@ -808,6 +810,14 @@ def main():
 
     ctx = coro.Context(local)
     stream = torch.cuda.current_stream(device)
+    if args.coronagraph_only:
+        prec = {"tf32": coro.MFT_3XTF32, "bf16": coro.MFT_3XBF16, "ext": coro.MFT_EXT}[args.coronagraph_only]
+        line = coronagraph_bench(ctx, device, args.steps, args.warmup, prec, args.psf_lambdas, args.psf_probes)
+        line.update({"metric": METRIC, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                     "config": {"workload": f"broadband_lyot {args.psf_lambdas} x {args.psf_probes}"}})
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     n = args.n
     w, maps_np, maps, els = relay_setup(n, seed=rank, device=device)
     plan = coro.FresnelPlan(ctx, n=n, batch=1, pixelscale=w.dx, wavelength=w.wavelength_m,

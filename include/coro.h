@@ -291,12 +291,20 @@ coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent
  * the alternating layout, below; 8: quad kernel, four-column strips (whole 32-byte sectors)
  * as two packed pairs, streamed by TMA in quarter strips, exchanges in swizzled shared
  * memory of exactly N slots per pair.) */
+/* Radix sequence of pass i's line transforms (the FFT factorisation the chosen kernel runs):
+ * radices[0 .. min(*stages, max_radices) - 1], *stages the number of stages (radices may be
+ * NULL when max_radices is 0). Register-resident engines: radix 16 while it divides, the
+ * remainder last (4096 = 16 x 16 x 16); the shared-memory engine: mixed_plan's sequence
+ * (2800 = 16 x 5 x 5 x 7; row variant 5 / column lines -8 at a power of two: radix 8,
+ * 4096 = 8 x 8 x 8 x 8). Plain host query. */
+coro_status coro_fresnel_plan_pass_radix(coro_plan plan, int i, int* radices, int max_radices, int* stages);
 /* Override the tuned kernel choice of every pass of a complex64 plan.
  *   row_variant: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row
- *                pairs (2 and 3: N = 1024 ... 4096).
+ *                pairs, 5 the shared-memory engine with radix 8 (2, 3 and 5: N = 1024 ...
+ *                4096).
  *   col_lines:   columns per block (a width the plan's N supports), -1 persistent TMA,
- *                -2 unit-pipelined, -3 packed column pairs, -4 wide, -7 quad (-2 to -7:
- *                N = 1024 ... 4096), 0 default.
+ *                -2 unit-pipelined, -3 packed column pairs, -4 wide, -7 quad, -8 the
+ *                shared-memory engine with radix 8 (-2 to -8: N = 1024 ... 4096), 0 default.
  * Values the plan's N does not offer are rejected with CORO_EINVAL and nothing changes.
  * Every choice gives the same result up to FP32 rounding order (used to test each kernel). */
 coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, int col_lines);

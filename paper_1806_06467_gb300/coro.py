@@ -98,6 +98,7 @@ _SIGS = {
     "coro_lyot_plan_execute_range": (ct.c_int, [_P, _P, ct.POINTER(ct.c_double), _P, _P, ct.c_int, ct.c_int]),
     "coro_lyot_plan_flops": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
     "coro_lyot_plan_gemm_tile": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "coro_fresnel_plan_pass_radix": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.c_int, ct.POINTER(ct.c_int)]),
     "coro_lyot_plan_set_gemm_tile": (ct.c_int, [_P, ct.c_int]),
     "coro_version": (ct.c_int, []),
     "coro_last_error": (ct.c_char_p, []),
@@ -572,13 +573,21 @@ class FresnelPlan:
         row, _ = self.pass_info(i)
         kind = "row_pass" if row else "col_pass"
         name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide", "", "_mixed", "_pair_t", "_quad")[p.value]
+        if p.value == 6 and self.n & (self.n - 1) == 0:
+            name += "_r8"                               # the shared-memory engine at radix 8
         return f"{name}<{self.n}>" if row else f"{name}<{self.n},{w.value}>"
+
+    def pass_radix(self, i: int) -> list[int]:
+        """Radix sequence of pass i's line transforms (coro_fresnel_plan_pass_radix)."""
+        buf, k = (ct.c_int * 16)(), ct.c_int()
+        self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_radix(self.handle, i, buf, 16, ct.byref(k)))
+        return list(buf[:k.value])
 
     def set_pass_kernel(self, row_variant: int, col_lines: int) -> None:
         """Override the tuned kernels (row: 0 persistent, 1 per-group, 2 units, 3 packed row
-        pairs; column:
-        lines per block, -1 persistent TMA, -2 units, -3 packed column pairs, -4 wide
-        four-column groups, -7 quad four-column strips, 0 default)."""
+        pairs, 5 shared-memory radix-8 engine; column: lines per block, -1 persistent TMA,
+        -2 units, -3 packed column pairs, -4 wide four-column groups, -7 quad four-column
+        strips, -8 shared-memory radix-8 engine, 0 default)."""
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_set_pass_kernel(self.handle, row_variant, col_lines))
 
     def set_layout(self, transposed: bool) -> None:

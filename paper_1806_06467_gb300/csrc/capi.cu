@@ -138,16 +138,19 @@ __global__ void sep_table_kernel(C* out, int n, const TabSpec* spec) {
 
 namespace coro {
 
-const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st) {
+// linear: the table W_n^m of the shared-memory engine even when n is a power of two (kept
+// under the key -n beside the per-pass blocks).
+const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st, bool linear) {
     auto& cache = dbl ? ctx->tw64 : ctx->tw32;
-    auto it = cache.find(n);
+    const int key = (linear && is_pow2(n)) ? -n : n;
+    auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     void* p = nullptr;
     const size_t bytes = (size_t)n * (dbl ? sizeof(double2) : sizeof(float2));
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) { *st = cuda_fail(e, "cudaMalloc(twiddles)"); return nullptr; }
     const int th = 256;
-    if (!is_pow2(n)) {                          // mixed-radix passes: the linear table W_n^m
+    if (!is_pow2(n) || linear) {                // mixed-radix passes: the linear table W_n^m
         if (dbl) lin_twiddle_kernel<double2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((double2*)p, n);
         else lin_twiddle_kernel<float2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((float2*)p, n);
     } else if (dbl) {
@@ -157,7 +160,7 @@ const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st) {
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) { cudaFree(p); *st = cuda_fail(e, "twiddle_kernel"); return nullptr; }
-    cache[n] = p;
+    cache[key] = p;
     return p;
 }
 
@@ -549,6 +552,12 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
     coro_status st = CORO_OK;
     const C* tw = (const C*)get_twiddles(ctx, n, sizeof(C) == sizeof(double2), &st);
     if (!tw) return st;
+    const C* tw_lin = nullptr;                          // radix-8 shared-memory engine at a power of two
+    for (const Op& op : ops)
+        if (!tw_lin && ((op.row && op.variant == 5) || (!op.row && op.lines == -8))) {
+            tw_lin = (const C*)get_twiddles(ctx, n, sizeof(C) == sizeof(double2), &st, true);
+            if (!tw_lin) return st;
+        }
     PassLaunch pl{ctx->stream, batch};
     if (ev) {
         const cudaError_t e0 = record_timing_event(ev[0], ctx->stream);
@@ -563,7 +572,7 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
             RowArgs<C> a;
             a.in = (const C*)(t_in ? tbuf : field);
             a.out = (C*)field;
-            a.tw = tw;
+            a.tw = op.variant == 5 ? tw_lin : tw;
             a.flags = op.row_flags;
             a.err = ctx->err;
             a.elems = op.elems;
@@ -573,7 +582,7 @@ coro_status run_ops(coro_ctx ctx, int n, int batch, const std::vector<Op>& ops, 
             ColArgs<C> a;
             a.in = (const C*)field;
             a.out = (C*)(t_out ? tbuf : field);
-            a.tw = tw;
+            a.tw = op.lines == -8 ? tw_lin : tw;
             a.tab_x = (const C*)op.tab_x;
             a.tab_y = (const C*)op.tab_y;
             a.flags = op.col_flags;
@@ -844,8 +853,8 @@ std::vector<Op> timing_copy(const std::vector<Op>& ops) {
 
 coro_status autotune_ops(coro_ctx ctx, int dtype, int n, int batch, std::vector<Op>& ops, std::vector<std::string>* log) {
     if (dtype != CORO_C64 || !autotune_enabled()) return CORO_OK;
-    int cand[8];
-    const int nc = col_candidates(n, cand), nr = row_variant_count(n);
+    int cand[8], rcand[8];
+    const int nc = col_candidates(n, cand), nr = row_candidates(n, rcand);
     if (nc < 2 && nr < 2) return CORO_OK;
     coro_status st = CORO_OK;
     void* scratch = upload_async(ctx, nullptr, (size_t)batch * n * n * sizeof(float2), &st);
@@ -872,7 +881,8 @@ coro_status autotune_ops(coro_ctx ctx, int dtype, int n, int batch, std::vector<
     }
     if (row && nr > 1) {
         float best = 1e30f;
-        for (int v = 0; v < nr; ++v) {
+        for (int iv = 0; iv < nr; ++iv) {
+            const int v = rcand[iv];
             Op t = *row;
             t.variant = v;
             const float ms = time_ops<float2>(ctx, n, batch, {t}, scratch, 3);
@@ -1415,12 +1425,30 @@ extern "C" coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int*
     return CORO_OK;
 }
 
+extern "C" coro_status coro_fresnel_plan_pass_radix(coro_plan plan, int i, int* radices, int max_radices, int* stages) {
+    clear_error();
+    if (!plan || plan->kind() != 1) { set_error("coro_fresnel_plan_pass_radix: not a Fresnel plan"); return CORO_EINVAL; }
+    auto* p = static_cast<FresnelPlan*>(plan);
+    if (i < 0 || i >= (int)p->ops.size()) { set_error("coro_fresnel_plan_pass_radix: pass %d of %d", i, (int)p->ops.size()); return CORO_EINVAL; }
+    if (max_radices < 0 || (max_radices > 0 && !radices)) { set_error("coro_fresnel_plan_pass_radix: bad radices buffer"); return CORO_EINVAL; }
+    const Op& op = p->ops[i];
+    int r[16];
+    const int k = pass_radices(p->n, op.row, p->dtype == CORO_C64 ? op.variant : 0, p->dtype == CORO_C64 ? op.lines : 0, r, 16);
+    for (int j = 0; j < k && j < max_radices; ++j) radices[j] = r[j];
+    if (stages) *stages = k;
+    return CORO_OK;
+}
+
 extern "C" coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, int col_lines) {
     clear_error();
     if (!plan || plan->kind() != 1) { set_error("coro_fresnel_plan_set_pass_kernel: not a Fresnel plan"); return CORO_EINVAL; }
     auto* p = static_cast<FresnelPlan*>(plan);
     if (p->dtype != CORO_C64) { set_error("coro_fresnel_plan_set_pass_kernel: complex64 plans only"); return CORO_EINVAL; }
-    if (row_variant < 0 || row_variant >= row_variant_count(p->n)) {
+    int rcand[8];
+    const int nr = row_candidates(p->n, rcand);
+    bool row_ok = false;
+    for (int i = 0; i < nr; ++i) row_ok = row_ok || rcand[i] == row_variant;
+    if (!row_ok) {
         set_error("coro_fresnel_plan_set_pass_kernel: row variant %d not offered at n=%d", row_variant, p->n);
         return CORO_EINVAL;
     }

@@ -128,7 +128,7 @@ inline cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t s) {
 }
 
 // Twiddle table for n (built lazily on the context's stream).
-const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st);
+const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st, bool linear = false);
 // The Lyot plan at reference precision (lyot64.cu): complex128 fields, FP64 MFTs, item by item.
 coro_status lyot64_create(coro_ctx ctx, const coro_lyot_desc* d, coro_plan* out);
 coro_status lyot64_peak(coro_plan plan, const void* pupil, double* peak_out);

@@ -29,8 +29,11 @@ struct MixedPlan {
 };
 
 // Radix sequence of n; false when n is odd, below 16, has a prime factor above
-// kMixedMaxRadix or needs more stages than fit.
-inline bool mixed_plan(int n, MixedPlan* mp) {
+// kMixedMaxRadix or needs more stages than fit. pow2_radix (16 or 8) is the radix taken while
+// it divides what is left, before one smaller power of two (8 / 4 / 2) and the odd primes:
+// 4096 = 16 x 16 x 16 by default, 8 x 8 x 8 x 8 with pow2_radix 8 (the shared-memory engine's
+// alternative factorisation of the power-of-two lengths, a tuner candidate).
+inline bool mixed_plan(int n, MixedPlan* mp, int pow2_radix = 16) {
     if (n < 16 || (n & 1)) return false;
     mp->n = n;
     mp->stages = 0;
@@ -41,10 +44,11 @@ inline bool mixed_plan(int n, MixedPlan* mp) {
         m /= r;
         return true;
     };
-    while (m % 16 == 0)
-        if (!push(16)) return false;
+    if (pow2_radix != 16 && pow2_radix != 8) return false;
+    while (m % pow2_radix == 0)
+        if (!push(pow2_radix)) return false;
     for (int r : {8, 4, 2})
-        if (m % r == 0) {
+        if (r < pow2_radix && m % r == 0) {
             if (!push(r)) return false;
             break;
         }
@@ -312,9 +316,9 @@ template <typename C> inline bool mixed_supported(int n) {
 namespace detail {
 
 template <typename C>
-cudaError_t row_launch_mixed(int n, const RowArgs<C>& a, const PassLaunch& l) {
+cudaError_t row_launch_mixed(int n, const RowArgs<C>& a, const PassLaunch& l, int pow2_radix = 16) {
     MixedPlan mp;
-    if (!mixed_plan(n, &mp)) return cudaErrorInvalidValue;
+    if (!mixed_plan(n, &mp, pow2_radix)) return cudaErrorInvalidValue;
     const size_t smem = mixed_smem<C>(n, 1);
     if (smem > kMixedMaxSmem) return cudaErrorInvalidValue;
     static unsigned done = 0;
@@ -328,9 +332,9 @@ cudaError_t row_launch_mixed(int n, const RowArgs<C>& a, const PassLaunch& l) {
 // buffers fit in half the shared-memory budget run 512 threads, so that two share an SM and
 // one's loads and stores overlap the other's stages; larger ones run 1024 threads alone.
 template <typename C>
-cudaError_t col_launch_mixed(int n, int lines, const ColArgs<C>& a, const PassLaunch& l) {
+cudaError_t col_launch_mixed(int n, int lines, const ColArgs<C>& a, const PassLaunch& l, int pow2_radix = 16) {
     MixedPlan mp;
-    if (!mixed_plan(n, &mp)) return cudaErrorInvalidValue;
+    if (!mixed_plan(n, &mp, pow2_radix)) return cudaErrorInvalidValue;
     const int L = lines > 0 ? lines : mixed_col_lines<C>(n);
     if (L <= 0 || L > 8 || (L & (L - 1)) || n % L || mixed_smem<C>(n, L) > kMixedMaxSmem) return cudaErrorInvalidValue;
     const size_t smem = mixed_smem<C>(n, L);

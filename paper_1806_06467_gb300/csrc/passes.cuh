@@ -1472,6 +1472,10 @@ int col_candidates(int n, int* out);
 // up to 61, two lines in 200 KB of shared memory).
 bool mixed_length_ok(int n, bool dbl);
 int row_variant_count(int n);
+// Row variants the complex64 tuner times (row_variant_count's plus the radix-8 engine); <= 8.
+int row_candidates(int n, int* out);
+// Radix sequence of a pass's line transforms; returns the number of stages.
+int pass_radices(int n, bool row, int variant, int lines, int* out, int max_out);
 // The kernels used without tuning (CORO_AUTOTUNE=0, or sizes without candidates).
 int row_variant_default(int n);
 // The kernel a pass with these settings launches: persistent (1) or not, and its lines.

@@ -16,16 +16,19 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
         case 256: return row_launch<float2, 256>(a, l);
         case 512: return row_launch<float2, 512>(a, l);
         case 1024:
+            if (l.variant == 5) return row_launch_mixed<float2>(n, a, l, 8);
             if (l.variant == 4) return row_launch_pair<1024, 8, 4, true>(a, l);
             if (l.variant == 3) return row_launch_pair<1024, 8, 4>(a, l);
             if (l.variant == 2) return row_launch_units<float2, 1024, 8, 4>(a, l);
             return l.variant == 1 ? row_launch<float2, 1024>(a, l) : row_launch_persistent<float2, 1024>(a, l);
         case 2048:
+            if (l.variant == 5) return row_launch_mixed<float2>(n, a, l, 8);
             if (l.variant == 4) return row_launch_pair<2048, 4, 2, true>(a, l);
             if (l.variant == 3) return row_launch_pair<2048, 4, 2>(a, l);
             if (l.variant == 2) return row_launch_units<float2, 2048, 8, 4>(a, l);
             return l.variant == 1 ? row_launch<float2, 2048>(a, l) : row_launch_persistent<float2, 2048>(a, l);
         case 4096:
+            if (l.variant == 5) return row_launch_mixed<float2>(n, a, l, 8);
             if (l.variant == 4) return row_launch_pair<4096, 2, 1, true>(a, l);
             if (l.variant == 3) return row_launch_pair<4096, 2, 1>(a, l);
             if (l.variant == 2) return row_launch_units<float2, 4096, 4, 2>(a, l);
@@ -40,7 +43,9 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
 // -2 = unit-pipelined kernel (two columns per unit), -3 = unit-pipelined kernel on packed
 // FP32x2 column pairs, -4 = wide kernel (four columns, packed pairs, staged by TMA), -6 = the
 // packed-pair kernel writing its result transposed to a separate plane (row variant 4 reads it),
-// -7 = quad kernel (four columns as two packed pairs, whole-sector strips, swizzled exchanges).
+// -7 = quad kernel (four columns as two packed pairs, whole-sector strips, swizzled exchanges),
+// -8 = the shared-memory Stockham engine of mixed.cuh with radix 8 (N = 8^k x 2 or 4): the
+// alternative factorisation of the power-of-two lengths.
 template <>
 cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, const PassLaunch& l) {
     using namespace detail;
@@ -52,6 +57,7 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
         case 256: return col_launch<float2, 256, 16>(a, l);
         case 512: return col_launch<float2, 512, 16>(a, l);
         case 1024:
+            if (lines == -8) return col_launch_mixed<float2>(n, 0, a, l, 8);
             if (lines == -7) return col_launch_quad<1024>(a, l);
             if (lines == -4) return col_launch_wide<1024>(a, l);
             if (lines == -6) return col_launch_pair<1024, 8, 4, true>(a, l);
@@ -60,6 +66,7 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
             if (lines == -1) return col_launch_persistent<float2, 1024, 4>(a, l);
             return lines == 8 ? col_launch<float2, 1024, 8>(a, l) : col_launch<float2, 1024, 16>(a, l);
         case 2048:
+            if (lines == -8) return col_launch_mixed<float2>(n, 0, a, l, 8);
             if (lines == -7) return col_launch_quad<2048>(a, l);
             if (lines == -4) return col_launch_wide<2048>(a, l);
             if (lines == -6) return col_launch_pair<2048, 4, 2, true>(a, l);
@@ -68,6 +75,7 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
             if (lines == -1) return col_launch_persistent<float2, 2048, 2>(a, l);
             return lines == 4 ? col_launch<float2, 2048, 4>(a, l) : col_launch<float2, 2048, 8>(a, l);
         case 4096:
+            if (lines == -8) return col_launch_mixed<float2>(n, 0, a, l, 8);
             if (lines == -7) return col_launch_quad<4096>(a, l);
             if (lines == -4) return col_launch_wide<4096>(a, l);
             if (lines == -6) return col_launch_pair<4096, 2, 1, true>(a, l);
@@ -103,9 +111,9 @@ int row_variant_default(int n) { return (n >= 1024 && n <= 4096) ? 3 : 0; }
 int col_candidates(int n, int* out) {
     switch (n) {
         case 8192: out[0] = 2; out[1] = 1; return 2;
-        case 4096: out[5] = -4; out[6] = -7; out[0] = 4; out[1] = 2; out[2] = -1; out[3] = -2; out[4] = -3; return 7;
-        case 2048: out[5] = -4; out[6] = -7; out[0] = 8; out[1] = 4; out[2] = -1; out[3] = -2; out[4] = -3; return 7;
-        case 1024: out[5] = -4; out[6] = -7; out[0] = 16; out[1] = 8; out[2] = -1; out[3] = -2; out[4] = -3; return 7;
+        case 4096: out[5] = -4; out[6] = -7; out[7] = -8; out[0] = 4; out[1] = 2; out[2] = -1; out[3] = -2; out[4] = -3; return 8;
+        case 2048: out[5] = -4; out[6] = -7; out[7] = -8; out[0] = 8; out[1] = 4; out[2] = -1; out[3] = -2; out[4] = -3; return 8;
+        case 1024: out[5] = -4; out[6] = -7; out[7] = -8; out[0] = 16; out[1] = 8; out[2] = -1; out[3] = -2; out[4] = -3; return 8;
         default:                                            // mixed radix: widest fit, and half of it
             out[0] = 0;
             if (!mixed_supported<float2>(n)) return 1;
@@ -116,10 +124,42 @@ int col_candidates(int n, int* out) {
     }
 }
 
-// row variants: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row pairs
-// (4, packed row pairs read from a transposed plane, is only paired with column lines -6 and is
-// not a tuning candidate)
+// row variants: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row
+// pairs, 5 the shared-memory engine with radix 8 (4, packed row pairs read from a transposed
+// plane, is only paired with column lines -6 and is not a tuning candidate)
 int row_variant_count(int n) { return (n >= 1024 && n <= 4096) ? 4 : n == 8192 ? 2 : 1; }
+
+int row_candidates(int n, int* out) {
+    const int k = row_variant_count(n);
+    for (int v = 0; v < k; ++v) out[v] = v;
+    if (n >= 1024 && n <= 4096) {
+        out[k] = 5;
+        return k + 1;
+    }
+    return k;
+}
+
+// Radix sequence of the line transforms of a pass (complex64 kernels; the FP64 passes share
+// the radix-16 engine): the register-resident engines take radix 16 while it divides and the
+// remainder in the last stage; the shared-memory engine (mixed-radix lengths, or row variant 5 /
+// column lines -8 at powers of two) follows mixed_plan.
+int pass_radices(int n, bool row, int variant, int lines, int* out, int max_out) {
+    MixedPlan mp;
+    const bool radix8 = row ? variant == 5 : lines == -8;
+    if ((n & (n - 1)) || radix8) {
+        if (!mixed_plan(n, &mp, radix8 ? 8 : 16)) return 0;
+    } else {
+        mp.stages = 0;
+        int m = n;
+        while (m > 1 && mp.stages < kMixedMaxStages) {
+            const int r = m >= 16 ? 16 : m;
+            mp.radix[mp.stages++] = r;
+            m /= r;
+        }
+    }
+    for (int i = 0; i < mp.stages && i < max_out; ++i) out[i] = mp.radix[i];
+    return mp.stages;
+}
 
 bool mixed_length_ok(int n, bool dbl) { return dbl ? mixed_supported<double2>(n) : mixed_supported<float2>(n); }
 
@@ -131,6 +171,11 @@ void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persi
         return;
     }
     if (variant < 0) variant = row_variant_default(n);
+    if ((row && variant == 5 && !dbl) || (!row && lines == -8 && !dbl)) {   // radix-8 shared-memory engine
+        if (persistent) *persistent = 6;
+        if (out_lines) *out_lines = row ? 1 : mixed_col_lines<float2>(n);
+        return;
+    }
     if (row) {                                              // mirrors launch_row_pass
         p = (!dbl && n >= 1024) ? (variant == 1 ? 0 : (variant == 2 || variant == 3) && n <= 4096 ? variant : 1) : 0;
         if (!dbl && variant == 4 && n >= 1024 && n <= 4096) p = 7;

@@ -278,9 +278,9 @@ def test_relay_graph_replay_matches_eager(ctx):
 
 KERNEL_CHOICES = {
     # n: (row variants, column kernels) the complex64 plan offers
-    1024: ([0, 1, 2, 3], [16, 8, -1, -2, -3, -4, -7]),
-    2048: ([0, 1, 2, 3], [8, 4, -1, -2, -3, -4, -7]),
-    4096: ([0, 1, 2, 3], [4, 2, -1, -2, -3, -4, -7]),
+    1024: ([0, 1, 2, 3, 5], [16, 8, -1, -2, -3, -4, -7, -8]),
+    2048: ([0, 1, 2, 3, 5], [8, 4, -1, -2, -3, -4, -7, -8]),
+    4096: ([0, 1, 2, 3, 5], [4, 2, -1, -2, -3, -4, -7, -8]),
 }
 
 
@@ -297,16 +297,21 @@ def _relay_all_kernels(ctx, n, npix, seed):
     seen = set()
     # every row kernel with one column kernel, every column kernel with one row kernel
     combos = [(rv, cols[0]) for rv in rows] + [(rows[0], cl) for cl in cols[1:]]
+    r16 = {1024: [16, 16, 4], 2048: [16, 16, 8], 4096: [16, 16, 16]}[n]
+    r8 = {1024: [8, 8, 8, 2], 2048: [8, 8, 8, 4], 4096: [8, 8, 8, 8]}[n]
     for rv, cl in combos:
         plan.set_pass_kernel(rv, cl)
         names = {plan.pass_kernel(i) for i in range(plan.launch_count)}
         seen |= names
+        for i in range(plan.launch_count):            # the FFT factorisation each pass runs
+            row, _ = plan.pass_info(i)
+            assert plan.pass_radix(i) == (r8 if (rv == 5 if row else cl == -8) else r16), (rv, cl, i)
         x.fill_(float("nan"))
         plan.execute(x)
         err = rel_l2(x.cpu().numpy()[0], ref)
         assert err < 1e-5, (rv, cl, sorted(names), err)
     with pytest.raises(RuntimeError):
-        plan.set_pass_kernel(len(rows), 0)
+        plan.set_pass_kernel(4, 0)                     # the transposed-input row kernel is not a choice
     with pytest.raises(RuntimeError):
         plan.set_pass_kernel(0, 3)
     return seen
@@ -315,7 +320,9 @@ def _relay_all_kernels(ctx, n, npix, seed):
 @pytest.mark.parametrize("n", [1024, 2048])
 def test_relay_every_pass_kernel(ctx, n):
     """Every row and column kernel the plan can pick (per-group, persistent, unit-pipelined,
-    packed pairs, wide, quad) gives the oracle's relay to 1e-5 relative L2."""
+    packed pairs, wide, quad, and the radix-8 shared-memory engine: a second factorisation of
+    the power-of-two lengths) gives the oracle's relay to 1e-5 relative L2, and reports its
+    radix sequence."""
     seen = _relay_all_kernels(ctx, n, n // 2, seed=2)
     assert any("_units" in k for k in seen) and any("_persistent" in k for k in seen)
 
@@ -326,6 +333,7 @@ def test_relay_every_pass_kernel_4096(ctx):
     seen = _relay_all_kernels(ctx, 4096, 1024, seed=0)
     assert "row_pass_units<4096>" in seen and "col_pass_units<4096,2>" in seen and "col_pass_pair<4096,2>" in seen
     assert "col_pass_wide<4096,4>" in seen and "row_pass_pair<4096>" in seen and "col_pass_quad<4096,4>" in seen
+    assert "row_pass_mixed_r8<4096>" in seen and any(k.startswith("col_pass_mixed_r8<4096,") for k in seen)
 
 
 def relay_oracle_planes(w, maps_np):

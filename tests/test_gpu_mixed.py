@@ -73,6 +73,7 @@ def test_relay_plan_2800(ctx):
                             distances=list(w.distances()), elements=els, init_uniform=True)
     assert plan.launch_count == 11
     assert all("_mixed" in plan.pass_kernel(i) for i in range(plan.launch_count))
+    assert all(plan.pass_radix(i) == [16, 5, 5, 7] for i in range(plan.launch_count))   # 2800 = 16 x 5 x 5 x 7
     x = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
     plan.execute(x)
     lam, dx = w.wavelength_m, w.dx
