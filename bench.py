@@ -553,6 +553,7 @@ def coronagraph_bench(ctx, device, steps: int, warmup: int, precision: int, n_la
            "workload": "broadband_lyot: 21 wavelengths (500-600 nm) x 8 DM sinc probes, 1024^2 pupil, "
                        "occulter 235-282 px at 0.05 lc/l lambda/D, detector 512^2",
            "ms_per_step": total_ms / steps, "gpu_launches_per_step": 8, "graph_replays": 1,
+           "gemm_tile": list(plan.gemm_tile()),
            "roofline": {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": pk,
                         "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
                         "flops_per_step": useful_flops, "time_share": gemm_ms / float(per.sum()),

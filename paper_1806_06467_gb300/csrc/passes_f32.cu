@@ -132,7 +132,7 @@ int row_variant_count(int n) { return (n >= 1024 && n <= 4096) ? 4 : n == 8192 ?
 int row_candidates(int n, int* out) {
     const int k = row_variant_count(n);
     for (int v = 0; v < k; ++v) out[v] = v;
-    if (n >= 1024 && n <= 4096) {
+    if (n >= 1024 && n <= 4096 && !(n & (n - 1))) {
         out[k] = 5;
         return k + 1;
     }
@@ -145,7 +145,7 @@ int row_candidates(int n, int* out) {
 // column lines -8 at powers of two) follows mixed_plan.
 int pass_radices(int n, bool row, int variant, int lines, int* out, int max_out) {
     MixedPlan mp;
-    const bool radix8 = row ? variant == 5 : lines == -8;
+    const bool radix8 = !(n & (n - 1)) && (row ? variant == 5 : lines == -8);   // a power-of-two choice only
     if ((n & (n - 1)) || radix8) {
         if (!mixed_plan(n, &mp, radix8 ? 8 : 16)) return 0;
     } else {
