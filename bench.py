@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--psf-probes", type=int, default=8, help="DM probe states in the coronagraph batch")
     ap.add_argument("--coronagraph-only", default=None, choices=["tf32", "bf16", "ext"],
                     help="time only the broadband Lyot batch at this precision (for profiler captures)")
+    ap.add_argument("--gemm-tile", type=int, default=0,
+                    help="with --coronagraph-only: run this GEMM tile width instead of the plan's tuned one")
     return ap.parse_args()
 
 
@@ -500,7 +502,7 @@ def max_darkhole_error(inten, ref, items, md: int, device) -> float:
 
 
 def coronagraph_bench(ctx, device, steps: int, warmup: int, precision: int, n_lambda: int = 21,
-                      n_probe: int = 8, pupils=None, keep_output: bool = False) -> dict:
+                      n_probe: int = 8, pupils=None, keep_output: bool = False, gemm_tile: int = 0) -> dict:
     import numpy as np
     import torch
 
@@ -510,6 +512,8 @@ def coronagraph_bench(ctx, device, steps: int, warmup: int, precision: int, n_la
     pupils, items, lw = pupils
     B, n, md = len(items), lw.n, lw.m_det
     plan = coro.LyotPlan(ctx, n=n, npix=lw.npix, lyot_frac=lw.lyot_frac, m_det=md, items=items, precision=precision)
+    if gemm_tile:
+        plan.set_gemm_tile(gemm_tile)
     peak = plan.peak(pupils)                          # normalisation, computed once
     psf = torch.empty((B, md, md), dtype=torch.float32, device=device)   # the PSFs, written every step
     stream = torch.cuda.current_stream(device)
@@ -813,7 +817,8 @@ def main():
     stream = torch.cuda.current_stream(device)
     if args.coronagraph_only:
         prec = {"tf32": coro.MFT_3XTF32, "bf16": coro.MFT_3XBF16, "ext": coro.MFT_EXT}[args.coronagraph_only]
-        line = coronagraph_bench(ctx, device, args.steps, args.warmup, prec, args.psf_lambdas, args.psf_probes)
+        line = coronagraph_bench(ctx, device, args.steps, args.warmup, prec, args.psf_lambdas, args.psf_probes,
+                                 gemm_tile=args.gemm_tile)
         line.update({"metric": METRIC, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                      "config": {"workload": f"broadband_lyot {args.psf_lambdas} x {args.psf_probes}"}})
         if rank == 0:

@@ -159,6 +159,30 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, ui
     }
 }
 
+// BF16 MMA with the A-operand collector: FILL reads A from shared memory and keeps it; USE
+// takes A from the collector (a previous FILL with the same descriptor, no MMA with another A
+// in between); LASTUSE does the same and releases it. Consecutive MMAs that share A then
+// read it from shared memory once.
+enum CollectorOp { COLL_NONE = 0, COLL_FILL = 1, COLL_USE = 2, COLL_LASTUSE = 3 };
+template <int OP>
+__device__ __forceinline__ void umma_bf16_coll(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    if constexpr (OP == COLL_FILL) {
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}\n"
+                     ::"r"(d_tmem), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+    } else if constexpr (OP == COLL_USE) {
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}\n"
+                     ::"r"(d_tmem), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+    } else if constexpr (OP == COLL_LASTUSE) {
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}\n"
+                     ::"r"(d_tmem), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+    } else {
+        umma<true>(d_tmem, a, b, id, acc);
+    }
+}
+
 // Arrive on `bar` once every previously issued MMA of this thread has completed.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))

@@ -2,12 +2,13 @@
 // tcx_gemm.cuh for the number format and why the level-0 accumulation is exact), its operand
 // producers and launcher.
 //
-// One CTA owns a 128 x 64 complex output tile. Warp 0 streams 32-byte K steps (16 BF16) of the
+// One CTA owns a 128 x 64 (or 128 x 32) complex output tile. Warp 0 streams 32-byte K steps (16 BF16) of the
 // eight X planes (128 rows) and the twelve W planes (64 rows) through a 4-stage shared-memory
 // ring, one 4-D TMA per operand (32-byte swizzle). Warp 1 issues, per K step, the ten slice
 // products of levels 0..3, each as two N = 128 MMAs (real X slice against [Re W; Im W], imaginary
-// X slice against [-Im W; Re W]), into two TMEM accumulators of 128 columns (level 0; levels 1-3),
-// double-buffered across groups of two K steps (32 K elements: the operands' scaling groups).
+// X slice against [-Im W; Re W]), grouped so that MMAs sharing an X plane take it from the
+// A-operand collector, into two TMEM accumulators of 128 columns (level 0; levels 1-3),
+// double-buffered across groups of four K steps (64 K elements: the operands' scaling groups).
 // Warps 2-17 drain each finished group into two-float registers and run the epilogue.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -26,7 +27,8 @@ namespace {
 
 constexpr int BM = 128;                  // rows of X per tile (UMMA M)
 constexpr int KSTEP = 16;                // BF16 K elements per stage (32 bytes, one MMA)
-constexpr int GROUP = 32;                // K elements per scaling group = per TMEM drain
+constexpr int GROUP = 64;                // K elements per scaling group = per TMEM drain
+constexpr int STEPS_PER_GROUP = GROUP / KSTEP;
 constexpr int XPLANE_BYTES = BM * 32;    // 4 KB
 constexpr int X_BYTES = TCX_X_PLANES * XPLANE_BYTES;   // 32 KB
 constexpr int EPI_WARPS = 16;            // four per TMEM lane quarter
@@ -68,13 +70,30 @@ __device__ __forceinline__ int ceil_log2(float ax) {
     return (b & 0x7fffff) ? ex + 1 : ex;
 }
 
-// Group exponent from the lanes' magnitudes (all 32 lanes must call): 2^e >= every |value|.
+// Largest |value| of the warp's 32 lanes (all lanes must call), as float bits: non-negative
+// floats order like their bit patterns.
+__device__ __forceinline__ uint32_t warp_max_bits(float amax) {
+    return __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+}
+
+// Group exponent from the group's largest magnitude m (float bits): 2^e >= every |value|.
 // Clamped to [-90, 120] so that every slice scale 2^(e - 32) stays a normal float.
-__device__ __forceinline__ int group_exp(float amax) {
-    const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+__device__ __forceinline__ int group_exp_of(uint32_t m) {
     if (m == 0) return -90;
     int e = ceil_log2(__uint_as_float(m));
     return e < -90 ? -90 : (e > 120 ? 120 : e);
+}
+
+// Exponent of a 64-element group held by two consecutive warps of a block (warps 2w, 2w + 1);
+// every thread of the block calls (two block barriers). sh: one word per warp.
+__device__ __forceinline__ int group64_exp_block(float amax, uint32_t* sh) {
+    const uint32_t wm = warp_max_bits(amax);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sh[w] = wm;
+    __syncthreads();
+    const uint32_t m = max(sh[w & ~1], sh[w | 1]);
+    __syncthreads();
+    return group_exp_of(m);
 }
 
 // Four slices of the two-float value (h, l) in the group with exponent e.
@@ -151,7 +170,7 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int g0 = 0, ngroups = (it.K + GROUP - 1) / GROUP;
     tile_k_range<BM, BN>(it, m0, n0, GROUP, EPI == TC_EPI_SPLITT || EPI == TC_EPI_BABINET, g0, ngroups);
-    const int nsteps = 2 * ngroups;
+    const int nsteps = STEPS_PER_GROUP * ngroups;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
@@ -185,14 +204,11 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t ID = tc::idesc<true>(BM, 2 * BN, false);
-            // the ten products (X slice i, W slice j) of levels i + j <= 3, level 0 first
-            constexpr int PX[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-            constexpr int PW[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
             bool ok = true;
             for (int k = 0; k < nsteps && ok; ++k) {
                 const int s = k % STAGES;
                 const uint32_t ph = (k / STAGES) & 1;
-                const int g = k >> 1, buf = g & 1, half = k & 1;
+                const int g = k / STEPS_PER_GROUP, buf = g & 1, half = k % STEPS_PER_GROUP;
                 if (half == 0) {
                     if (!(ok = tc::mbar_wait(&tempty[buf], ((g >> 1) & 1) ^ 1, a.err, 14))) break;
                     tc::tc_fence_after();
@@ -204,20 +220,29 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
                 // start-address field (addresses stay below 256 KB, so no carry leaves it)
                 const uint64_t dx = sdesc_sw32(tc::smem_u32(smem + s * STAGE_BYTES));
                 const uint64_t dw = sdesc_sw32(tc::smem_u32(smem + s * STAGE_BYTES + X_BYTES));
+                // the ten products (X slice i, W slice j) of levels i + j <= 3, grouped by the X slice
+                // component they read: consecutive MMAs with the same A keep it in the collector,
+                // so each of the eight X planes leaves shared memory once per step
 #pragma unroll
-                for (int p = 0; p < 10; ++p) {
-                    const int i = PX[p], j = PW[p];
-                    const uint32_t d = p == 0 ? d0 : d1;
-                    const uint64_t a_re = dx + (uint64_t)((2 * i) * XPLANE_BYTES >> 4);
-                    const uint64_t a_im = dx + (uint64_t)((2 * i + 1) * XPLANE_BYTES >> 4);
-                    const uint64_t b_ri = dw + (uint64_t)((3 * j + 1) * WPLANE_BYTES >> 4);   // [Re W; Im W]
-                    const uint64_t b_nr = dw + (uint64_t)((3 * j) * WPLANE_BYTES >> 4);       // [-Im W; Re W]
-                    const uint32_t acc = (half == 0 && (p == 0 || p == 1)) ? 0u : 1u;
-                    tc::umma<true>(d, a_re, b_ri, ID, acc);
-                    tc::umma<true>(d, a_im, b_nr, ID, 1u);
+                for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {                   // 0: real X slice, 1: imaginary
+                        const uint64_t a_desc = dx + (uint64_t)((2 * i + c) * XPLANE_BYTES >> 4);
+#pragma unroll
+                        for (int j = 0; j <= 3 - i; ++j) {
+                            // [Re W; Im W] for the real slice, [-Im W; Re W] for the imaginary one
+                            const uint64_t b_desc = dw + (uint64_t)((3 * j + 1 - c) * WPLANE_BYTES >> 4);
+                            const uint32_t d = (i + j == 0) ? d0 : d1;
+                            const uint32_t acc = (half == 0 && i == 0 && c == 0 && j <= 1) ? 0u : 1u;
+                            if (i == 3) tc::umma_bf16_coll<tc::COLL_NONE>(d, a_desc, b_desc, ID, acc);
+                            else if (j == 0) tc::umma_bf16_coll<tc::COLL_FILL>(d, a_desc, b_desc, ID, acc);
+                            else if (j == 3 - i) tc::umma_bf16_coll<tc::COLL_LASTUSE>(d, a_desc, b_desc, ID, acc);
+                            else tc::umma_bf16_coll<tc::COLL_USE>(d, a_desc, b_desc, ID, acc);
+                        }
+                    }
                 }
                 tc::umma_commit(&empty[s]);             // frees the stage once these MMAs retire
-                if (half == 1 || k == nsteps - 1) tc::umma_commit(&tfull[buf]);
+                if (half == STEPS_PER_GROUP - 1 || k == nsteps - 1) tc::umma_commit(&tfull[buf]);
             }
         }
     } else {
@@ -236,30 +261,39 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
             if (!(ok = tc::mbar_wait(&tfull[buf], (g >> 1) & 1, a.err, 13))) break;
             __syncwarp();
             tc::tc_fence_after();
-            // eight columns at a time: level 0 and levels 1-3 of the same outputs
+            // eight columns at a time, level 0 and levels 1-3 of the same outputs; BATCH such
+            // pairs of loads are in flight before each wait (32 registers)
             constexpr int PARTS = EPI_COLS / 8;                     // per component
+            constexpr int BATCH = 2;
 #pragma unroll
-            for (int part = 0; part < 2 * PARTS; ++part) {
-                const int c = (part % PARTS) * 8;                   // column offset within the warp's
-                const int imag = part / PARTS;                      // real parts first, then imaginary
-                const uint32_t col = buf * 2 * ACC + imag * BN + c;
-                uint32_t p0[8], p1[8];
-                tc::tmem_ld8(lane_base + col, p0);
-                tc::tmem_ld8(lane_base + col + ACC, p1);
+            for (int p0i = 0; p0i < 2 * PARTS; p0i += BATCH) {
+                uint32_t q0[BATCH][8], q1[BATCH][8];
+#pragma unroll
+                for (int bb = 0; bb < BATCH; ++bb) {
+                    const int part = p0i + bb;
+                    const uint32_t col = buf * 2 * ACC + (part / PARTS) * BN + (part % PARTS) * 8;
+                    tc::tmem_ld8(lane_base + col, q0[bb]);
+                    tc::tmem_ld8(lane_base + col + ACC, q1[bb]);
+                }
                 tc::tmem_ld_wait();
-                if (part == 2 * PARTS - 1) {
+                if (p0i + BATCH >= 2 * PARTS) {                     // the buffer is drained
                     tc::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&tempty[buf]);
                 }
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float& h = imag ? hi_[c + j] : hr[c + j];
-                    float& l = imag ? li[c + j] : lr[c + j];
-                    float s, e;
-                    two_sum(h, __uint_as_float(p0[j]), s, e);
-                    h = s;
-                    l += e + __uint_as_float(p1[j]);
+                for (int bb = 0; bb < BATCH; ++bb) {
+                    const int part = p0i + bb;
+                    const int c = (part % PARTS) * 8, imag = part / PARTS;   // real parts first
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float& h = imag ? hi_[c + j] : hr[c + j];
+                        float& l = imag ? li[c + j] : lr[c + j];
+                        float s, e;
+                        two_sum(h, __uint_as_float(q0[bb][j]), s, e);
+                        h = s;
+                        l += e + __uint_as_float(q1[bb][j]);
+                    }
                 }
             }
         }
@@ -274,6 +308,11 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
         const size_t plane = (size_t)a.dst_rows * a.dst_ld;
         if constexpr (EPI == TC_EPI_SPLITT || EPI == TC_EPI_BABINET) {
             __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(a.dst);
+            // pass 1: the output values (Babinet subtraction, mask) in place, and this warp's
+            // largest magnitude per column; the 64 rows m0 + 64 h ... + 63 of a scaling group
+            // (the next GEMM's K elements) belong to warps q = 2h and 2h + 1 of the same column group
+            uint32_t* xmax = reinterpret_cast<uint32_t*>(smem);   // stage memory: every MMA has retired
+            const int ew = warp - 2;
 #pragma unroll
             for (int j = 0; j < EPI_COLS; ++j) {
                 const int n = n0 + cg * EPI_COLS + j;
@@ -302,15 +341,27 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
                         vi = s; vil = e + (ail - vil);
                     }
                 }
-                const float amax = fmaxf(fabsf(vr), fabsf(vi));
-                const int ge = group_exp(amax);                // all lanes: rows m0 + 32 q .. + 31
+                hr[j] = vr; lr[j] = vrl; hi_[j] = vi; li[j] = vil;
+                const uint32_t wm = warp_max_bits(fmaxf(fabsf(vr), fabsf(vi)));
+                if (lane == 0) xmax[ew * EPI_COLS + j] = wm;
+            }
+            // the two warps of each scaling group meet at their own named barrier (ids 1-8)
+            asm volatile("bar.sync %0, 64;" ::"r"(1 + cg * 2 + (q >> 1)) : "memory");
+            // epilogue warp w = 4 cg + i has TMEM lane quarter q = (i + 2) & 3 (warp = w + 2)
+            const int partner = 4 * cg + (((q ^ 1) + 2) & 3);
+#pragma unroll
+            for (int j = 0; j < EPI_COLS; ++j) {
+                const int n = n0 + cg * EPI_COLS + j;
+                const bool valid = ok && m < it.M && n < it.N;
+                const uint32_t gm = max(xmax[ew * EPI_COLS + j], xmax[partner * EPI_COLS + j]);
+                const int ge = group_exp_of(gm);
                 if (valid) {
                     float sr[4], si[4];
-                    make_slices(vr, vrl, ge, sr);
-                    make_slices(vi, vil, ge, si);
+                    make_slices(hr[j], lr[j], ge, sr);
+                    make_slices(hi_[j], li[j], ge, si);
                     const size_t off = b * a.dst_bstride + (size_t)n * a.dst_ld + m;
                     store_sliced(dst, plane, off, sr, si);
-                    if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(vr + vrl, vi + vil);
+                    if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(hr[j] + lr[j], hi_[j] + li[j]);
                 }
             }
         } else if constexpr (EPI == TC_EPI_C64T) {
@@ -389,10 +440,12 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
 
 // ---------------------------------------------------------------- operand producers
 
-// complex64 rows -> sliced X planes; one thread per element, a warp per 32-element group.
+// complex64 rows -> sliced X planes; one thread per element, two warps per 64-element group
+// (blocks of 128 threads).
 __global__ void tcx_split_kernel(const float2* __restrict__ src, long long sb, int sld, __nv_bfloat16* dst, int rows,
                                  int cols, int ld, const int* __restrict__ keep_r2) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;   // blockDim a multiple of 32: warps = groups
+    __shared__ uint32_t sh[4];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y, b = blockIdx.z;
     float2 v = make_float2(0.f, 0.f);
     if (k < cols) v = src[b * sb + (size_t)r * sld + k];
@@ -400,7 +453,7 @@ __global__ void tcx_split_kernel(const float2* __restrict__ src, long long sb, i
         const int kx = k - cols / 2, ky = r - rows / 2;
         if (kx * kx + ky * ky > keep_r2[b]) v = make_float2(0.f, 0.f);
     }
-    const int ge = group_exp(fmaxf(fabsf(v.x), fabsf(v.y)));
+    const int ge = group64_exp_block(fmaxf(fabsf(v.x), fabsf(v.y)), sh);
     if (k >= ld) return;
     float sr[4], si[4];
     make_slices(v.x, 0.f, ge, sr);
@@ -413,6 +466,7 @@ __global__ void tcx_split_kernel(const float2* __restrict__ src, long long sb, i
 // cycle, then sliced from the FP64 value (no FP32 rounding of the basis).
 __global__ void tcx_basis_kernel(double c, int sign, __nv_bfloat16* dst, int rows, int cols, int ld, int plane_rows,
                                  int item) {
+    __shared__ uint32_t sh[4];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     double re = 0.0, im = 0.0;
@@ -425,7 +479,7 @@ __global__ void tcx_basis_kernel(double c, int sign, __nv_bfloat16* dst, int row
         re = co;
         im = sign < 0 ? -s : s;
     }
-    const int ge = group_exp(fmaxf((float)fabs(re), (float)fabs(im)));
+    const int ge = group64_exp_block(fmaxf((float)fabs(re), (float)fabs(im)), sh);
     if (k >= ld) return;
     const float rh = (float)re, rl = (float)(re - (double)rh), ih = (float)im, il = (float)(im - (double)ih);
     float sr[4], si[4];

@@ -6,12 +6,12 @@
 // Operand format ("sliced"): every complex value v of a row is written as four BF16 slices per
 // real component, v = s0 + s1 + s2 + s3 with s_i = a_i 2^(e - 8(i+1)), a_i an integer, |a_0| <=
 // 256, |a_i| <= 128 for i >= 1, and 2^e a power of two no smaller than max(|Re|, |Im|) over the
-// value's group of 32 consecutive K elements of its row (groups aligned at K = 0, 32, ...).
+// value's group of 64 consecutive K elements of its row (groups aligned at K = 0, 64, ...).
 // Four slices carry 32 bits below the group's largest value.
 //
 // Why it is exact: with both operands in this form, every product s_i(X) s_j(W) inside one
 // group is an integer multiple of 2^(eX + eW - 8(i+j+2)), at most 2^16 such units for i = j = 0.
-// A complex real part sums 2 x 32 of them per group: below 2^22 units, so the FP32 tensor-core
+// A complex real part sums 2 x 64 of them per group: at most 2^23 units, so the FP32 tensor-core
 // accumulator holds the level-0 (i = j = 0) group sum exactly, whatever order or truncation it
 // uses inside. The level-1..3 products (i + j = 1..3; the terms i + j >= 4 fall below 2^-32 and
 // are dropped) go to a second accumulator; they are 2^-8 smaller, so its FP32 rounding sits near

@@ -59,3 +59,27 @@ def test_tc_mft_inverse(ctx, m, n, npix, prec):
         err = rel_l2(y[b], propagation.imft(f[b], npix, n, du[b]))
         print(f"prec {prec} m {m} n {n} item {b}: rel L2 {err:.3e}")
         assert err < TOL[prec]
+
+
+def test_ext_mft_degenerate_inputs(ctx):
+    """Extended precision on inputs that stress its per-group scaling: an all-zero field (every
+    scaling group empty) gives exact zeros; a centred impulse gives the constant s * v exactly
+    (X_j = 0 there, every basis entry 1); a field whose rows span twelve decades keeps the
+    oracle's answer to the complex64 rounding of the output."""
+    n, npix, m, du = 96, 80, 40, 0.3
+    z = torch.zeros((1, n, n), dtype=torch.complex64, device="cuda")
+    y = coro.propagate_mft(ctx, z, npix, -1, m, [du], coro.MFT_EXT)
+    assert torch.count_nonzero(y).item() == 0
+    v = 0.7 - 0.2j
+    f = np.zeros((1, n, n), np.complex64)
+    f[0, n // 2, n // 2] = v
+    y = coro.propagate_mft(ctx, torch.from_numpy(f).cuda(), npix, -1, m, [du], coro.MFT_EXT).cpu().numpy()
+    expect = np.complex64(complex(np.complex64(v)) * du / npix)
+    assert np.max(np.abs(y - expect)) <= 2.0 ** -23 * abs(expect)
+    g = inputs.random_field((1, n, n), seed=77)
+    g = g * (10.0 ** np.linspace(-6, 6, n))[None, :, None]
+    x = torch.from_numpy(g.astype(np.complex64)).cuda()
+    y = coro.propagate_mft(ctx, x, npix, -1, m, [du], coro.MFT_EXT).cpu().numpy()
+    err = rel_l2(y[0], propagation.mft(g[0].astype(np.complex64).astype(np.complex128), npix, m, du))
+    print(f"EXT twelve-decade rows: rel L2 {err:.3e}")
+    assert err < TOL[coro.MFT_EXT]
