@@ -41,7 +41,7 @@ template <int BN> struct TcxCfg {
     static constexpr int W_BYTES = TCX_W_PLANES * WPLANE_BYTES;
     static constexpr int STAGE_BYTES = X_BYTES + W_BYTES;
     static constexpr int STAGES = BN == 64 ? 4 : 5;
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + 1024 /*maxima*/;
     static constexpr int EPI_COLS = BN / 4;                       // complex columns per epilogue warp
     static constexpr uint32_t ACC_COLS = 2 * BN;                  // one accumulator: Re | Im
     static constexpr uint32_t TMEM_COLS = 4 * ACC_COLS;           // 2 buffers x 2 levels
@@ -147,17 +147,42 @@ __device__ __forceinline__ void load_sliced(const __nv_bfloat16* base, size_t pl
     l += s3;
 }
 
+// One tile of the persistent walk: its item, origin and K groups (all warps derive the same).
+struct TcxTile {
+    int b, m0, n0, g0, ngroups;
+    bool live;                                       // false: outside its item's M x N
+};
+
+template <int BN, int EPI>
+__device__ __forceinline__ TcxTile tcx_tile(const TcArgs& a, int t, int tiles_n, int tiles_m) {
+    TcxTile tl;
+    tl.b = t / (tiles_n * tiles_m);
+    const int r = t % (tiles_n * tiles_m);
+    tl.m0 = (r / tiles_n) * BM;
+    tl.n0 = (r % tiles_n) * BN;
+    const TcItem& it = a.items[tl.b];
+    tl.live = tl.m0 < it.M && tl.n0 < it.N;
+    tl.g0 = 0;
+    tl.ngroups = (it.K + GROUP - 1) / GROUP;
+    if (tl.live) tile_k_range<BM, BN>(it, tl.m0, tl.n0, GROUP, EPI == TC_EPI_SPLITT || EPI == TC_EPI_BABINET, tl.g0, tl.ngroups);
+    else tl.ngroups = 0;
+    return tl;
+}
+
+// Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the tiles_n x
+// tiles_m x batch grid (column tiles fastest, so neighbouring CTAs share X rows). The TMA, MMA
+// and epilogue warps follow the same walk with running stage / group counters, so the MMAs of
+// the next tile start as soon as the epilogue has drained the last group of the current one,
+// while the epilogue is still finishing that tile's outputs.
 template <int BN, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
-tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw, const TcArgs a) {
+tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw, const TcArgs a,
+                 int tiles_n, int tiles_m, int batch) {
     using Cfg = TcxCfg<BN>;
     constexpr int STAGES = Cfg::STAGES, STAGE_BYTES = Cfg::STAGE_BYTES, WPLANE_BYTES = Cfg::WPLANE_BYTES;
     constexpr int EPI_COLS = Cfg::EPI_COLS;
     constexpr uint32_t ACC = Cfg::ACC_COLS, TMEM_COLS = Cfg::TMEM_COLS;
-    const int b = blockIdx.z;
-    const TcItem it = a.items[b];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    if (m0 >= it.M || n0 >= it.N) return;            // uniform: uneven items skip empty tiles
+    const int total = tiles_n * tiles_m * batch;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -166,11 +191,9 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
     uint64_t* tfull = empty + STAGES;                // accumulator buffer holds a finished group
     uint64_t* tempty = tfull + 2;                    // accumulator buffer has been drained
     uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint32_t* xmax = reinterpret_cast<uint32_t*>(smem + STAGES * STAGE_BYTES + 256);   // [16][EPI_COLS]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int g0 = 0, ngroups = (it.K + GROUP - 1) / GROUP;
-    tile_k_range<BM, BN>(it, m0, n0, GROUP, EPI == TC_EPI_SPLITT || EPI == TC_EPI_BABINET, g0, ngroups);
-    const int nsteps = STEPS_PER_GROUP * ngroups;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
@@ -190,27 +213,39 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int k = 0; k < nsteps; ++k) {
-                const int s = k % STAGES;
-                const uint32_t ph = (k / STAGES) & 1;
-                if (!tc::mbar_wait(&empty[s], ph ^ 1, a.err, 11)) break;
-                unsigned char* st = smem + s * STAGE_BYTES;
-                const int kx = g0 * GROUP + k * KSTEP;
-                tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                tc::tma_load_4d(st, &mx, &full[s], kx, m0, 0, it.x_idx);
-                tc::tma_load_4d(st + X_BYTES, &mw, &full[s], kx, n0, 0, it.w_idx);
+            long long kk = 0;                                    // running stage counter
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const TcxTile tl = tcx_tile<BN, EPI>(a, t, tiles_n, tiles_m);
+                const TcItem& it = a.items[tl.b];
+                const int nsteps = STEPS_PER_GROUP * tl.ngroups;
+                for (int k = 0; k < nsteps; ++k, ++kk) {
+                    const int s = (int)(kk % STAGES);
+                    const uint32_t ph = (uint32_t)(kk / STAGES) & 1;
+                    if (!(ok = tc::mbar_wait(&empty[s], ph ^ 1, a.err, 11))) break;
+                    unsigned char* st = smem + s * STAGE_BYTES;
+                    const int kx = tl.g0 * GROUP + k * KSTEP;
+                    tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    tc::tma_load_4d(st, &mx, &full[s], kx, tl.m0, 0, it.x_idx);
+                    tc::tma_load_4d(st + X_BYTES, &mw, &full[s], kx, tl.n0, 0, it.w_idx);
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t ID = tc::idesc<true>(BM, 2 * BN, false);
             bool ok = true;
-            for (int k = 0; k < nsteps && ok; ++k) {
-                const int s = k % STAGES;
-                const uint32_t ph = (k / STAGES) & 1;
-                const int g = k / STEPS_PER_GROUP, buf = g & 1, half = k % STEPS_PER_GROUP;
+            long long kk = 0, gg = 0;                            // running stage / group counters
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            const TcxTile tl = tcx_tile<BN, EPI>(a, t, tiles_n, tiles_m);
+            const int nsteps = STEPS_PER_GROUP * tl.ngroups;
+            for (int k = 0; k < nsteps && ok; ++k, ++kk) {
+                const int s = (int)(kk % STAGES);
+                const uint32_t ph = (uint32_t)(kk / STAGES) & 1;
+                const long long g = gg + k / STEPS_PER_GROUP;
+                const int buf = (int)(g & 1), half = k % STEPS_PER_GROUP;
                 if (half == 0) {
-                    if (!(ok = tc::mbar_wait(&tempty[buf], ((g >> 1) & 1) ^ 1, a.err, 14))) break;
+                    if (!(ok = tc::mbar_wait(&tempty[buf], (uint32_t)((g >> 1) & 1) ^ 1, a.err, 14))) break;
                     tc::tc_fence_after();
                 }
                 if (!(ok = tc::mbar_wait(&full[s], ph, a.err, 12))) break;
@@ -244,21 +279,32 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
                 tc::umma_commit(&empty[s]);             // frees the stage once these MMAs retire
                 if (half == STEPS_PER_GROUP - 1 || k == nsteps - 1) tc::umma_commit(&tfull[buf]);
             }
+            gg += tl.ngroups;
+            }
         }
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..17)
         const int q = warp & 3;                          // TMEM lane quarter this warp may read
         const int cg = (warp - 2) >> 2;                  // which quarter of the tile's complex columns
         const int row = q * 32 + lane;
-        const int m = m0 + row;
         const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16) + cg * EPI_COLS;
+        bool ok = true;
+        long long gg = 0;                                // running group counter
+        // every epilogue warp walks every tile even after a wait has failed (ok = false: no
+        // further waits or stores), so that the partner warps always meet at their barriers
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const TcxTile tl = tcx_tile<BN, EPI>(a, t, tiles_n, tiles_m);
+        if (!tl.live) continue;
+        const int b = tl.b, m0 = tl.m0, n0 = tl.n0;
+        const TcItem it = a.items[b];
+        const int m = m0 + row;
         float hr[EPI_COLS], lr[EPI_COLS], hi_[EPI_COLS], li[EPI_COLS];
 #pragma unroll
         for (int j = 0; j < EPI_COLS; ++j) { hr[j] = 0.f; lr[j] = 0.f; hi_[j] = 0.f; li[j] = 0.f; }
-        bool ok = true;
-        for (int g = 0; g < ngroups; ++g) {
-            const int buf = g & 1;
-            if (!(ok = tc::mbar_wait(&tfull[buf], (g >> 1) & 1, a.err, 13))) break;
+        for (int gl = 0; gl < tl.ngroups; ++gl) {
+            const long long g = gg + gl;
+            const int buf = (int)(g & 1);
+            if (!ok || !(ok = tc::mbar_wait(&tfull[buf], (uint32_t)(g >> 1) & 1, a.err, 13))) break;
             __syncwarp();
             tc::tc_fence_after();
             // eight columns at a time, level 0 and levels 1-3 of the same outputs; BATCH such
@@ -297,6 +343,7 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
                 }
             }
         }
+        gg += tl.ngroups;
         // scale: Y * scale64 in two-float
         const float sh = (float)it.scale64, sl = (float)(it.scale64 - (double)sh);
 #pragma unroll
@@ -311,7 +358,6 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
             // pass 1: the output values (Babinet subtraction, mask) in place, and this warp's
             // largest magnitude per column; the 64 rows m0 + 64 h ... + 63 of a scaling group
             // (the next GEMM's K elements) belong to warps q = 2h and 2h + 1 of the same column group
-            uint32_t* xmax = reinterpret_cast<uint32_t*>(smem);   // stage memory: every MMA has retired
             const int ew = warp - 2;
 #pragma unroll
             for (int j = 0; j < EPI_COLS; ++j) {
@@ -346,7 +392,8 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
                 if (lane == 0) xmax[ew * EPI_COLS + j] = wm;
             }
             // the two warps of each scaling group meet at their own named barrier (ids 1-8)
-            asm volatile("bar.sync %0, 64;" ::"r"(1 + cg * 2 + (q >> 1)) : "memory");
+            const int pair_bar = 1 + cg * 2 + (q >> 1);
+            asm volatile("bar.sync %0, 64;" ::"r"(pair_bar) : "memory");
             // epilogue warp w = 4 cg + i has TMEM lane quarter q = (i + 2) & 3 (warp = w + 2)
             const int partner = 4 * cg + (((q ^ 1) + 2) & 3);
 #pragma unroll
@@ -364,6 +411,8 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
                     if (a.c64) a.c64[b * a.c64_bstride + (size_t)n * a.c64_ld + m] = make_float2(hr[j] + lr[j], hi_[j] + li[j]);
                 }
             }
+            // both warps have read the pair's maxima before either writes the next tile's
+            asm volatile("bar.sync %0, 64;" ::"r"(pair_bar) : "memory");
         } else if constexpr (EPI == TC_EPI_C64T) {
             if (ok && m < it.M) {
 #pragma unroll
@@ -429,6 +478,7 @@ tcx_cgemm_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__
             if (lane == 0 && a.peak64)
                 atomicMax(reinterpret_cast<unsigned long long*>(a.peak64) + b, (unsigned long long)__double_as_longlong(pk));
         }
+        }                                                // tiles
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -520,8 +570,18 @@ cudaError_t launch_t(const CUtensorMap& mx, const CUtensorMap& mw, int max_m, in
         if (e != cudaSuccess) return e;
         attr_done = dev;
     }
-    dim3 grid((max_n + BN - 1) / BN, (max_m + BM - 1) / BM, batch);
-    tcx_cgemm_kernel<BN, EPI><<<grid, THREADS, SMEM, stream>>>(mx, mw, args);
+    static int sms[64] = {};
+    if (dev >= 0 && dev < 64 && sms[dev] == 0) {
+        cudaError_t e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    const int tiles_n = (max_n + BN - 1) / BN, tiles_m = (max_m + BM - 1) / BM;
+    const long long total = (long long)tiles_n * tiles_m * batch;
+    if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const int per_sm = (dev >= 0 && dev < 64) ? sms[dev] : 148;
+    const int grid = total < per_sm ? (int)total : per_sm;
+    if (grid == 0) return cudaSuccess;
+    tcx_cgemm_kernel<BN, EPI><<<grid, THREADS, SMEM, stream>>>(mx, mw, args, tiles_n, tiles_m, batch);
     return cudaGetLastError();
 }
 
