@@ -290,7 +290,9 @@ coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent
 /* (*persistent 6: mixed-radix kernels for n not a power of two; 7: the packed-pair kernels of
  * the alternating layout, below; 8: quad kernel, four-column strips (whole 32-byte sectors)
  * as two packed pairs, streamed by TMA in quarter strips, exchanges in swizzled shared
- * memory of exactly N slots per pair.) */
+ * memory of exactly N slots per pair; 9: mixed-radix packed-pair kernels, two lines per block
+ * in packed FP32x2 arithmetic with the radix plan fixed at compile time, in place in one
+ * shared buffer, for the lengths built in (1400, 2800).) */
 /* Radix sequence of pass i's line transforms (the FFT factorisation the chosen kernel runs):
  * radices[0 .. min(*stages, max_radices) - 1], *stages the number of stages (radices may be
  * NULL when max_radices is 0). Register-resident engines: radix 16 while it divides, the
@@ -301,10 +303,13 @@ coro_status coro_fresnel_plan_pass_radix(coro_plan plan, int i, int* radices, in
 /* Override the tuned kernel choice of every pass of a complex64 plan.
  *   row_variant: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row
  *                pairs, 5 the shared-memory engine with radix 8 (2, 3 and 5: N = 1024 ...
- *                4096).
+ *                4096); at mixed-radix N: 0 the shared-memory engine, 6 the packed-pair
+ *                engine (N = 1400, 2800).
  *   col_lines:   columns per block (a width the plan's N supports), -1 persistent TMA,
  *                -2 unit-pipelined, -3 packed column pairs, -4 wide, -7 quad, -8 the
- *                shared-memory engine with radix 8 (-2 to -8: N = 1024 ... 4096), 0 default.
+ *                shared-memory engine with radix 8 (-2 to -8: N = 1024 ... 4096), 0 default;
+ *                at mixed-radix N: columns per block of the shared-memory engine, or -5 the
+ *                packed-pair engine (N = 1400, 2800).
  * Values the plan's N does not offer are rejected with CORO_EINVAL and nothing changes.
  * Every choice gives the same result up to FP32 rounding order (used to test each kernel). */
 coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, int col_lines);

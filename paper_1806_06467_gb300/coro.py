@@ -572,7 +572,8 @@ class FresnelPlan:
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_pass_kernel(self.handle, i, ct.byref(p), ct.byref(w)))
         row, _ = self.pass_info(i)
         kind = "row_pass" if row else "col_pass"
-        name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide", "", "_mixed", "_pair_t", "_quad")[p.value]
+        name = kind + ("_kernel", "_persistent", "_units", "_pair", "_wide", "", "_mixed", "_pair_t", "_quad",
+                              "_mixed_pair")[p.value]
         if p.value == 6 and self.n & (self.n - 1) == 0:
             name += "_r8"                               # the shared-memory engine at radix 8
         return f"{name}<{self.n}>" if row else f"{name}<{self.n},{w.value}>"
@@ -585,9 +586,10 @@ class FresnelPlan:
 
     def set_pass_kernel(self, row_variant: int, col_lines: int) -> None:
         """Override the tuned kernels (row: 0 persistent, 1 per-group, 2 units, 3 packed row
-        pairs, 5 shared-memory radix-8 engine; column: lines per block, -1 persistent TMA,
-        -2 units, -3 packed column pairs, -4 wide four-column groups, -7 quad four-column
-        strips, -8 shared-memory radix-8 engine, 0 default)."""
+        pairs, 5 shared-memory radix-8 engine, 6 packed-pair mixed-radix engine; column: lines
+        per block, -1 persistent TMA, -2 units, -3 packed column pairs, -4 wide four-column
+        groups, -5 packed-pair mixed-radix engine, -7 quad four-column strips, -8 shared-memory
+        radix-8 engine, 0 default)."""
         self.ctx.lib.check(self.ctx.lib.coro_fresnel_plan_set_pass_kernel(self.handle, row_variant, col_lines))
 
     def set_layout(self, transposed: bool) -> None:

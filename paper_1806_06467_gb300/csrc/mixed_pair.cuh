@@ -1,0 +1,359 @@
+// mixed_pair.cuh -- mixed-radix line transforms on packed line pairs, the radix plan fixed at
+// compile time (N = 2800 of Sec. 3.1, and 1400).
+//
+// The Stockham stages of mixed.cuh (stage s of radix R, NS = the product of the earlier radices:
+// butterfly j reads x[j + r N/R], multiplies by W_{NS R}^{r (j mod NS)}, takes an R-point DFT and
+// writes position (j / NS) NS R + j mod NS + r NS), on two lines at once in packed FP32x2
+// arithmetic (fft_pair.cuh: lane 0 holds line A, lane 1 line B, every add / mul / fma issues once
+// for both). With N a template parameter every stage's radix, span and butterfly count are
+// compile-time constants, so there is no run-time division and the butterfly loops unroll; and
+// each thread keeps its K = ceil((N/R) / T) butterflies of a stage in registers between a read
+// phase and a write phase, so one buffer of N pair slots serves every stage in place (two block
+// barriers per stage) and two blocks fit on an SM. Radices: 16, 8, 4, 2 (the engine's
+// butterflies) and odd primes up to 13 (the pair-sum DFT of mixed.cuh); lengths with a larger
+// prime factor keep the shared-memory engine of mixed.cuh.
+#pragma once
+#include "fft_pair.cuh"
+#include "mixed.cuh"
+
+namespace coro {
+namespace mpair {
+
+using pk::CP;
+using pk::u64;
+
+constexpr int kMaxOddRadix = 13;
+
+// Threads per line pair: the smallest divisor of n from 256 to 320 (every thread then holds
+// exactly n / T samples of the pair between the transforms: 280 at 1400 and 2800), else 256.
+__host__ __device__ constexpr int pair_threads(int n) {
+    for (int t = 256; t <= 320; ++t)
+        if (n % t == 0) return t;
+    return 256;
+}
+
+struct PairPlan {
+    int stages = 0;                                // -1: not a length this engine takes
+    int radix[kMixedMaxStages] = {};
+};
+
+// The radix sequence of mixed_plan (16s, then one of 8 / 4 / 2, then odd primes ascending),
+// restricted to odd primes up to kMaxOddRadix.
+__host__ __device__ constexpr PairPlan pair_plan(int n) {
+    PairPlan p{};
+    if (n < 16 || (n & 1)) {
+        p.stages = -1;
+        return p;
+    }
+    int m = n;
+    while (m % 16 == 0 && p.stages < kMixedMaxStages) {
+        p.radix[p.stages++] = 16;
+        m /= 16;
+    }
+    if (m % 8 == 0) {
+        p.radix[p.stages++] = 8;
+        m /= 8;
+    } else if (m % 4 == 0) {
+        p.radix[p.stages++] = 4;
+        m /= 4;
+    } else if (m % 2 == 0) {
+        p.radix[p.stages++] = 2;
+        m /= 2;
+    }
+    for (int q = 3; q <= kMaxOddRadix && m > 1; q += 2)
+        while (m % q == 0 && p.stages < kMixedMaxStages) {
+            p.radix[p.stages++] = q;
+            m /= q;
+        }
+    if (m != 1) p.stages = -1;
+    return p;
+}
+
+// Shared bytes of one line pair (N pair slots at mpad positions).
+__host__ __device__ constexpr size_t pair_smem(int n) { return (size_t)(mpad(n) + 1) * sizeof(CP); }
+
+// Odd R-point DFT of a packed pair, natural order in and out, from the pair sums
+// s_b = u_b + u_{R-b} and differences d_b = u_b - u_{R-b} (as odd_dft in mixed.cuh):
+// re_a = u_0 + sum_b s_b cos(2 pi ab/R), im_a = sum_b d_b sin(2 pi ab/R); forward
+// out[a] = re_a - i im_a, out[R-a] = re_a + i im_a, signs swapped for the inverse.
+// cs[m], sn[m], ns[m] = cos, sin, -sin of 2 pi m / R on both lanes, m = 0 ... (R-1)/2.
+template <int R, bool INV>
+__device__ __forceinline__ void odd_dftp(CP (&u)[R], const u64* cs, const u64* sn, const u64* ns) {
+    constexpr int H = (R - 1) / 2;
+    CP sm[H + 1], df[H + 1];
+    CP o0 = u[0];
+#pragma unroll
+    for (int b = 1; b <= H; ++b) {
+        sm[b] = pk::cadd(u[b], u[R - b]);
+        df[b] = pk::csub(u[b], u[R - b]);
+        o0 = pk::cadd(o0, sm[b]);
+    }
+#pragma unroll
+    for (int a = 1; a <= H; ++a) {
+        CP re = u[0];
+        CP im{0ull, 0ull};
+#pragma unroll
+        for (int b = 1; b <= H; ++b) {
+            const int m = (a * b) % R;
+            const u64 c = m <= H ? cs[m] : cs[R - m];
+            const u64 s = m <= H ? sn[m] : ns[R - m];
+            re.re = pk::fma2(sm[b].re, c, re.re);
+            re.im = pk::fma2(sm[b].im, c, re.im);
+            im.re = pk::fma2(df[b].re, s, im.re);
+            im.im = pk::fma2(df[b].im, s, im.im);
+        }
+        // -i im = (im.im, -im.re)
+        const CP p{pk::add2(re.re, im.im), pk::sub2(re.im, im.re)};
+        const CP q{pk::sub2(re.re, im.im), pk::add2(re.im, im.re)};
+        u[a] = INV ? q : p;
+        u[R - a] = INV ? p : q;
+    }
+    u[0] = o0;
+}
+
+// One in-place Stockham stage over the line pair in buf (every thread of the block calls it
+// after a barrier that made buf complete; it ends with one). lin: the linear table W_N^m.
+template <int N, int T, int R, int NS, bool INV>
+__device__ __forceinline__ void pair_stage(CP* buf, int tid, const float2* __restrict__ lin) {
+    constexpr int NB = N / R;                       // butterflies
+    constexpr int K = (NB + T - 1) / T;             // per thread
+    constexpr bool FULL = NB % T == 0;
+    constexpr int STEP = N / (NS * R);              // W_{NS R}^e = W_N^(e STEP)
+    CP u[K][R];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int j = tid + i * T;
+        if (FULL || j < NB) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[i][r] = buf[mpad(j + r * NB)];
+        }
+    }
+    __syncthreads();
+    constexpr int H = R % 2 ? (R - 1) / 2 + 1 : 1;
+    u64 cs[H], sn[H], ns[H];
+    if constexpr (R % 2 == 1) {
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            const float2 w = __ldg(lin + m * (N / R));     // cos - i sin of 2 pi m / R
+            cs[m] = pk::pack(w.x, w.x);
+            sn[m] = pk::pack(-w.y, -w.y);
+            ns[m] = pk::pack(w.y, w.y);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int j = tid + i * T;
+        if (FULL || j < NB) {
+            const int k = j % NS;
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    u64 wr, wi;
+                    pk::load_tw(lin + r * k * STEP, wr, wi);
+                    u[i][r] = pk::cmul_b<INV>(u[i][r], wr, wi);
+                }
+            }
+            if constexpr (R % 2 == 1) odd_dftp<R, INV>(u[i], cs, sn, ns);
+            else pk::dftp<R, INV>(u[i]);
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[mpad(base + r * NS)] = u[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+// N-point DFT of the line pair in buf, natural order in and out.
+template <int N, int T, bool INV, int S = 0, int NS = 1>
+__device__ __forceinline__ void pair_fft(CP* buf, int tid, const float2* __restrict__ lin) {
+    constexpr PairPlan P = pair_plan(N);
+    static_assert(P.stages > 0, "a length of the packed-pair mixed engine");
+    if constexpr (S < P.stages) {
+        constexpr int R = P.radix[S];
+        pair_stage<N, T, R, NS, INV>(buf, tid, lin);
+        pair_fft<N, T, INV, S + 1, NS * R>(buf, tid, lin);
+    }
+}
+
+}  // namespace mpair
+
+// grid (N / 2, batch): one block per row pair (rows 2 blockIdx.x and 2 blockIdx.x + 1, packed
+// as lanes 0 / 1); a.tw is the linear table of N. Elements are evaluated per row and sample
+// (apply_elems_n, as in the one-line engines) between the inverse and the forward transform.
+template <int N, int T>
+__global__ void __launch_bounds__(T, 2)
+row_pass_mixed_pair_kernel(const __grid_constant__ RowArgs<float2> a) {
+    using mpair::CP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CP* buf = reinterpret_cast<CP*>(smem_raw);
+    constexpr int S = (N + T - 1) / T;
+    const int ya = 2 * blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+    const size_t ra = ((size_t)b * N + ya) * N, rb = ra + N;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int x = tid + s * T;
+        if (S * T == N || x < N) {
+            float2 va = make_float2(1.f, 0.f), vb = va;
+            if (!(a.flags & RF_INIT_ONE)) {
+                va = a.in[ra + x];
+                vb = a.in[rb + x];
+            }
+            buf[mpad(x)] = CP{pk::pack(va.x, vb.x), pk::pack(va.y, vb.y)};
+        }
+    }
+    __syncthreads();
+    if (a.flags & RF_INV_FIRST) mpair::pair_fft<N, T, true>(buf, tid, a.tw);
+    if (a.elems.count) {
+        if constexpr (S * T == N) {
+            // every thread holds S samples of both rows: one call per row, so that the
+            // element loads (OPD maps) of all S samples are in flight at once
+            const float pre[S] = {};
+            float2 pa[S], pb[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const CP v = buf[mpad(tid + s * T)];
+                pk::unpack(v.re, pa[s].x, pb[s].x);
+                pk::unpack(v.im, pa[s].y, pb[s].y);
+            }
+            apply_elems_n<float2, T, S>(pa, tid, ya, b, N, a.elems, pre, -1);
+            apply_elems_n<float2, T, S>(pb, tid, ya + 1, b, N, a.elems, pre, -1);
+#pragma unroll
+            for (int s = 0; s < S; ++s) buf[mpad(tid + s * T)] = CP{pk::pack(pa[s].x, pb[s].x), pk::pack(pa[s].y, pb[s].y)};
+        } else {
+            const float pre1[1] = {0.f};
+#pragma unroll 1
+            for (int s = 0; s < S; ++s) {
+                const int x = tid + s * T;
+                if (x < N) {
+                    const CP v = buf[mpad(x)];
+                    float2 pa[1], pb[1];
+                    pk::unpack(v.re, pa[0].x, pb[0].x);
+                    pk::unpack(v.im, pa[0].y, pb[0].y);
+                    apply_elems_n<float2, 1, 1>(pa, x, ya, b, N, a.elems, pre1, -1);
+                    apply_elems_n<float2, 1, 1>(pb, x, ya + 1, b, N, a.elems, pre1, -1);
+                    buf[mpad(x)] = CP{pk::pack(pa[0].x, pb[0].x), pk::pack(pa[0].y, pb[0].y)};
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (a.flags & RF_FWD_AFTER) mpair::pair_fft<N, T, false>(buf, tid, a.tw);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int x = tid + s * T;
+        if (S * T == N || x < N) {
+            const CP v = buf[mpad(x)];
+            float2 va, vb;
+            pk::unpack(v.re, va.x, vb.x);
+            pk::unpack(v.im, va.y, vb.y);
+            a.out[ra + x] = va;
+            a.out[rb + x] = vb;
+        }
+    }
+}
+
+// grid (N / 2, batch): one block per column pair (columns 2 blockIdx.x, 2 blockIdx.x + 1: one
+// 16-byte segment per row); tab_y multiplies between the transforms, tab_x (per column, which
+// commutes with the column transforms) after them.
+template <int N, int T>
+__global__ void __launch_bounds__(T, 2)
+col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a) {
+    using mpair::CP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CP* buf = reinterpret_cast<CP*>(smem_raw);
+    constexpr int S = (N + T - 1) / T;
+    constexpr size_t ROW4 = N / 2;                  // float4 per row
+    const int col = 2 * blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+    const float4* src = reinterpret_cast<const float4*>(a.in + (size_t)b * N * N + col);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int y = tid + s * T;
+        if (S * T == N || y < N) {
+            const float4 q = src[(size_t)y * ROW4];              // (re_A, im_A, re_B, im_B)
+            buf[mpad(y)] = CP{pk::pack(q.x, q.z), pk::pack(q.y, q.w)};
+        }
+    }
+    __syncthreads();
+    if (a.flags & CF_FWD) mpair::pair_fft<N, T, false>(buf, tid, a.tw);
+    if (a.flags & CF_TABLE) {
+        const float2* ty = a.tab_y + (size_t)b * N;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int y = tid + s * T;
+            if (S * T == N || y < N) {
+                const float2 h = ty[y];
+                buf[mpad(y)] = pk::cmul_b<false>(buf[mpad(y)], pk::pack(h.x, h.x), pk::pack(h.y, h.y));
+            }
+        }
+        __syncthreads();
+    }
+    if (a.flags & CF_INV) mpair::pair_fft<N, T, true>(buf, tid, a.tw);
+    pk::u64 hr = pk::pack(1.f, 1.f), hi = 0ull;
+    if (a.flags & CF_TABLE) {
+        const float2 ha = a.tab_x[(size_t)b * N + col], hb = a.tab_x[(size_t)b * N + col + 1];
+        hr = pk::pack(ha.x, hb.x);
+        hi = pk::pack(ha.y, hb.y);
+    }
+    float4* dst = reinterpret_cast<float4*>(a.out + (size_t)b * N * N + col);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int y = tid + s * T;
+        if (S * T == N || y < N) {
+            CP v = buf[mpad(y)];
+            if (a.flags & CF_TABLE)
+                v = CP{pk::sub2(pk::mul2(v.re, hr), pk::mul2(v.im, hi)), pk::fma2(v.re, hi, pk::mul2(v.im, hr))};
+            float4 q;
+            pk::unpack(v.re, q.x, q.z);
+            pk::unpack(v.im, q.y, q.w);
+            dst[(size_t)y * ROW4] = q;
+        }
+    }
+}
+
+// Whether the packed-pair engine has an instance for complex64 lines of length n.
+inline bool mixed_pair_length(int n) { return n == 1400 || n == 2800; }
+
+namespace detail {
+
+template <int N>
+cudaError_t row_launch_mixed_pair_n(const RowArgs<float2>& a, const PassLaunch& l) {
+    constexpr int T = mpair::pair_threads(N);
+    const size_t smem = mpair::pair_smem(N);
+    static unsigned done = 0;
+    cudaError_t e = ensure_smem(row_pass_mixed_pair_kernel<N, T>, smem, done);
+    if (e != cudaSuccess) return e;
+    row_pass_mixed_pair_kernel<N, T><<<dim3(N / 2, l.batch), T, smem, l.stream>>>(a);
+    return cudaGetLastError();
+}
+
+// The 16-byte row segments need 16-byte aligned planes (checked on the host).
+template <int N>
+cudaError_t col_launch_mixed_pair_n(const ColArgs<float2>& a, const PassLaunch& l) {
+    constexpr int T = mpair::pair_threads(N);
+    if (((uintptr_t)a.in & 15) || ((uintptr_t)a.out & 15)) return cudaErrorInvalidValue;
+    const size_t smem = mpair::pair_smem(N);
+    static unsigned done = 0;
+    cudaError_t e = ensure_smem(col_pass_mixed_pair_kernel<N, T>, smem, done);
+    if (e != cudaSuccess) return e;
+    col_pass_mixed_pair_kernel<N, T><<<dim3(N / 2, l.batch), T, smem, l.stream>>>(a);
+    return cudaGetLastError();
+}
+
+inline cudaError_t row_launch_mixed_pair(int n, const RowArgs<float2>& a, const PassLaunch& l) {
+    switch (n) {
+        case 1400: return row_launch_mixed_pair_n<1400>(a, l);
+        case 2800: return row_launch_mixed_pair_n<2800>(a, l);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+inline cudaError_t col_launch_mixed_pair(int n, const ColArgs<float2>& a, const PassLaunch& l) {
+    switch (n) {
+        case 1400: return col_launch_mixed_pair_n<1400>(a, l);
+        case 2800: return col_launch_mixed_pair_n<2800>(a, l);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace detail
+}  // namespace coro

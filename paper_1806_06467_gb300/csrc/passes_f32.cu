@@ -1,6 +1,7 @@
 // passes_f32.cu -- complex64 row/column pass launchers (N = 32 ... 8192).
 #include "passes_launch.cuh"
 #include "mixed.cuh"
+#include "mixed_pair.cuh"
 
 namespace coro {
 
@@ -34,7 +35,9 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
             if (l.variant == 2) return row_launch_units<float2, 4096, 4, 2>(a, l);
             return l.variant == 1 ? row_launch<float2, 4096>(a, l) : row_launch_persistent<float2, 4096>(a, l);
         case 8192: return l.variant == 1 ? row_launch<float2, 8192>(a, l) : row_launch_persistent<float2, 8192>(a, l);
-        default: return row_launch_mixed<float2>(n, a, l);
+        default:
+            if (l.variant == 6 && mixed_pair_length(n)) return row_launch_mixed_pair(n, a, l);
+            return row_launch_mixed<float2>(n, a, l);
     }
 }
 
@@ -45,7 +48,8 @@ cudaError_t launch_row_pass<float2>(int n, const RowArgs<float2>& a, const PassL
 // packed-pair kernel writing its result transposed to a separate plane (row variant 4 reads it),
 // -7 = quad kernel (four columns as two packed pairs, whole-sector strips, swizzled exchanges),
 // -8 = the shared-memory Stockham engine of mixed.cuh with radix 8 (N = 8^k x 2 or 4): the
-// alternative factorisation of the power-of-two lengths.
+// alternative factorisation of the power-of-two lengths; mixed-radix lengths: columns per block
+// of the shared-memory engine, or -5 = the packed-pair engine of mixed_pair.cuh (its lengths).
 template <>
 cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, const PassLaunch& l) {
     using namespace detail;
@@ -84,7 +88,9 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
             if (lines == -1) return col_launch_persistent<float2, 4096, 2>(a, l);
             return lines == 2 ? col_launch<float2, 4096, 2>(a, l) : col_launch<float2, 4096, 4>(a, l);
         case 8192: return lines == 1 ? col_launch<float2, 8192, 1>(a, l) : col_launch<float2, 8192, 2>(a, l);
-        default: return col_launch_mixed<float2>(n, lines, a, l);
+        default:
+            if (lines == -5 && mixed_pair_length(n)) return col_launch_mixed_pair(n, a, l);
+            return col_launch_mixed<float2>(n, lines, a, l);
     }
 }
 
@@ -114,19 +120,22 @@ int col_candidates(int n, int* out) {
         case 4096: out[5] = -4; out[6] = -7; out[7] = -8; out[0] = 4; out[1] = 2; out[2] = -1; out[3] = -2; out[4] = -3; return 8;
         case 2048: out[5] = -4; out[6] = -7; out[7] = -8; out[0] = 8; out[1] = 4; out[2] = -1; out[3] = -2; out[4] = -3; return 8;
         case 1024: out[5] = -4; out[6] = -7; out[7] = -8; out[0] = 16; out[1] = 8; out[2] = -1; out[3] = -2; out[4] = -3; return 8;
-        default:                                            // mixed radix: widest fit, and half of it
+        default: {                                          // mixed radix: widest fit, and half of it
             out[0] = 0;
             if (!mixed_supported<float2>(n)) return 1;
             out[0] = mixed_col_lines<float2>(n);
-            if (out[0] < 2) return 1;
-            out[1] = out[0] / 2;
-            return 2;
+            int k = 1;
+            if (out[0] >= 2) out[k++] = out[0] / 2;
+            if (mixed_pair_length(n)) out[k++] = -5;    // packed pairs, compile-time radix plan
+            return k;
+        }
     }
 }
 
 // row variants: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row
 // pairs, 5 the shared-memory engine with radix 8 (4, packed row pairs read from a transposed
-// plane, is only paired with column lines -6 and is not a tuning candidate)
+// plane, is only paired with column lines -6 and is not a tuning candidate); mixed-radix
+// lengths: 0 the shared-memory engine, 6 the packed-pair engine (its lengths)
 int row_variant_count(int n) { return (n >= 1024 && n <= 4096) ? 4 : n == 8192 ? 2 : 1; }
 
 int row_candidates(int n, int* out) {
@@ -134,6 +143,10 @@ int row_candidates(int n, int* out) {
     for (int v = 0; v < k; ++v) out[v] = v;
     if (n >= 1024 && n <= 4096 && !(n & (n - 1))) {
         out[k] = 5;
+        return k + 1;
+    }
+    if (mixed_pair_length(n)) {
+        out[k] = 6;
         return k + 1;
     }
     return k;
@@ -165,6 +178,11 @@ bool mixed_length_ok(int n, bool dbl) { return dbl ? mixed_supported<double2>(n)
 
 void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persistent, int* out_lines) {
     int p = 0, w = 0;
+    if ((n & (n - 1)) && !dbl && mixed_pair_length(n) && (row ? variant == 6 : lines == -5)) {
+        if (persistent) *persistent = 9;                    // mixed-radix packed pairs
+        if (out_lines) *out_lines = row ? 1 : 2;
+        return;
+    }
     if (n & (n - 1)) {                                      // mixed-radix passes
         if (persistent) *persistent = 6;
         if (out_lines) *out_lines = row ? 1 : dbl ? mixed_col_lines<double2>(n) : lines > 0 ? lines : mixed_col_lines<float2>(n);

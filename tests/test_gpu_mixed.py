@@ -83,18 +83,48 @@ def test_relay_plan_2800(ctx):
             optics.circle_stop(n, dx, w.field_stop_frac * r)]
     ref = propagation.fresnel_chain(np.ones((n, n), complex), dx, lam, oels, list(w.distances()))
     assert rel_l2(x.cpu().numpy()[0], ref) < 1e-5
-    # both column widths the tuner chooses from: 4 columns per 1024-thread block (alone on its
-    # SM) and 2 per 512-thread block (two per SM)
-    widths = set()
-    for cl in (4, 2):
-        plan.set_pass_kernel(0, cl)
-        widths |= {plan.pass_kernel(i) for i in range(plan.launch_count) if "col_" in plan.pass_kernel(i)}
+    # every kernel the tuner chooses from: the shared-memory engine's column widths, 4 columns
+    # per 1024-thread block (alone on its SM) and 2 per 512-thread block (two per SM), and the
+    # packed-pair engine's row and column kernels (compile-time radix plan, in place)
+    kernels = set()
+    for rv, cl in ((0, 4), (0, 2), (6, -5), (6, 4), (0, -5)):
+        plan.set_pass_kernel(rv, cl)
+        kernels |= {plan.pass_kernel(i) for i in range(plan.launch_count)}
+        assert all(plan.pass_radix(i) == [16, 5, 5, 7] for i in range(plan.launch_count))
         x.fill_(float("nan"))
         plan.execute(x)
-        assert rel_l2(x.cpu().numpy()[0], ref) < 1e-5, cl
-    assert widths == {"col_pass_mixed<2800,4>", "col_pass_mixed<2800,2>"}
+        assert rel_l2(x.cpu().numpy()[0], ref) < 1e-5, (rv, cl)
+    assert kernels == {"col_pass_mixed<2800,4>", "col_pass_mixed<2800,2>", "row_pass_mixed<2800>",
+                       "col_pass_mixed_pair<2800,2>", "row_pass_mixed_pair<2800>"}
     with pytest.raises(coro.CoroError):
         plan.set_pass_kernel(0, 8)
+
+
+@pytest.mark.parametrize("n,npix", [(1400, 350), (2800, 700)])
+def test_mixed_pair_engine_direct_and_as_hops(ctx, n, npix):
+    """The packed-pair mixed-radix kernels (row variant 6, column kernel -5) on a direct hop
+    (forward-only column pass) and an angular-spectrum hop on two wavelengths, batch 2, against
+    the oracle; 1400 = 8 x 5 x 5 x 7 has a radix-8 stage, 2800 = 16 x 5 x 5 x 7 a radix-16 one."""
+    dx = 1.0 / npix
+    lams = np.array([500e-9, 600e-9])
+    els = [coro.element(coro.EL_APERTURE, plane=0, radius=0.5, obscuration=0.1, n_spiders=4, spider_width=0.02),
+           coro.element(coro.EL_LENS, plane=0, focal_length=10.0),
+           coro.element(coro.EL_CIRCLE, plane=1, radius=40e-6, flags=coro.ELF_OPAQUE_INSIDE)]
+    plan = coro.FresnelPlan(ctx, n=n, batch=2, pixelscale=dx, wavelength=lams, distances=[10.0, 0.05],
+                            methods=[coro.FRESNEL_DIRECT, coro.FRESNEL_AS], elements=els, init_uniform=True)
+    plan.set_pass_kernel(6, -5)
+    names = {plan.pass_kernel(i) for i in range(plan.launch_count)}
+    assert names == {f"row_pass_mixed_pair<{n}>", f"col_pass_mixed_pair<{n},2>"}
+    x = torch.empty((2, n, n), dtype=torch.complex64, device="cuda")
+    ps = plan.execute(x)
+    got = x.cpu().numpy()
+    for b in range(2):
+        e = optics.circular_aperture(n, dx, 0.5, 0.1, 4, 0.02) * optics.thin_lens(n, dx, lams[b], 10.0)
+        e, du = propagation.direct_fresnel(e, dx, lams[b], 10.0)
+        e = e * optics.circle_stop(n, du, 40e-6, opaque_inside=True)
+        e = propagation.angular_spectrum(e, du, lams[b], 0.05)
+        assert abs(ps[b] - du) < 1e-15 * du
+        assert rel_l2(got[b], e) < 1e-5
 
 
 def test_direct_hop_mixed_two_wavelengths(ctx):
