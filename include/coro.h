@@ -292,7 +292,7 @@ coro_status coro_fresnel_plan_pass_kernel(coro_plan plan, int i, int* persistent
  * as two packed pairs, streamed by TMA in quarter strips, exchanges in swizzled shared
  * memory of exactly N slots per pair; 9: mixed-radix packed-pair kernels, two lines per block
  * in packed FP32x2 arithmetic with the radix plan fixed at compile time, in place in one
- * shared buffer, for the lengths built in (1400, 2800).) */
+ * shared buffer, for the lengths built in (1400, 2800, 4100).) */
 /* Radix sequence of pass i's line transforms (the FFT factorisation the chosen kernel runs):
  * radices[0 .. min(*stages, max_radices) - 1], *stages the number of stages (radices may be
  * NULL when max_radices is 0). Register-resident engines: radix 16 while it divides, the
@@ -304,12 +304,12 @@ coro_status coro_fresnel_plan_pass_radix(coro_plan plan, int i, int* radices, in
  *   row_variant: 0 persistent, 1 one block per line group, 2 unit-pipelined, 3 packed row
  *                pairs, 5 the shared-memory engine with radix 8 (2, 3 and 5: N = 1024 ...
  *                4096); at mixed-radix N: 0 the shared-memory engine, 6 the packed-pair
- *                engine (N = 1400, 2800).
+ *                engine (N = 1400, 2800, 4100).
  *   col_lines:   columns per block (a width the plan's N supports), -1 persistent TMA,
  *                -2 unit-pipelined, -3 packed column pairs, -4 wide, -7 quad, -8 the
  *                shared-memory engine with radix 8 (-2 to -8: N = 1024 ... 4096), 0 default;
  *                at mixed-radix N: columns per block of the shared-memory engine, or -5 the
- *                packed-pair engine (N = 1400, 2800).
+ *                packed-pair engine (N = 1400, 2800, 4100).
  * Values the plan's N does not offer are rejected with CORO_EINVAL and nothing changes.
  * Every choice gives the same result up to FP32 rounding order (used to test each kernel). */
 coro_status coro_fresnel_plan_set_pass_kernel(coro_plan plan, int row_variant, int col_lines);

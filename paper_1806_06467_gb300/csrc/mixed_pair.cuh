@@ -1,5 +1,5 @@
 // mixed_pair.cuh -- mixed-radix line transforms on packed line pairs, the radix plan fixed at
-// compile time (N = 2800 of Sec. 3.1, and 1400).
+// compile time (N = 2800 of Sec. 3.1, N = 4100 = 4 x 1025 of App. B, and 1400).
 //
 // The Stockham stages of mixed.cuh (stage s of radix R, NS = the product of the earlier radices:
 // butterfly j reads x[j + r N/R], multiplies by W_{NS R}^{r (j mod NS)}, takes an R-point DFT and
@@ -10,8 +10,8 @@
 // each thread keeps its K = ceil((N/R) / T) butterflies of a stage in registers between a read
 // phase and a write phase, so one buffer of N pair slots serves every stage in place (two block
 // barriers per stage) and two blocks fit on an SM. Radices: 16, 8, 4, 2 (the engine's
-// butterflies) and odd primes up to 13 (the pair-sum DFT of mixed.cuh); lengths with a larger
-// prime factor keep the shared-memory engine of mixed.cuh.
+// butterflies), odd primes up to 13 (the pair-sum DFT of mixed.cuh) and one larger prime up to
+// 61 as the last stage (pair_stage_big).
 #pragma once
 #include "fft_pair.cuh"
 #include "mixed.cuh"
@@ -24,10 +24,18 @@ using pk::u64;
 
 constexpr int kMaxOddRadix = 13;
 
-// Threads per line pair: the smallest divisor of n from 256 to 320 (every thread then holds
-// exactly n / T samples of the pair between the transforms: 280 at 1400 and 2800), else 256.
+// Threads per line pair, a divisor of n where there is one, so that every thread holds exactly
+// n / T samples of the pair between the transforms. With a radix-8 or radix-16 stage (n a
+// multiple of 8: 16 samples per butterfly held in registers) the smallest divisor from 256 to
+// 320, else the largest from 192 to 255 (280 at 1400 and 2800); without one, where the largest
+// register-held group is smaller, the smallest from 384 to 448 (410 at 4100); else 256.
 __host__ __device__ constexpr int pair_threads(int n) {
+    if (n % 8 != 0)
+        for (int t = 384; t <= 448; ++t)
+            if (n % t == 0) return t;
     for (int t = 256; t <= 320; ++t)
+        if (n % t == 0) return t;
+    for (int t = 255; t >= 192; --t)
         if (n % t == 0) return t;
     return 256;
 }
@@ -37,8 +45,9 @@ struct PairPlan {
     int radix[kMixedMaxStages] = {};
 };
 
-// The radix sequence of mixed_plan (16s, then one of 8 / 4 / 2, then odd primes ascending),
-// restricted to odd primes up to kMaxOddRadix.
+// The radix sequence of mixed_plan (16s, then one of 8 / 4 / 2, then odd primes ascending):
+// odd primes up to kMaxOddRadix, and at most one larger prime (up to kMixedMaxRadix), which
+// the ascending order makes the last stage.
 __host__ __device__ constexpr PairPlan pair_plan(int n) {
     PairPlan p{};
     if (n < 16 || (n & 1)) {
@@ -65,6 +74,11 @@ __host__ __device__ constexpr PairPlan pair_plan(int n) {
             p.radix[p.stages++] = q;
             m /= q;
         }
+    // what is left has no factor up to 13: a prime when it is at most 61 (< 17^2)
+    if (m > 1 && m <= kMixedMaxRadix && p.stages < kMixedMaxStages) {
+        p.radix[p.stages++] = m;
+        m = 1;
+    }
     if (m != 1) p.stages = -1;
     return p;
 }
@@ -163,6 +177,98 @@ __device__ __forceinline__ void pair_stage(CP* buf, int tid, const float2* __res
     __syncthreads();
 }
 
+// The last stage when its radix R is a prime above kMaxOddRadix (41 at N = 4100): the last
+// stage's butterfly j writes exactly the positions j + r N/R it reads, so it runs in place in
+// two block-wide steps, as mixed_stage_any in mixed.cuh. (1) One task per butterfly and pair
+// b = 1 ... (R-1)/2 twiddles u_b and u_{R-b} and leaves s_b = u_b + u_{R-b}, d_b = u_b - u_{R-b}
+// in their places. (2) One task per butterfly and group of G outputs (a = g G + 1 ... g G + G,
+// with their mirrors R - a, and a = 0 for group 0) accumulates the pair-sum DFT in registers,
+// reading every s_b, d_b of its butterfly; after a barrier the tasks write their outputs.
+template <int N, int T, int R, int NS, bool INV>
+__device__ __forceinline__ void pair_stage_big(CP* buf, int tid, const float2* __restrict__ lin) {
+    static_assert(NS * R == N, "a prime radix above 13 runs as the last stage");
+    constexpr int NB = N / R;                       // butterflies = the stage's span NS
+    constexpr int H = (R - 1) / 2;
+    // output groups per butterfly: as many as the block has threads for (one task each), at
+    // least enough for groups of at most 10 outputs
+    constexpr int GN_T = T / NB > 0 ? T / NB : 1;
+    constexpr int GN_MIN = (H + 9) / 10;
+    constexpr int GN = GN_T > GN_MIN ? (GN_T < H ? GN_T : H) : GN_MIN;
+    constexpr int G = (H + GN - 1) / GN;
+    constexpr int TASKS = NB * GN;
+    static_assert(TASKS <= T, "one task per thread");
+    static_assert(R <= 64, "entries of the constant table");
+    __shared__ CP cst[64];                          // (cos, sin) of 2 pi m / R, m < R, both lanes
+    for (int m = tid; m < R; m += T) {
+        const float2 w = __ldg(lin + m * NB);       // cos - i sin
+        cst[m] = CP{pk::pack(w.x, w.x), pk::pack(-w.y, -w.y)};
+    }
+    // (1) twiddles W_N^{b j} (the last stage's span is N / R, its step 1) and pair sums
+#pragma unroll 2
+    for (int task = tid; task < NB * H; task += T) {
+        const int j = task % NB, b = task / NB + 1;
+        const int pb = mpad(j + b * NB), pc = mpad(j + (R - b) * NB);
+        u64 wr, wi;
+        CP ub = buf[pb], uc = buf[pc];
+        pk::load_tw(lin + b * j, wr, wi);
+        ub = pk::cmul_b<INV>(ub, wr, wi);
+        pk::load_tw(lin + (R - b) * j, wr, wi);
+        uc = pk::cmul_b<INV>(uc, wr, wi);
+        buf[pb] = pk::cadd(ub, uc);
+        buf[pc] = pk::csub(ub, uc);
+    }
+    __syncthreads();
+    // (2) sums of task (g, j), held in registers until every task has read its butterfly;
+    // the loop over b runs at run time (m = a b mod R advanced by additions) so that the
+    // constant-table loads stay next to their use
+    CP re[G], im[G], o0;
+    const int g = tid / NB, j = tid % NB;
+    const bool busy = tid < TASKS;
+    if (busy) {
+        const CP u0 = buf[mpad(j)];
+        o0 = u0;
+        int m[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            re[q] = u0;
+            im[q] = CP{0ull, 0ull};
+            m[q] = 0;
+        }
+        const int a0 = g * G + 1;
+#pragma unroll 1
+        for (int b = 1; b <= H; ++b) {
+            const CP sb = buf[mpad(j + b * NB)], db = buf[mpad(j + (R - b) * NB)];
+            o0 = pk::cadd(o0, sb);                  // used by group 0 only
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                m[q] += a0 + q;
+                if (m[q] >= R) m[q] -= R;
+                const CP w = cst[m[q]];             // w.re = cos, w.im = sin
+                re[q].re = pk::fma2(sb.re, w.re, re[q].re);
+                re[q].im = pk::fma2(sb.im, w.re, re[q].im);
+                im[q].re = pk::fma2(db.re, w.im, im[q].re);
+                im[q].im = pk::fma2(db.im, w.im, im[q].im);
+            }
+        }
+    }
+    __syncthreads();
+    if (busy) {
+        if (g == 0) buf[mpad(j)] = o0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int a = g * G + 1 + q;
+            if (a <= H) {
+                // -i im = (im.im, -im.re)
+                const CP p{pk::add2(re[q].re, im[q].im), pk::sub2(re[q].im, im[q].re)};
+                const CP r{pk::sub2(re[q].re, im[q].im), pk::add2(re[q].im, im[q].re)};
+                buf[mpad(j + a * NB)] = INV ? r : p;
+                buf[mpad(j + (R - a) * NB)] = INV ? p : r;
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // N-point DFT of the line pair in buf, natural order in and out.
 template <int N, int T, bool INV, int S = 0, int NS = 1>
 __device__ __forceinline__ void pair_fft(CP* buf, int tid, const float2* __restrict__ lin) {
@@ -170,7 +276,11 @@ __device__ __forceinline__ void pair_fft(CP* buf, int tid, const float2* __restr
     static_assert(P.stages > 0, "a length of the packed-pair mixed engine");
     if constexpr (S < P.stages) {
         constexpr int R = P.radix[S];
-        pair_stage<N, T, R, NS, INV>(buf, tid, lin);
+        if constexpr (R % 2 == 1 && R > kMaxOddRadix) {
+            pair_stage_big<N, T, R, NS, INV>(buf, tid, lin);
+        } else {
+            pair_stage<N, T, R, NS, INV>(buf, tid, lin);
+        }
         pair_fft<N, T, INV, S + 1, NS * R>(buf, tid, lin);
     }
 }
@@ -311,7 +421,7 @@ col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a) {
 }
 
 // Whether the packed-pair engine has an instance for complex64 lines of length n.
-inline bool mixed_pair_length(int n) { return n == 1400 || n == 2800; }
+inline bool mixed_pair_length(int n) { return n == 1400 || n == 2800 || n == 4100; }
 
 namespace detail {
 
@@ -343,6 +453,7 @@ inline cudaError_t row_launch_mixed_pair(int n, const RowArgs<float2>& a, const 
     switch (n) {
         case 1400: return row_launch_mixed_pair_n<1400>(a, l);
         case 2800: return row_launch_mixed_pair_n<2800>(a, l);
+        case 4100: return row_launch_mixed_pair_n<4100>(a, l);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -351,6 +462,7 @@ inline cudaError_t col_launch_mixed_pair(int n, const ColArgs<float2>& a, const 
     switch (n) {
         case 1400: return col_launch_mixed_pair_n<1400>(a, l);
         case 2800: return col_launch_mixed_pair_n<2800>(a, l);
+        case 4100: return col_launch_mixed_pair_n<4100>(a, l);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -95,7 +95,8 @@ cudaError_t launch_col_pass<float2>(int n, int lines, const ColArgs<float2>& a, 
 }
 
 int col_lines_default(int n, bool dbl) {
-    if (n & (n - 1)) return 0;                      // mixed radix: its launcher picks the width
+    if (n & (n - 1)) return !dbl && mixed_pair_length(n) ? -5 : 0;   // mixed radix: packed pairs, or
+                                                                      // the launcher picks the width
     if (dbl) {
         switch (n) {
             case 4096: return 1;
@@ -112,7 +113,7 @@ int col_lines_default(int n, bool dbl) {
     }
 }
 
-int row_variant_default(int n) { return (n >= 1024 && n <= 4096) ? 3 : 0; }
+int row_variant_default(int n) { return mixed_pair_length(n) ? 6 : (n >= 1024 && n <= 4096) ? 3 : 0; }
 
 int col_candidates(int n, int* out) {
     switch (n) {
@@ -178,6 +179,10 @@ bool mixed_length_ok(int n, bool dbl) { return dbl ? mixed_supported<double2>(n)
 
 void describe_pass(int n, bool dbl, bool row, int variant, int lines, int* persistent, int* out_lines) {
     int p = 0, w = 0;
+    if ((n & (n - 1)) && !dbl) {                            // the defaults of launch_*_pass<float2>
+        if (row && variant < 0) variant = row_variant_default(n);
+        if (!row && lines == 0) lines = col_lines_default(n, false);
+    }
     if ((n & (n - 1)) && !dbl && mixed_pair_length(n) && (row ? variant == 6 : lines == -5)) {
         if (persistent) *persistent = 9;                    // mixed-radix packed pairs
         if (out_lines) *out_lines = row ? 1 : 2;

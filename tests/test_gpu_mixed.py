@@ -100,6 +100,26 @@ def test_relay_plan_2800(ctx):
         plan.set_pass_kernel(0, 8)
 
 
+def test_mixed_pair_engine_4100_both_engines(ctx):
+    """N = 4100 = 4 x 5 x 5 x 41 (App. B's npix 1025 x 4): an angular-spectrum hop on the
+    packed-pair engine (its default; the prime 41 as an in-place last stage) and on the
+    shared-memory engine, against the oracle."""
+    n, dx, lam, z = 4100, 2.0 / 4100, 600e-9, 1.5
+    f = inputs.random_field((1, n, n), seed=11)
+    ref = propagation.angular_spectrum(f[0], dx, lam, z)
+    plan = coro.FresnelPlan(ctx, n=n, batch=1, pixelscale=dx, wavelength=np.array([lam]), distances=[z],
+                            methods=[coro.FRESNEL_AS], elements=[])
+    seen = set()
+    for rv, cl in ((6, -5), (0, 2)):
+        plan.set_pass_kernel(rv, cl)
+        seen |= {plan.pass_kernel(i) for i in range(plan.launch_count)}
+        assert all(plan.pass_radix(i) == [4, 5, 5, 41] for i in range(plan.launch_count))
+        x = to_dev(f, torch.complex64)
+        plan.execute(x)
+        assert rel_l2(x.cpu().numpy()[0], ref) < 1e-5, (rv, cl)
+    assert {"row_pass_mixed_pair<4100>", "col_pass_mixed_pair<4100,2>"} <= seen
+
+
 @pytest.mark.parametrize("n,npix", [(1400, 350), (2800, 700)])
 def test_mixed_pair_engine_direct_and_as_hops(ctx, n, npix):
     """The packed-pair mixed-radix kernels (row variant 6, column kernel -5) on a direct hop
