@@ -84,6 +84,37 @@ __global__ void lin_twiddle_kernel(C* tw, int n) {
     tw[m] = mk<C>((typename real_of<C>::type)c, (typename real_of<C>::type)s);
 }
 
+// Per-stage twiddle blocks of the mixed-radix packed-pair engine (mixed_pair.cuh), stored after
+// the linear table: stage s (radix R, span NS > 1) holds W_{NS R}^{r k} at (r - 1) NS + k,
+// r = 1 ... R-1, k < NS, so that the twiddles of consecutive butterflies are adjacent.
+struct StagePlan {
+    int stages;
+    int radix[16];
+};
+
+template <typename C>
+__global__ void stage_twiddle_kernel(C* tw, int count, StagePlan sp) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    int ns = 1, off = 0;
+    for (int st = 0; st < sp.stages; ++st) {
+        const int r_pass = sp.radix[st];
+        if (ns > 1) {
+            const int len = (r_pass - 1) * ns;
+            if (m < off + len) {
+                const int r = 1 + (m - off) / ns, k = (m - off) % ns;
+                double s, c;
+                sincospi(-2.0 * (double)((long long)r * k) / (double)((long long)ns * r_pass), &s, &c);
+                tw[m] = mk<C>((typename real_of<C>::type)c, (typename real_of<C>::type)s);
+                return;
+            }
+            off += len;
+        }
+        ns *= r_pass;
+    }
+    tw[m] = mk<C>(0, 0);
+}
+
 template <typename C>
 __global__ void twiddle_kernel(C* tw, int n) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,20 +170,30 @@ __global__ void sep_table_kernel(C* out, int n, const TabSpec* spec) {
 namespace coro {
 
 // linear: the table W_n^m of the shared-memory engine even when n is a power of two (kept
-// under the key -n beside the per-pass blocks).
+// under the key -n beside the per-pass blocks). At a mixed-radix n the complex64 table holds the
+// linear table, then the per-stage blocks of the packed-pair engine (stage_twiddle_kernel).
 const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st, bool linear) {
     auto& cache = dbl ? ctx->tw64 : ctx->tw32;
     const int key = (linear && is_pow2(n)) ? -n : n;
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
+    StagePlan sp{};
+    int extra = 0;
+    if (!is_pow2(n) && !dbl) {
+        sp.stages = pass_radices(n, true, 0, 0, sp.radix, 16);
+        for (int s = 0, ns = 1; s < sp.stages; ns *= sp.radix[s], ++s)
+            if (ns > 1) extra += (sp.radix[s] - 1) * ns;
+    }
     void* p = nullptr;
-    const size_t bytes = (size_t)n * (dbl ? sizeof(double2) : sizeof(float2));
+    const size_t bytes = (size_t)(n + extra) * (dbl ? sizeof(double2) : sizeof(float2));
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) { *st = cuda_fail(e, "cudaMalloc(twiddles)"); return nullptr; }
     const int th = 256;
     if (!is_pow2(n) || linear) {                // mixed-radix passes: the linear table W_n^m
         if (dbl) lin_twiddle_kernel<double2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((double2*)p, n);
         else lin_twiddle_kernel<float2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((float2*)p, n);
+        if (extra > 0)
+            stage_twiddle_kernel<float2><<<(extra + th - 1) / th, th, 0, ctx->stream>>>((float2*)p + n, extra, sp);
     } else if (dbl) {
         twiddle_kernel<double2><<<(n + th - 1) / th, th, 0, ctx->stream>>>((double2*)p, n);
     } else {

@@ -126,13 +126,13 @@ __device__ __forceinline__ void odd_dftp(CP (&u)[R], const u64* cs, const u64* s
 }
 
 // One in-place Stockham stage over the line pair in buf (every thread of the block calls it
-// after a barrier that made buf complete; it ends with one). lin: the linear table W_N^m.
-template <int N, int T, int R, int NS, bool INV>
+// after a barrier that made buf complete; it ends with one). lin: the linear table W_N^m, and
+// from entry OFF the stage's twiddle block, W_{NS R}^{r k} at (r - 1) NS + k.
+template <int N, int T, int R, int NS, int OFF, bool INV>
 __device__ __forceinline__ void pair_stage(CP* buf, int tid, const float2* __restrict__ lin) {
     constexpr int NB = N / R;                       // butterflies
     constexpr int K = (NB + T - 1) / T;             // per thread
     constexpr bool FULL = NB % T == 0;
-    constexpr int STEP = N / (NS * R);              // W_{NS R}^e = W_N^(e STEP)
     CP u[K][R];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
@@ -163,7 +163,7 @@ __device__ __forceinline__ void pair_stage(CP* buf, int tid, const float2* __res
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
                     u64 wr, wi;
-                    pk::load_tw(lin + r * k * STEP, wr, wi);
+                    pk::load_tw(lin + OFF + (r - 1) * NS + k, wr, wi);
                     u[i][r] = pk::cmul_b<INV>(u[i][r], wr, wi);
                 }
             }
@@ -184,7 +184,7 @@ __device__ __forceinline__ void pair_stage(CP* buf, int tid, const float2* __res
 // in their places. (2) One task per butterfly and group of G outputs (a = g G + 1 ... g G + G,
 // with their mirrors R - a, and a = 0 for group 0) accumulates the pair-sum DFT in registers,
 // reading every s_b, d_b of its butterfly; after a barrier the tasks write their outputs.
-template <int N, int T, int R, int NS, bool INV>
+template <int N, int T, int R, int NS, int OFF, bool INV>
 __device__ __forceinline__ void pair_stage_big(CP* buf, int tid, const float2* __restrict__ lin) {
     static_assert(NS * R == N, "a prime radix above 13 runs as the last stage");
     constexpr int NB = N / R;                       // butterflies = the stage's span NS
@@ -203,16 +203,16 @@ __device__ __forceinline__ void pair_stage_big(CP* buf, int tid, const float2* _
         const float2 w = __ldg(lin + m * NB);       // cos - i sin
         cst[m] = CP{pk::pack(w.x, w.x), pk::pack(-w.y, -w.y)};
     }
-    // (1) twiddles W_N^{b j} (the last stage's span is N / R, its step 1) and pair sums
+    // (1) twiddles W_N^{b j} (the last stage's span NS is N / R) and pair sums
 #pragma unroll 2
     for (int task = tid; task < NB * H; task += T) {
         const int j = task % NB, b = task / NB + 1;
         const int pb = mpad(j + b * NB), pc = mpad(j + (R - b) * NB);
         u64 wr, wi;
         CP ub = buf[pb], uc = buf[pc];
-        pk::load_tw(lin + b * j, wr, wi);
+        pk::load_tw(lin + OFF + (b - 1) * NB + j, wr, wi);
         ub = pk::cmul_b<INV>(ub, wr, wi);
-        pk::load_tw(lin + (R - b) * j, wr, wi);
+        pk::load_tw(lin + OFF + (R - b - 1) * NB + j, wr, wi);
         uc = pk::cmul_b<INV>(uc, wr, wi);
         buf[pb] = pk::cadd(ub, uc);
         buf[pc] = pk::csub(ub, uc);
@@ -269,27 +269,29 @@ __device__ __forceinline__ void pair_stage_big(CP* buf, int tid, const float2* _
     __syncthreads();
 }
 
-// N-point DFT of the line pair in buf, natural order in and out.
-template <int N, int T, bool INV, int S = 0, int NS = 1>
+// N-point DFT of the line pair in buf, natural order in and out. lin: the linear table W_N^m
+// followed by the per-stage twiddle blocks of every stage with NS > 1 (OFF: the next block).
+template <int N, int T, bool INV, int S = 0, int NS = 1, int OFF = N>
 __device__ __forceinline__ void pair_fft(CP* buf, int tid, const float2* __restrict__ lin) {
     constexpr PairPlan P = pair_plan(N);
     static_assert(P.stages > 0, "a length of the packed-pair mixed engine");
     if constexpr (S < P.stages) {
         constexpr int R = P.radix[S];
         if constexpr (R % 2 == 1 && R > kMaxOddRadix) {
-            pair_stage_big<N, T, R, NS, INV>(buf, tid, lin);
+            pair_stage_big<N, T, R, NS, OFF, INV>(buf, tid, lin);
         } else {
-            pair_stage<N, T, R, NS, INV>(buf, tid, lin);
+            pair_stage<N, T, R, NS, OFF, INV>(buf, tid, lin);
         }
-        pair_fft<N, T, INV, S + 1, NS * R>(buf, tid, lin);
+        pair_fft<N, T, INV, S + 1, NS * R, (NS > 1 ? OFF + (R - 1) * NS : OFF)>(buf, tid, lin);
     }
 }
 
 }  // namespace mpair
 
 // grid (N / 2, batch): one block per row pair (rows 2 blockIdx.x and 2 blockIdx.x + 1, packed
-// as lanes 0 / 1); a.tw is the linear table of N. Elements are evaluated per row and sample
-// (apply_elems_n, as in the one-line engines) between the inverse and the forward transform.
+// as lanes 0 / 1); a.tw is the linear table of N with the per-stage blocks after it. Elements
+// are evaluated per row and sample (apply_elems_n, as in the one-line engines) between the
+// inverse and the forward transform.
 template <int N, int T>
 __global__ void __launch_bounds__(T, 2)
 row_pass_mixed_pair_kernel(const __grid_constant__ RowArgs<float2> a) {
