@@ -83,6 +83,11 @@ __host__ __device__ constexpr PairPlan pair_plan(int n) {
     return p;
 }
 
+// Resident blocks per SM the kernels are compiled for (their register budget): three where a
+// stage holds at most 16 samples per thread (1400, 2800), two at 4100, whose 410-thread blocks
+// hold the radix-41 output sums.
+__host__ __device__ constexpr int pair_min_blocks(int n) { return pair_threads(n) <= 320 ? 3 : 2; }
+
 // Shared bytes of one line pair (N pair slots at mpad positions).
 __host__ __device__ constexpr size_t pair_smem(int n) { return (size_t)(mpad(n) + 1) * sizeof(CP); }
 
@@ -293,7 +298,7 @@ __device__ __forceinline__ void pair_fft(CP* buf, int tid, const float2* __restr
 // are evaluated per row and sample (apply_elems_n, as in the one-line engines) between the
 // inverse and the forward transform.
 template <int N, int T>
-__global__ void __launch_bounds__(T, 2)
+__global__ void __launch_bounds__(T, mpair::pair_min_blocks(N))
 row_pass_mixed_pair_kernel(const __grid_constant__ RowArgs<float2> a) {
     using mpair::CP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -368,7 +373,7 @@ row_pass_mixed_pair_kernel(const __grid_constant__ RowArgs<float2> a) {
 // 16-byte segment per row); tab_y multiplies between the transforms, tab_x (per column, which
 // commutes with the column transforms) after them.
 template <int N, int T>
-__global__ void __launch_bounds__(T, 2)
+__global__ void __launch_bounds__(T, mpair::pair_min_blocks(N))
 col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a) {
     using mpair::CP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
