@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace coro {
 
 template <typename T> struct cplx;
@@ -28,6 +30,28 @@ template <typename C> __device__ __forceinline__ C mk(typename real_of<C>::type 
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+// complex64: the real and imaginary parts of one sample as one FP32x2 pair, so that a complex
+// add or subtract issues as one packed instruction (Blackwell .f32x2) instead of two
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return bits_f2(d);
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return bits_f2(d);
+}
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -74,8 +98,22 @@ template <bool INV, typename C> __device__ __forceinline__ void dft2(C& a0, C& a
 }
 
 template <bool INV, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
-    C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mi<INV>(csub(a1, a3));
-    a0 = cadd(t0, t2); a2 = csub(t0, t2); a1 = cadd(t1, t3); a3 = csub(t1, t3);
+    if constexpr (std::is_same<C, float2>::value) {
+        // the -+i rotation of d folds into scalar adds; the other six complex adds are packed
+        const C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
+        a0 = cadd(t0, t2);
+        a2 = csub(t0, t2);
+        if (INV) {                                  // t3 = +i d = (-d.y, d.x)
+            a1 = mk<C>(t1.x - d.y, t1.y + d.x);
+            a3 = mk<C>(t1.x + d.y, t1.y - d.x);
+        } else {                                    // t3 = -i d = (d.y, -d.x)
+            a1 = mk<C>(t1.x + d.y, t1.y - d.x);
+            a3 = mk<C>(t1.x - d.y, t1.y + d.x);
+        }
+    } else {
+        C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mi<INV>(csub(a1, a3));
+        a0 = cadd(t0, t2); a2 = csub(t0, t2); a1 = cadd(t1, t3); a3 = csub(t1, t3);
+    }
 }
 
 // R-point DFT in place, natural order in and out: out[k] = sum_r in[r] W_R^{rk}.
