@@ -15,6 +15,7 @@
 
 #include "capi_common.h"
 #include "passes.cuh"
+#include "rader.cuh"
 #include "tc_ptx.cuh"
 
 using namespace coro;
@@ -96,6 +97,7 @@ template <typename C>
 __global__ void stage_twiddle_kernel(C* tw, int count, StagePlan sp) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= count) return;
+    using R = typename real_of<C>::type;
     int ns = 1, off = 0;
     for (int st = 0; st < sp.stages; ++st) {
         const int r_pass = sp.radix[st];
@@ -105,12 +107,41 @@ __global__ void stage_twiddle_kernel(C* tw, int count, StagePlan sp) {
                 const int r = 1 + (m - off) / ns, k = (m - off) % ns;
                 double s, c;
                 sincospi(-2.0 * (double)((long long)r * k) / (double)((long long)ns * r_pass), &s, &c);
-                tw[m] = mk<C>((typename real_of<C>::type)c, (typename real_of<C>::type)s);
+                tw[m] = mk<C>((R)c, (R)s);
                 return;
             }
             off += len;
         }
         ns *= r_pass;
+    }
+    // Rader tables of a prime last radix p (rader.cuh): w_L^i, then B_f[k], B_i[k] =
+    // (1/L) sum_i b_i w_L^(ik) with b_i = exp(-+2 pi i g^(-i) / p), each term's phase reduced as
+    // an exact fraction of a cycle before the FP64 sine and cosine
+    const int p = sp.stages > 0 ? sp.radix[sp.stages - 1] : 0;
+    const int L = p - 1, i = m - off;
+    if (rader_l1(p) && i >= 0 && i < 3 * L) {
+        if (i < L) {
+            double s, c;
+            sincospi(-2.0 * (double)i / (double)L, &s, &c);
+            tw[m] = mk<C>((R)c, (R)s);
+            return;
+        }
+        const int k = (i - L) % L;
+        const double sgn = i < 2 * L ? -1.0 : 1.0;    // B_f: W_p = exp(-2 pi i / p); B_i: its conjugate
+        const int g = rader_root(p);
+        double re = 0.0, im = 0.0;
+        for (int t = 0; t < L; ++t) {
+            const int gi = rader_pow(g, (L - t) % L, p);            // g^(-t) mod p
+            // phase in cycles: sgn g^-t / p - t k / L (mod 1)
+            double cyc = sgn * (double)gi / (double)p - (double)((t * k) % L) / (double)L;
+            cyc -= rint(cyc);
+            double s, c;
+            sincospi(2.0 * cyc, &s, &c);
+            re += c;
+            im += s;
+        }
+        tw[m] = mk<C>((R)(re / L), (R)(im / L));
+        return;
     }
     tw[m] = mk<C>(0, 0);
 }
@@ -183,6 +214,7 @@ const void* get_twiddles(coro_ctx ctx, int n, bool dbl, coro_status* st, bool li
         sp.stages = pass_radices(n, true, 0, 0, sp.radix, 16);
         for (int s = 0, ns = 1; s < sp.stages; ns *= sp.radix[s], ++s)
             if (ns > 1) extra += (sp.radix[s] - 1) * ns;
+        if (sp.stages > 0) extra += rader_table_len(sp.radix[sp.stages - 1]);
     }
     void* p = nullptr;
     const size_t bytes = (size_t)(n + extra) * (dbl ? sizeof(double2) : sizeof(float2));

@@ -11,10 +11,11 @@
 // phase and a write phase, so one buffer of N pair slots serves every stage in place (two block
 // barriers per stage) and two blocks fit on an SM. Radices: 16, 8, 4, 2 (the engine's
 // butterflies), odd primes up to 13 (the pair-sum DFT of mixed.cuh) and one larger prime up to
-// 61 as the last stage (pair_stage_big).
+// 61 as the last stage (pair_stage_rader; pair_stage_big where R - 1 has no Rader split).
 #pragma once
 #include "fft_pair.cuh"
 #include "mixed.cuh"
+#include "rader.cuh"
 
 namespace coro {
 namespace mpair {
@@ -274,6 +275,132 @@ __device__ __forceinline__ void pair_stage_big(CP* buf, int tid, const float2* _
     __syncthreads();
 }
 
+// Rader's stage for a prime last radix R (41 at N = 4100; rader.cuh): the butterfly's R outputs
+// from a cyclic convolution of length L = R - 1 = L1 L2 done as two length-L DFTs, in place in
+// the butterfly's own slots. Index i of the convolution lives at slot g^i (position
+// j + g^i N/R). The second DFT is a forward one: its output at index i is the convolution at
+// -i, which is X[g^i] - x[0], so every value returns to the slot it came from and no step holds
+// registers across a barrier. (1) One task per butterfly and q2 < L2: the Stockham twiddles, an
+// L1-point DFT over i = L2 q1 + q2, the twiddles w_L^(q2 k1). (2) One task per butterfly and
+// k1 < L1: an L2-point DFT (giving A = DFT_L(a); x[0] + A[0] is X[0]), the product with the
+// table B (the DFT of the convolution kernel, divided by L), another L2-point DFT and the
+// twiddles of the second transform. (3) One task per butterfly and i2 < L2: an L1-point DFT,
+// plus x[0].
+template <int N, int T, int R, int NS, int OFF, bool INV>
+__device__ __forceinline__ void pair_stage_rader(CP* buf, int tid, const float2* __restrict__ lin) {
+    static_assert(NS * R == N, "a prime radix above 13 runs as the last stage");
+    constexpr int NB = N / R;
+    constexpr int L = R - 1;
+    constexpr int L1 = rader_l1(R);
+    constexpr int L2 = L / L1;
+    constexpr int G = rader_root(R);
+    constexpr int G2 = rader_pow(G, L2, R);        // g^L2: one step of q1 (or k1, i1)
+    constexpr int ROFF = OFF + (R - 1) * NS;       // the Rader tables follow the stage's block
+    static_assert(L1 > 0 && L1 * L2 == L && (L2 % 2 == 1), "Rader split");
+    const float2* wl = lin + ROFF;                  // w_L^m
+    const float2* bt = lin + ROFF + (INV ? 2 : 1) * L;
+    __shared__ CP xs[NB];                           // x[0] of every butterfly
+    constexpr int H = (L2 - 1) / 2 + 1;
+    u64 cs[H], sn[H], ns[H];                        // L2-point DFT constants: w_L^(m L1) = w_L2^m
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+        const float2 w = __ldg(wl + m * L1);
+        cs[m] = pk::pack(w.x, w.x);
+        sn[m] = pk::pack(-w.y, -w.y);
+        ns[m] = pk::pack(w.y, w.y);
+    }
+    // (1)
+#pragma unroll 1
+    for (int task = tid; task < NB * L2; task += T) {
+        const int q2 = task / NB, j = task % NB;
+        const int r0 = rader_pow(G, q2, R);
+        CP u[L1];
+        int r = r0;
+#pragma unroll
+        for (int q1 = 0; q1 < L1; ++q1) {
+            u64 wr, wi;
+            pk::load_tw(lin + OFF + (r - 1) * NS + j, wr, wi);
+            u[q1] = pk::cmul_b<INV>(buf[mpad(j + r * NB)], wr, wi);
+            r = r * G2 % R;
+        }
+        pk::dftp<L1, false>(u);
+#pragma unroll
+        for (int k1 = 1; k1 < L1; ++k1) {
+            u64 wr, wi;
+            pk::load_tw(wl + q2 * k1, wr, wi);
+            u[k1] = pk::cmul_b<false>(u[k1], wr, wi);
+        }
+        r = r0;
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) {
+            buf[mpad(j + r * NB)] = u[k1];
+            r = r * G2 % R;
+        }
+    }
+    __syncthreads();
+    // (2)
+#pragma unroll 1
+    for (int task = tid; task < NB * L1; task += T) {
+        const int k1 = task / NB, j = task % NB;
+        const int r0 = rader_pow(G2, k1, R);
+        CP v[L2];
+        int r = r0;
+#pragma unroll
+        for (int q2 = 0; q2 < L2; ++q2) {
+            v[q2] = buf[mpad(j + r * NB)];
+            r = r * G % R;
+        }
+        if constexpr (L2 > 1) odd_dftp<L2, false>(v, cs, sn, ns);        // A[k1 + L1 k2] in v[k2]
+        if (k1 == 0) {
+            const CP x0 = buf[mpad(j)];
+            xs[j] = x0;
+            buf[mpad(j)] = pk::cadd(x0, v[0]);                          // X[0] = x[0] + A[0]
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) {
+            u64 wr, wi;
+            pk::load_tw(bt + k1 + L1 * k2, wr, wi);
+            v[k2] = pk::cmul_b<false>(v[k2], wr, wi);
+        }
+        if constexpr (L2 > 1) odd_dftp<L2, false>(v, cs, sn, ns);
+#pragma unroll
+        for (int i2 = 1; i2 < L2; ++i2) {
+            u64 wr, wi;
+            pk::load_tw(wl + i2 * k1, wr, wi);
+            v[i2] = pk::cmul_b<false>(v[i2], wr, wi);
+        }
+        r = r0;
+#pragma unroll
+        for (int i2 = 0; i2 < L2; ++i2) {
+            buf[mpad(j + r * NB)] = v[i2];
+            r = r * G % R;
+        }
+    }
+    __syncthreads();
+    // (3)
+#pragma unroll 1
+    for (int task = tid; task < NB * L2; task += T) {
+        const int i2 = task / NB, j = task % NB;
+        const int r0 = rader_pow(G, i2, R);
+        CP u[L1];
+        int r = r0;
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) {
+            u[k1] = buf[mpad(j + r * NB)];
+            r = r * G2 % R;
+        }
+        pk::dftp<L1, false>(u);
+        const CP x0 = xs[j];
+        r = r0;
+#pragma unroll
+        for (int i1 = 0; i1 < L1; ++i1) {
+            buf[mpad(j + r * NB)] = pk::cadd(x0, u[i1]);
+            r = r * G2 % R;
+        }
+    }
+    __syncthreads();
+}
+
 // N-point DFT of the line pair in buf, natural order in and out. lin: the linear table W_N^m
 // followed by the per-stage twiddle blocks of every stage with NS > 1 (OFF: the next block).
 template <int N, int T, bool INV, int S = 0, int NS = 1, int OFF = N>
@@ -282,7 +409,9 @@ __device__ __forceinline__ void pair_fft(CP* buf, int tid, const float2* __restr
     static_assert(P.stages > 0, "a length of the packed-pair mixed engine");
     if constexpr (S < P.stages) {
         constexpr int R = P.radix[S];
-        if constexpr (R % 2 == 1 && R > kMaxOddRadix) {
+        if constexpr (R % 2 == 1 && R > kMaxOddRadix && rader_l1(R) > 0) {
+            pair_stage_rader<N, T, R, NS, OFF, INV>(buf, tid, lin);
+        } else if constexpr (R % 2 == 1 && R > kMaxOddRadix) {
             pair_stage_big<N, T, R, NS, OFF, INV>(buf, tid, lin);
         } else {
             pair_stage<N, T, R, NS, OFF, INV>(buf, tid, lin);
