@@ -11,7 +11,7 @@
 // phase and a write phase, so one buffer of N pair slots serves every stage in place (two block
 // barriers per stage) and two blocks fit on an SM. Radices: 16, 8, 4, 2 (the engine's
 // butterflies), odd primes up to 13 (the pair-sum DFT of mixed.cuh) and one larger prime up to
-// 61 as the last stage (pair_stage_rader; pair_stage_big where R - 1 has no Rader split).
+// 61 whose R - 1 splits into them, as a Rader stage last (pair_stage_rader).
 #pragma once
 #include "fft_pair.cuh"
 #include "mixed.cuh"
@@ -47,8 +47,8 @@ struct PairPlan {
 };
 
 // The radix sequence of mixed_plan (16s, then one of 8 / 4 / 2, then odd primes ascending):
-// odd primes up to kMaxOddRadix, and at most one larger prime (up to kMixedMaxRadix), which
-// the ascending order makes the last stage.
+// odd primes up to kMaxOddRadix, and at most one larger prime (up to kMixedMaxRadix, with a
+// Rader split), which the ascending order makes the last stage.
 __host__ __device__ constexpr PairPlan pair_plan(int n) {
     PairPlan p{};
     if (n < 16 || (n & 1)) {
@@ -75,8 +75,9 @@ __host__ __device__ constexpr PairPlan pair_plan(int n) {
             p.radix[p.stages++] = q;
             m /= q;
         }
-    // what is left has no factor up to 13: a prime when it is at most 61 (< 17^2)
-    if (m > 1 && m <= kMixedMaxRadix && p.stages < kMixedMaxStages) {
+    // what is left has no factor up to 13: a prime when it is at most 61 (< 17^2), taken as a
+    // Rader stage where R - 1 splits into the engine's butterflies (rader.cuh)
+    if (m > 1 && m <= kMixedMaxRadix && rader_l1(m) > 0 && p.stages < kMixedMaxStages) {
         p.radix[p.stages++] = m;
         m = 1;
     }
@@ -84,9 +85,8 @@ __host__ __device__ constexpr PairPlan pair_plan(int n) {
     return p;
 }
 
-// Resident blocks per SM the kernels are compiled for (their register budget): three where a
-// stage holds at most 16 samples per thread (1400, 2800), two at 4100, whose 410-thread blocks
-// hold the radix-41 output sums.
+// Resident blocks per SM the kernels are compiled for (their register budget): three with
+// blocks of up to 320 threads (1400, 2800), two with the 410-thread blocks of 4100.
 __host__ __device__ constexpr int pair_min_blocks(int n) { return pair_threads(n) <= 320 ? 3 : 2; }
 
 // Shared bytes of one line pair (N pair slots at mpad positions).
@@ -178,98 +178,6 @@ __device__ __forceinline__ void pair_stage(CP* buf, int tid, const float2* __res
             const int base = (j / NS) * NS * R + k;
 #pragma unroll
             for (int r = 0; r < R; ++r) buf[mpad(base + r * NS)] = u[i][r];
-        }
-    }
-    __syncthreads();
-}
-
-// The last stage when its radix R is a prime above kMaxOddRadix (41 at N = 4100): the last
-// stage's butterfly j writes exactly the positions j + r N/R it reads, so it runs in place in
-// two block-wide steps, as mixed_stage_any in mixed.cuh. (1) One task per butterfly and pair
-// b = 1 ... (R-1)/2 twiddles u_b and u_{R-b} and leaves s_b = u_b + u_{R-b}, d_b = u_b - u_{R-b}
-// in their places. (2) One task per butterfly and group of G outputs (a = g G + 1 ... g G + G,
-// with their mirrors R - a, and a = 0 for group 0) accumulates the pair-sum DFT in registers,
-// reading every s_b, d_b of its butterfly; after a barrier the tasks write their outputs.
-template <int N, int T, int R, int NS, int OFF, bool INV>
-__device__ __forceinline__ void pair_stage_big(CP* buf, int tid, const float2* __restrict__ lin) {
-    static_assert(NS * R == N, "a prime radix above 13 runs as the last stage");
-    constexpr int NB = N / R;                       // butterflies = the stage's span NS
-    constexpr int H = (R - 1) / 2;
-    // output groups per butterfly: as many as the block has threads for (one task each), at
-    // least enough for groups of at most 10 outputs
-    constexpr int GN_T = T / NB > 0 ? T / NB : 1;
-    constexpr int GN_MIN = (H + 9) / 10;
-    constexpr int GN = GN_T > GN_MIN ? (GN_T < H ? GN_T : H) : GN_MIN;
-    constexpr int G = (H + GN - 1) / GN;
-    constexpr int TASKS = NB * GN;
-    static_assert(TASKS <= T, "one task per thread");
-    static_assert(R <= 64, "entries of the constant table");
-    __shared__ CP cst[64];                          // (cos, sin) of 2 pi m / R, m < R, both lanes
-    for (int m = tid; m < R; m += T) {
-        const float2 w = __ldg(lin + m * NB);       // cos - i sin
-        cst[m] = CP{pk::pack(w.x, w.x), pk::pack(-w.y, -w.y)};
-    }
-    // (1) twiddles W_N^{b j} (the last stage's span NS is N / R) and pair sums
-#pragma unroll 2
-    for (int task = tid; task < NB * H; task += T) {
-        const int j = task % NB, b = task / NB + 1;
-        const int pb = mpad(j + b * NB), pc = mpad(j + (R - b) * NB);
-        u64 wr, wi;
-        CP ub = buf[pb], uc = buf[pc];
-        pk::load_tw(lin + OFF + (b - 1) * NB + j, wr, wi);
-        ub = pk::cmul_b<INV>(ub, wr, wi);
-        pk::load_tw(lin + OFF + (R - b - 1) * NB + j, wr, wi);
-        uc = pk::cmul_b<INV>(uc, wr, wi);
-        buf[pb] = pk::cadd(ub, uc);
-        buf[pc] = pk::csub(ub, uc);
-    }
-    __syncthreads();
-    // (2) sums of task (g, j), held in registers until every task has read its butterfly;
-    // the loop over b runs at run time (m = a b mod R advanced by additions) so that the
-    // constant-table loads stay next to their use
-    CP re[G], im[G], o0;
-    const int g = tid / NB, j = tid % NB;
-    const bool busy = tid < TASKS;
-    if (busy) {
-        const CP u0 = buf[mpad(j)];
-        o0 = u0;
-        int m[G];
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-            re[q] = u0;
-            im[q] = CP{0ull, 0ull};
-            m[q] = 0;
-        }
-        const int a0 = g * G + 1;
-#pragma unroll 1
-        for (int b = 1; b <= H; ++b) {
-            const CP sb = buf[mpad(j + b * NB)], db = buf[mpad(j + (R - b) * NB)];
-            o0 = pk::cadd(o0, sb);                  // used by group 0 only
-#pragma unroll
-            for (int q = 0; q < G; ++q) {
-                m[q] += a0 + q;
-                if (m[q] >= R) m[q] -= R;
-                const CP w = cst[m[q]];             // w.re = cos, w.im = sin
-                re[q].re = pk::fma2(sb.re, w.re, re[q].re);
-                re[q].im = pk::fma2(sb.im, w.re, re[q].im);
-                im[q].re = pk::fma2(db.re, w.im, im[q].re);
-                im[q].im = pk::fma2(db.im, w.im, im[q].im);
-            }
-        }
-    }
-    __syncthreads();
-    if (busy) {
-        if (g == 0) buf[mpad(j)] = o0;
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-            const int a = g * G + 1 + q;
-            if (a <= H) {
-                // -i im = (im.im, -im.re)
-                const CP p{pk::add2(re[q].re, im[q].im), pk::sub2(re[q].im, im[q].re)};
-                const CP r{pk::sub2(re[q].re, im[q].im), pk::add2(re[q].im, im[q].re)};
-                buf[mpad(j + a * NB)] = INV ? r : p;
-                buf[mpad(j + (R - a) * NB)] = INV ? p : r;
-            }
         }
     }
     __syncthreads();
@@ -409,10 +317,8 @@ __device__ __forceinline__ void pair_fft(CP* buf, int tid, const float2* __restr
     static_assert(P.stages > 0, "a length of the packed-pair mixed engine");
     if constexpr (S < P.stages) {
         constexpr int R = P.radix[S];
-        if constexpr (R % 2 == 1 && R > kMaxOddRadix && rader_l1(R) > 0) {
+        if constexpr (R % 2 == 1 && R > kMaxOddRadix) {
             pair_stage_rader<N, T, R, NS, OFF, INV>(buf, tid, lin);
-        } else if constexpr (R % 2 == 1 && R > kMaxOddRadix) {
-            pair_stage_big<N, T, R, NS, OFF, INV>(buf, tid, lin);
         } else {
             pair_stage<N, T, R, NS, OFF, INV>(buf, tid, lin);
         }
