@@ -9,7 +9,7 @@
 // compile-time constants, so there is no run-time division and the butterfly loops unroll; and
 // each thread keeps its K = ceil((N/R) / T) butterflies of a stage in registers between a read
 // phase and a write phase, so one buffer of N pair slots serves every stage in place (two block
-// barriers per stage) and two blocks fit on an SM. Radices: 16, 8, 4, 2 (the engine's
+// barriers per stage) and two or three blocks share an SM. Radices: 16, 8, 4, 2 (the engine's
 // butterflies), odd primes up to 13 (the pair-sum DFT of mixed.cuh) and one larger prime up to
 // 61 whose R - 1 splits into them, as a Rader stage last (pair_stage_rader).
 #pragma once
