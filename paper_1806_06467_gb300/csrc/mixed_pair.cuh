@@ -329,9 +329,9 @@ __device__ __forceinline__ void pair_fft(CP* buf, int tid, const float2* __restr
 }  // namespace mpair
 
 // grid (N / 2, batch): one block per row pair (rows 2 blockIdx.x and 2 blockIdx.x + 1, packed
-// as lanes 0 / 1); a.tw is the linear table of N with the per-stage blocks after it. Elements
-// are evaluated per row and sample (apply_elems_n, as in the one-line engines) between the
-// inverse and the forward transform.
+// as lanes 0 / 1); a.tw is the linear table of N, then the per-stage blocks and Rader tables.
+// Elements are evaluated per row and sample (apply_elems_n, as in the one-line engines) between
+// the inverse and the forward transform.
 template <int N, int T>
 __global__ void __launch_bounds__(T, mpair::pair_min_blocks(N))
 row_pass_mixed_pair_kernel(const __grid_constant__ RowArgs<float2> a) {
