@@ -67,6 +67,9 @@ def test_plan_entry_points_reject_null_plans(dll):
         lambda: dll.coro_lyot_plan_peak(None, None, None),
         lambda: dll.coro_lyot_plan_gradient(None, None, None, None, None, 0, 0),
         lambda: dll.coro_wfc_plan_resident(None, ct.byref(i), ct.byref(i)),
+        lambda: dll.coro_fresnel_plan_pass_radix(None, 0, None, 0, ct.byref(i)),
+        lambda: dll.coro_lyot_plan_gemm_tile(None, ct.byref(i), ct.byref(i)),
+        lambda: dll.coro_lyot_plan_set_gemm_tile(None, 64),
     ]
     for k, call in enumerate(calls):
         assert call() == coro.EINVAL, k
