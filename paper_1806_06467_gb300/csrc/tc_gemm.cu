@@ -401,13 +401,15 @@ cudaError_t tc_make_operand_map(const TcOperand& op, bool bf16, CUtensorMap* map
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t tc_make_field_map(const void* base, int n, long long rows_total, int box_cols, CUtensorMap* map) {
+cudaError_t tc_make_field_map(const void* base, int n, long long rows_total, int box_cols, CUtensorMap* map,
+                              int box_rows) {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
-    if (((uintptr_t)base & 15) || box_cols * 8 % 16 || rows_total < 256) return cudaErrorInvalidValue;
+    if (((uintptr_t)base & 15) || box_cols * 8 % 16 || box_rows < 1 || box_rows > 256 || rows_total < box_rows)
+        return cudaErrorInvalidValue;
     cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows_total};
     cuuint64_t strides[1] = {(cuuint64_t)n * 8};
-    cuuint32_t box[2] = {(cuuint32_t)box_cols, 256};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -112,8 +112,9 @@ cudaError_t tc_make_operand_map(const TcOperand& op, bool bf16, CUtensorMap* map
 // *issued = the same for every 128 x 128 tile and K slice the kernel runs. Added to the outputs.
 void tc_count_flops(bool bf16, int epi, const TcItem* items, int batch, int max_m, int max_n, double* useful,
                     double* issued);
-// A field of 8-byte samples [rows_total][n] as a 2-D tensor map with boxes of box_cols x 256.
-cudaError_t tc_make_field_map(const void* base, int n, long long rows_total, int box_cols, CUtensorMap* map);
+// A field of 8-byte samples [rows_total][n] as a 2-D tensor map with boxes of box_cols x box_rows.
+cudaError_t tc_make_field_map(const void* base, int n, long long rows_total, int box_cols, CUtensorMap* map,
+                              int box_rows = 256);
 cudaError_t tc_launch(bool bf16, int epi, const CUtensorMap& mx, const CUtensorMap& mw, int max_m, int max_n,
                       int max_k, int batch, const TcArgs& args, cudaStream_t stream);
 
