@@ -92,20 +92,22 @@ __host__ __device__ constexpr int pair_min_blocks(int n) { return pair_threads(n
 // Shared bytes of one line pair (N pair slots at mpad positions).
 __host__ __device__ constexpr size_t pair_smem(int n) { return (size_t)(mpad(n) + 1) * sizeof(CP); }
 
-// Rows per TMA box of the column pass: the largest divisor of n up to 256 that is a multiple of
-// 8 (each box then starts on a 128-byte boundary of the staging buffer: 200 at 1400 and 2800),
-// or 0 where there is none (4100), which keeps plain loads and stores (a staging buffer with
-// padded boxes would leave room for one 4100 block per SM instead of two).
+// Rows per TMA box of the column pass: the largest divisor of n up to 256 (200 at 1400 and
+// 2800, 205 at 4100). Boxes sit in the staging copy at a pitch of whole 8-row (128-byte) units,
+// so that each starts on a 128-byte boundary; 0 (plain loads and stores) where the padded
+// boxes would not fit in the line buffer.
+__host__ __device__ constexpr int pair_tma_pitch(int rows) { return (rows + 7) / 8 * 8; }
 __host__ __device__ constexpr int pair_tma_rows(int n) {
-    for (int r = 256; r >= 8; r -= 8)
-        if (n % r == 0) return r;
+    for (int r = 256; r >= 8; --r)
+        if (n % r == 0)
+            return (size_t)(n / r) * pair_tma_pitch(r) * sizeof(CP) <= pair_smem(n) ? r : 0;
     return 0;
 }
-// Column-pass shared memory: the line pair, then (TMA) a dense staging copy of the two columns
-// (16 bytes per row) and its mbarrier.
-__host__ __device__ constexpr size_t pair_col_stage_off(int n) { return (pair_smem(n) + 127) / 128 * 128; }
+// Column-pass shared memory: the line pair (which also holds the dense TMA staging copy of the
+// strip on the way in and out), then the TMA mbarrier.
+__host__ __device__ constexpr size_t pair_col_bar_off(int n) { return (pair_smem(n) + 15) / 16 * 16; }
 __host__ __device__ constexpr size_t pair_col_smem(int n) {
-    return pair_tma_rows(n) ? pair_col_stage_off(n) + (size_t)n * sizeof(CP) + 16 : pair_smem(n);
+    return pair_tma_rows(n) ? pair_col_bar_off(n) + 16 : pair_smem(n);
 }
 
 // Odd R-point DFT of a packed pair, natural order in and out, from the pair sums
@@ -423,9 +425,11 @@ row_pass_mixed_pair_kernel(const __grid_constant__ RowArgs<float2> a) {
 // grid (N / 2, batch): one block per column pair (columns 2 blockIdx.x, 2 blockIdx.x + 1: one
 // 16-byte segment per row); tab_y multiplies between the transforms, tab_x (per column, which
 // commutes with the column transforms) after them. With BR > 0 the strip arrives and leaves by
-// TMA, in boxes of 2 columns x BR rows through a dense staging buffer, which moves the strided
+// TMA, in boxes of 2 columns x BR rows through a staging copy, which moves the strided
 // 16-byte rows faster than plain loads and stores (the 2800 column pass: 98 -> 86 us); mi / mo
-// are the tensor maps of a.in / a.out (boxes 2 x BR).
+// are the tensor maps of a.in / a.out (boxes 2 x BR). The staging copy is the line buffer itself,
+// read into registers before it is rearranged into the padded layout (and back on the way out),
+// so that three blocks still share an SM.
 template <int N, int T, int BR>
 __global__ void __launch_bounds__(T, mpair::pair_min_blocks(N))
 col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __grid_constant__ CUtensorMap mi,
@@ -433,12 +437,17 @@ col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __gr
     using mpair::CP;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     CP* buf = reinterpret_cast<CP*>(smem_raw);
-    float4* stage = reinterpret_cast<float4*>(smem_raw + mpair::pair_col_stage_off(N));   // [N] rows
-    uint64_t* bar = reinterpret_cast<uint64_t*>(stage + N);
+    float4* stage = reinterpret_cast<float4*>(smem_raw);                 // TMA boxes of BR rows
+    constexpr int BRP = mpair::pair_tma_pitch(BR > 0 ? BR : 8);          // box pitch in rows
+    auto srow = [](int y) { return BR > 0 ? (y / BR) * BRP + y % BR : y; };
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + mpair::pair_col_bar_off(N));
     constexpr int S = (N + T - 1) / T;
     constexpr size_t ROW4 = N / 2;                  // float4 per row
     const int col = 2 * blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
-    if constexpr (BR > 0) {
+    // TMA wants the staging boxes on 128-byte boundaries: a block whose shared memory were placed
+    // otherwise would move its strip with plain loads and stores instead (same results)
+    const bool tma = BR > 0 && (tc::smem_u32(stage) & 127u) == 0;
+    if (tma) {
         if (tid == 0) {
             tc::mbar_init(bar, 1);
             tc::fence_mbar_init();
@@ -448,17 +457,23 @@ col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __gr
         if (tid == 0) {
             tc::mbar_arrive_expect_tx(bar, (uint32_t)(N * sizeof(CP)));
 #pragma unroll 1
-            for (int q = 0; q < N / BR; ++q) tc::tma_load_2d(stage + q * BR, &mi, bar, col, b * N + q * BR);
+            for (int q = 0; q < N / BR; ++q) tc::tma_load_2d(stage + q * BRP, &mi, bar, col, b * N + q * BR);
         }
         tc::mbar_wait(bar, 0, a.err, 16);
     }
     const float4* src = reinterpret_cast<const float4*>(a.in + (size_t)b * N * N + col);
+    {
+        float4 q[S];                                 // (re_A, im_A, re_B, im_B) of rows tid + s T
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const int y = tid + s * T;
-        if (S * T == N || y < N) {
-            const float4 q = BR > 0 ? stage[y] : src[(size_t)y * ROW4];     // (re_A, im_A, re_B, im_B)
-            buf[mpad(y)] = CP{pk::pack(q.x, q.z), pk::pack(q.y, q.w)};
+        for (int s = 0; s < S; ++s) {
+            const int y = tid + s * T;
+            if (S * T == N || y < N) q[s] = tma ? stage[srow(y)] : src[(size_t)y * ROW4];
+        }
+        if (tma) __syncthreads();                    // every staged row read before the rearrangement
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int y = tid + s * T;
+            if (S * T == N || y < N) buf[mpad(y)] = CP{pk::pack(q[s].x, q[s].z), pk::pack(q[s].y, q[s].w)};
         }
     }
     __syncthreads();
@@ -483,6 +498,7 @@ col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __gr
         hi = pk::pack(ha.y, hb.y);
     }
     float4* dst = reinterpret_cast<float4*>(a.out + (size_t)b * N * N + col);
+    float4 q[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const int y = tid + s * T;
@@ -490,19 +506,23 @@ col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __gr
             CP v = buf[mpad(y)];
             if (a.flags & CF_TABLE)
                 v = CP{pk::sub2(pk::mul2(v.re, hr), pk::mul2(v.im, hi)), pk::fma2(v.re, hi, pk::mul2(v.im, hr))};
-            float4 q;
-            pk::unpack(v.re, q.x, q.z);
-            pk::unpack(v.im, q.y, q.w);
-            if constexpr (BR > 0) stage[y] = q;
-            else dst[(size_t)y * ROW4] = q;
+            pk::unpack(v.re, q[s].x, q[s].z);
+            pk::unpack(v.im, q[s].y, q[s].w);
+            if (!tma) dst[(size_t)y * ROW4] = q[s];
         }
     }
-    if constexpr (BR > 0) {
+    if (tma) {
+        __syncthreads();                             // every padded slot read before the staged copy
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int y = tid + s * T;
+            if (S * T == N || y < N) stage[srow(y)] = q[s];
+        }
         tc::fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
 #pragma unroll 1
-            for (int q = 0; q < N / BR; ++q) tc::tma_store_2d(&mo, stage + q * BR, col, b * N + q * BR);
+            for (int q = 0; q < N / BR; ++q) tc::tma_store_2d(&mo, stage + q * BRP, col, b * N + q * BR);
             tc::bulk_commit();
             tc::bulk_wait<0>();
         }
