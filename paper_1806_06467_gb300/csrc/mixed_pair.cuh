@@ -220,12 +220,13 @@ __device__ __forceinline__ void pair_stage_rader(CP* buf, int tid, const float2*
     constexpr int L1 = rader_l1(R);
     constexpr int L2 = L / L1;
     constexpr int G = rader_root(R);
-    constexpr int G2 = rader_pow(G, L2, R);        // g^L2: one step of q1 (or k1, i1)
     constexpr int ROFF = OFF + (R - 1) * NS;       // the Rader tables follow the stage's block
     static_assert(L1 > 0 && L1 * L2 == L && (L2 % 2 == 1), "Rader split");
     const float2* wl = lin + ROFF;                  // w_L^m
     const float2* bt = lin + ROFF + (INV ? 2 : 1) * L;
-    __shared__ CP xs[NB];                           // x[0] of every butterfly
+    // static shared arrays sized in whole 128-byte units, so that the dynamic line buffer after
+    // them stays 128-byte aligned for the column pass's TMA boxes
+    __shared__ __align__(128) CP xs[(NB + 7) / 8 * 8];      // x[0] of every butterfly
     constexpr int H = (L2 - 1) / 2 + 1;
     u64 cs[H], sn[H], ns[H];                        // L2-point DFT constants: w_L^(m L1) = w_L2^m
 #pragma unroll
@@ -235,19 +236,22 @@ __device__ __forceinline__ void pair_stage_rader(CP* buf, int tid, const float2*
         sn[m] = pk::pack(-w.y, -w.y);
         ns[m] = pk::pack(w.y, w.y);
     }
+    __shared__ __align__(128) int gtab[(L + 31) / 32 * 32];  // g^i mod R: the slot of index i
+    for (int m = tid; m < L; m += T) gtab[m] = rader_pow(G, m, R);
+    __syncthreads();
     // (1)
 #pragma unroll 1
     for (int task = tid; task < NB * L2; task += T) {
         const int q2 = task / NB, j = task % NB;
-        const int r0 = rader_pow(G, q2, R);
         CP u[L1];
-        int r = r0;
+        int pos[L1];                                // the slots of indices L2 q1 + q2, in and out
 #pragma unroll
         for (int q1 = 0; q1 < L1; ++q1) {
+            const int r = gtab[L2 * q1 + q2];
+            pos[q1] = mpad(j + r * NB);
             u64 wr, wi;
             pk::load_tw(lin + OFF + (r - 1) * NS + j, wr, wi);
-            u[q1] = pk::cmul_b<INV>(buf[mpad(j + r * NB)], wr, wi);
-            r = r * G2 % R;
+            u[q1] = pk::cmul_b<INV>(buf[pos[q1]], wr, wi);
         }
         pk::dftp<L1, false>(u);
 #pragma unroll
@@ -256,25 +260,20 @@ __device__ __forceinline__ void pair_stage_rader(CP* buf, int tid, const float2*
             pk::load_tw(wl + q2 * k1, wr, wi);
             u[k1] = pk::cmul_b<false>(u[k1], wr, wi);
         }
-        r = r0;
 #pragma unroll
-        for (int k1 = 0; k1 < L1; ++k1) {
-            buf[mpad(j + r * NB)] = u[k1];
-            r = r * G2 % R;
-        }
+        for (int k1 = 0; k1 < L1; ++k1) buf[pos[k1]] = u[k1];
     }
     __syncthreads();
     // (2)
 #pragma unroll 1
     for (int task = tid; task < NB * L1; task += T) {
         const int k1 = task / NB, j = task % NB;
-        const int r0 = rader_pow(G2, k1, R);
         CP v[L2];
-        int r = r0;
+        int pos[L2];                                // the slots of indices L2 k1 + q2
 #pragma unroll
         for (int q2 = 0; q2 < L2; ++q2) {
-            v[q2] = buf[mpad(j + r * NB)];
-            r = r * G % R;
+            pos[q2] = mpad(j + gtab[L2 * k1 + q2] * NB);
+            v[q2] = buf[pos[q2]];
         }
         if constexpr (L2 > 1) odd_dftp<L2, false>(v, cs, sn, ns);        // A[k1 + L1 k2] in v[k2]
         if (k1 == 0) {
@@ -295,34 +294,25 @@ __device__ __forceinline__ void pair_stage_rader(CP* buf, int tid, const float2*
             pk::load_tw(wl + i2 * k1, wr, wi);
             v[i2] = pk::cmul_b<false>(v[i2], wr, wi);
         }
-        r = r0;
 #pragma unroll
-        for (int i2 = 0; i2 < L2; ++i2) {
-            buf[mpad(j + r * NB)] = v[i2];
-            r = r * G % R;
-        }
+        for (int i2 = 0; i2 < L2; ++i2) buf[pos[i2]] = v[i2];
     }
     __syncthreads();
     // (3)
 #pragma unroll 1
     for (int task = tid; task < NB * L2; task += T) {
         const int i2 = task / NB, j = task % NB;
-        const int r0 = rader_pow(G, i2, R);
         CP u[L1];
-        int r = r0;
+        int pos[L1];                                // the slots of indices L2 k1 + i2
 #pragma unroll
         for (int k1 = 0; k1 < L1; ++k1) {
-            u[k1] = buf[mpad(j + r * NB)];
-            r = r * G2 % R;
+            pos[k1] = mpad(j + gtab[L2 * k1 + i2] * NB);
+            u[k1] = buf[pos[k1]];
         }
         pk::dftp<L1, false>(u);
         const CP x0 = xs[j];
-        r = r0;
 #pragma unroll
-        for (int i1 = 0; i1 < L1; ++i1) {
-            buf[mpad(j + r * NB)] = pk::cadd(x0, u[i1]);
-            r = r * G2 % R;
-        }
+        for (int i1 = 0; i1 < L1; ++i1) buf[pos[i1]] = pk::cadd(x0, u[i1]);
     }
     __syncthreads();
 }
