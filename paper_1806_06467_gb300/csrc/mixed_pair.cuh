@@ -103,11 +103,12 @@ __host__ __device__ constexpr int pair_tma_rows(int n) {
             return (size_t)(n / r) * pair_tma_pitch(r) * sizeof(CP) <= pair_smem(n) ? r : 0;
     return 0;
 }
-// Column-pass shared memory: the line pair (which also holds the dense TMA staging copy of the
-// strip on the way in and out), then the TMA mbarrier.
-__host__ __device__ constexpr size_t pair_col_bar_off(int n) { return (pair_smem(n) + 15) / 16 * 16; }
+// Shared memory of the passes: the line pair (which also holds the dense staging copy of the
+// rows or of the column strip on the way in, and of the strip on the way out), then the
+// mbarrier of the bulk / TMA copies.
+__host__ __device__ constexpr size_t pair_bar_off(int n) { return (pair_smem(n) + 15) / 16 * 16; }
 __host__ __device__ constexpr size_t pair_col_smem(int n) {
-    return pair_tma_rows(n) ? pair_col_bar_off(n) + 16 : pair_smem(n);
+    return pair_tma_rows(n) ? pair_bar_off(n) + 16 : pair_smem(n);
 }
 
 // Odd R-point DFT of a packed pair, natural order in and out, from the pair sums
@@ -349,16 +350,50 @@ row_pass_mixed_pair_kernel(const __grid_constant__ RowArgs<float2> a) {
     constexpr int S = (N + T - 1) / T;
     const int ya = 2 * blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const size_t ra = ((size_t)b * N + ya) * N, rb = ra + N;
+    // the two rows arrive by two bulk copies into the line buffer (dense, row A then row B),
+    // then move through registers into the padded pair layout
+    const bool bulk = !(a.flags & RF_INIT_ONE) && ((uintptr_t)a.in & 15) == 0;
+    if (bulk) {
+        float2* stage = reinterpret_cast<float2*>(smem_raw);
+        uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + mpair::pair_bar_off(N));
+        if (tid == 0) {
+            tc::mbar_init(bar, 1);
+            tc::fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            tc::mbar_arrive_expect_tx(bar, (uint32_t)(2 * N * sizeof(float2)));
+            tc::bulk_load(stage, a.in + ra, (uint32_t)(N * sizeof(float2)), bar);
+            tc::bulk_load(stage + N, a.in + rb, (uint32_t)(N * sizeof(float2)), bar);
+        }
+        tc::mbar_wait(bar, 0, a.err, 16);
+        float2 va[S], vb[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const int x = tid + s * T;
-        if (S * T == N || x < N) {
-            float2 va = make_float2(1.f, 0.f), vb = va;
-            if (!(a.flags & RF_INIT_ONE)) {
-                va = a.in[ra + x];
-                vb = a.in[rb + x];
+        for (int s = 0; s < S; ++s) {
+            const int x = tid + s * T;
+            if (S * T == N || x < N) {
+                va[s] = stage[x];
+                vb[s] = stage[N + x];
             }
-            buf[mpad(x)] = CP{pk::pack(va.x, vb.x), pk::pack(va.y, vb.y)};
+        }
+        __syncthreads();                             // every row sample read before the rearrangement
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int x = tid + s * T;
+            if (S * T == N || x < N) buf[mpad(x)] = CP{pk::pack(va[s].x, vb[s].x), pk::pack(va[s].y, vb[s].y)};
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int x = tid + s * T;
+            if (S * T == N || x < N) {
+                float2 va = make_float2(1.f, 0.f), vb = va;
+                if (!(a.flags & RF_INIT_ONE)) {
+                    va = a.in[ra + x];
+                    vb = a.in[rb + x];
+                }
+                buf[mpad(x)] = CP{pk::pack(va.x, vb.x), pk::pack(va.y, vb.y)};
+            }
         }
     }
     __syncthreads();
@@ -430,7 +465,7 @@ col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __gr
     float4* stage = reinterpret_cast<float4*>(smem_raw);                 // TMA boxes of BR rows
     constexpr int BRP = mpair::pair_tma_pitch(BR > 0 ? BR : 8);          // box pitch in rows
     auto srow = [](int y) { return BR > 0 ? (y / BR) * BRP + y % BR : y; };
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + mpair::pair_col_bar_off(N));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + mpair::pair_bar_off(N));
     constexpr int S = (N + T - 1) / T;
     constexpr size_t ROW4 = N / 2;                  // float4 per row
     const int col = 2 * blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
@@ -527,7 +562,7 @@ namespace detail {
 template <int N>
 cudaError_t row_launch_mixed_pair_n(const RowArgs<float2>& a, const PassLaunch& l) {
     constexpr int T = mpair::pair_threads(N);
-    const size_t smem = mpair::pair_smem(N);
+    const size_t smem = mpair::pair_bar_off(N) + 16;          // line buffer and mbarrier
     static unsigned done = 0;
     cudaError_t e = ensure_smem(row_pass_mixed_pair_kernel<N, T>, smem, done);
     if (e != cudaSuccess) return e;
