@@ -549,7 +549,7 @@ col_pass_mixed_pair_kernel(const __grid_constant__ ColArgs<float2> a, const __gr
 #pragma unroll 1
             for (int q = 0; q < N / BR; ++q) tc::tma_store_2d(&mo, stage + q * BRP, col, b * N + q * BR);
             tc::bulk_commit();
-            tc::bulk_wait<0>();
+            tc::bulk_wait_read<0>();         // staging read out; the writes finish with the grid
         }
     }
 }
